@@ -1,0 +1,339 @@
+"""Benchmark: SEM operator throughput and solve time on one GB300 (or N replicas).
+
+A step is one application of the assembled operator w = mask o QQ^T A_L u
+(Ax kernel + gather-scatter kernel) in FP64 on the 32x32x32-element
+deformed box [0, 2 pi]^3 at N = 7 (16,777,216 local GLL points), u ~ U(-1,1)
+seeded.  value = local points per second over all ranks (GDOF/s).  Extra
+keys report the FP32 operator, the Poisson solve to 1e-8 on the 48^3-element
+box (FP64 PCG against FP32-inner / FP64-refinement), the roofline of the Ax
+kernel, the end-to-end rate through the host-buffer C-ABI call and the
+oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--no-solve]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import seeded_inputs as si  # noqa: E402
+
+WORKLOAD = si.THROUGHPUT          # 32^3 elements, N = 7, deformed [0, 2 pi]^3
+SOLVE = si.SOLVE                  # 48^3 elements, N = 7, RHS of 8 Fourier modes, tol 1e-8
+METRIC = "Ax+dssum GDOF/s (FP64, N=7, E=32^3 deformed); CG solve to 1e-8 mixed vs FP64"
+UNIT = "GDOF/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not getattr(self, "out", ""):
+            return None
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_sample(nz):
+    """Oracle data for a 32 x 32 x nz slab of the throughput mesh (same element
+    size and deformation as the full mesh's first nz element layers)."""
+    from tests.helpers import OracleProblem
+    nel = (WORKLOAD["nel"][0], WORKLOAD["nel"][1], nz)
+    L = list(WORKLOAD["length"])
+    L[2] = L[2] * nz / WORKLOAD["nel"][2]
+    o = OracleProblem(nel, WORKLOAD["N"], length=tuple(L), deform=WORKLOAD["deform"])
+    u = si.uniform(o.shape, WORKLOAD["seed"])
+    return o, u
+
+
+def time_oracle(nz, min_seconds):
+    o, u = oracle_sample(nz)
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        o.matvec(u)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    n = u.size * runs
+    return n / el / 1e9, dict(points=u.size, runs=runs, seconds=el, nel=o.nel)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    o, u = oracle_sample(2)
+    for _ in range(args.warmup):
+        o.matvec(u)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.matvec(u)
+    el = time.perf_counter() - t0
+    value = u.size * args.steps / el / 1e9
+    sample = (f"oracle Ax+dssum on a 32x32x2 slab ({u.size} local points) of the "
+              f"32^3-element N=7 mesh per step, numpy, 1 thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "Ax+dssum, 32x32x32 deformed hex elements on [0,2pi]^3, N=7 "
+                               "(oracle sample: 32x32x2 slab)", "sample_points": int(u.size)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2107_01243_gb300 as sem
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    cfg = WORKLOAD
+    h = sem.sem_setup(cfg["nel"], cfg["N"], length=cfg["length"], deform=cfg["deform"])
+    n = h.n_local
+    u_host = torch.from_numpy(si.uniform(n, cfg["seed"])).pin_memory()
+    u = u_host.to(dev)
+    w = torch.empty_like(u)
+    u32 = u.float()
+    w32 = torch.empty_like(u32)
+
+    def step64():
+        sem.sem_ax(h, u, w)
+        sem.sem_dssum(h, w, apply_mask=True)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step64()
+    barrier()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        t0.record(stream)
+        for s in range(K):
+            ev[s][0].record(stream)
+            sem.sem_ax(h, u, w)
+            ev[s][1].record(stream)
+            sem.sem_dssum(h, w, apply_mask=True)
+            ev[s][2].record(stream)
+        t1.record(stream)
+        barrier()
+    ms = t0.elapsed_time(t1)
+    ax_ms = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
+    ds_ms = statistics.mean(b.elapsed_time(c) for _, b, c in ev)
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t)
+    value = world * n * K / (ms / 1e3) / 1e9
+
+    # FP32 operator
+    for _ in range(3):
+        sem.sem_ax(h, u32, w32)
+        sem.sem_dssum(h, w32, apply_mask=True)
+    torch.cuda.synchronize()
+    e32 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for s in range(K):
+        e32[s][0].record(stream)
+        sem.sem_ax(h, u32, w32)
+        e32[s][1].record(stream)
+        sem.sem_dssum(h, w32, apply_mask=True)
+        e32[s][2].record(stream)
+    torch.cuda.synchronize()
+    ax32 = statistics.mean(a.elapsed_time(b) for a, b, _ in e32)
+    ds32 = statistics.mean(b.elapsed_time(c) for _, b, c in e32)
+
+    # end to end through the host-buffer call
+    w_host = torch.empty_like(u_host).pin_memory()
+    for _ in range(3):
+        sem.sem_apply_host(h, u_host, w_host)
+    Ke = max(5, min(K, 50))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    a.record(stream)
+    for _ in range(Ke):
+        sem.sem_apply_host(h, u_host, w_host)
+    b.record(stream)
+    barrier()
+    e2e_ms = a.elapsed_time(b) / Ke
+    e2e = world * n / (e2e_ms / 1e3) / 1e9
+
+    hbm, peak_kind = peaks()
+    ax_bytes = 64 * n                       # u 8 + w 8 + 6 G x 8 per point
+    achieved = ax_bytes / (ax_ms / 1e3) / 1e9
+    nb_shared = 0.578125 * n                # boundary fraction at N = 7: 1 - (6/8)^3
+    ds_bytes = (8 + 8 + 4) * nb_shared
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "Ax+dssum (mask), 32x32x32 deformed hex elements on [0,2pi]^3, "
+                               "N=7, u~U(-1,1) seed 42",
+                   "local_points": n, "l2": "inputs larger than L2 (u 134 MB, G 805 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": "ax_kernel<8,double>",
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": ax_bytes},
+        "kernels": {"ax_f64_ms": ax_ms, "dssum_f64_ms": ds_ms,
+                    "dssum_f64_gbs": ds_bytes / (ds_ms / 1e3) / 1e9,
+                    "ax_f32_ms": ax32, "ax_f32_gbs": 32 * n / (ax32 / 1e3) / 1e9,
+                    "ax_f32_frac": 32 * n / (ax32 / 1e3) / 1e9 / hbm,
+                    "dssum_f32_ms": ds32,
+                    "ax_f64_gdofs": n / (ax_ms / 1e3) / 1e9,
+                    "axdssum_f32_gdofs": n / ((ax32 + ds32) / 1e3) / 1e9},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": 2 * K,
+        "clocks": clk.summary(),
+    }
+    del w, w32, u32
+    sem.sem_destroy(h)
+
+    if not args.no_solve:
+        line["solve"] = run_solves(sem, torch, dev)
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        gd, meta = time_oracle(8, 10.0)
+        line["cpu_baseline"] = {
+            "value": gd, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle Ax+dssum (numpy, FP64, 1 thread) on a 32x32x8 slab of the "
+                       f"throughput mesh ({meta['points']} points) x {meta['runs']} runs, "
+                       f"{meta['seconds']:.1f} s")}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_solves(sem, torch, dev):
+    cfg = SOLVE
+    h = sem.sem_setup(cfg["nel"], cfg["N"], length=cfg["length"], deform=cfg["deform"])
+    n = h.n_local
+    xs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(3)]
+    sem.sem_get_field(h, sem.SEM_FIELD_X, xs[0])
+    sem.sem_get_field(h, sem.SEM_FIELD_Y, xs[1])
+    sem.sem_get_field(h, sem.SEM_FIELD_Z, xs[2])
+    X, Y, Z = (t.cpu().numpy() for t in xs)
+    f = torch.from_numpy(si.eval_fourier(si.fourier_modes(cfg["seed"]), X, Y, Z)).to(dev)
+    del xs, X, Y, Z
+    b = torch.empty_like(f)
+    sem.sem_rhs(h, f, b)
+    out = {"workload": "Poisson, 48^3 deformed hex elements, N=7, 8 Fourier-mode RHS",
+           "local_points": n, "tol": cfg["tol"]}
+    for name, prec in (("fp64", sem.SEM_SOLVE_F64), ("mixed", sem.SEM_SOLVE_MIXED)):
+        x = torch.empty_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = sem.sem_cg_solve(h, b, x, tol=cfg["tol"], precision=prec)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        out[name] = {"seconds": el, "iters": info["iters"], "outer": info["outer_iters"],
+                     "rel_res": info["rel_res"], "status": info["status"]}
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    sem.sem_destroy(h)
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * sem.h -- C ABI of the GB300 spectral-element operator / solver library.
+ *
+ * The library applies and inverts the matrix-free SEM Poisson/Helmholtz
+ * operator on hexahedral elements with (N+1)^3 Gauss-Lobatto-Legendre points:
+ *
+ *   w_L = mask o QQ^T (h1 A_L + h2 B_L) u_L,   A^e = D^T G^e D
+ *
+ * (arXiv 2107.01243, §2, Eq. 9-10; gather-scatter §3.2; Krylov solve §2 end
+ * and §4).  Everything runs in hand-written sm_103a CUDA kernels; the host
+ * code only builds the mesh topology and launches.
+ *
+ * Conventions shared by every call:
+ *  - "L-vector": one value per local GLL point, n_L = E (N+1)^3 values, laid
+ *    out [e][k][j][i] with i fastest (the Fortran w(:,:,:,:) order of
+ *    Listing 1).  Element e = ex + nelx (ey + nely ez).
+ *  - Unless stated otherwise a vector argument is a DEVICE pointer owned by
+ *    the caller.  The library owns everything inside a handle (geometric
+ *    factors, mass, numbering, preconditioner, solver scratch).
+ *  - dtype: SEM_F64 (double) or SEM_F32 (float).
+ *  - stream: a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Calls are asynchronous on that stream unless stated.
+ *  - Errors: every call returns a sem_status; no exception crosses the ABI.
+ *    sem_last_error() gives a thread-local message for the last failure.
+ *  - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef SEM_GB300_H
+#define SEM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sem_handle sem_handle;
+typedef struct sem_batch sem_batch;
+
+typedef enum {
+  SEM_OK = 0,
+  SEM_ERR_ARG = 1,        /* invalid argument (sizes, null pointers, dtype) */
+  SEM_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+  SEM_ERR_NOCONV = 3,     /* solver hit maxit before reaching tol */
+  SEM_ERR_BREAKDOWN = 4,  /* CG found <p, Hp> <= 0 or a NaN (operator not SPD) */
+  SEM_ERR_TIMEOUT = 5,    /* a bounded device wait ran out */
+  SEM_ERR_OOM = 6,        /* device allocation failed */
+  SEM_ERR_STATE = 7       /* call not valid for this handle's state */
+} sem_status;
+
+enum { SEM_F64 = 0, SEM_F32 = 1 };
+
+/* precision_flags of sem_setup: which copies of the geometric factors to keep */
+enum { SEM_PREC_F64 = 1, SEM_PREC_F32 = 2 };
+
+/* solver precision (sem_solve_opts.precision) */
+enum { SEM_SOLVE_F64 = 0, SEM_SOLVE_MIXED = 1 };
+
+/* Dirichlet face bits */
+enum { SEM_FACE_XMIN = 1, SEM_FACE_XMAX = 2, SEM_FACE_YMIN = 4,
+       SEM_FACE_YMAX = 8, SEM_FACE_ZMIN = 16, SEM_FACE_ZMAX = 32,
+       SEM_FACE_ALL = 63 };
+
+/* fields readable with sem_get_field */
+enum { SEM_FIELD_X = 0, SEM_FIELD_Y = 1, SEM_FIELD_Z = 2,  /* GLL coordinates (n_L) */
+       SEM_FIELD_G = 3,      /* geometric factors, [e][6][p^3], order G11,G22,G33,G12,G13,G23 */
+       SEM_FIELD_B = 4,      /* lumped mass W detJ (n_L) */
+       SEM_FIELD_MULT = 5,   /* multiplicity of each local point (n_L) */
+       SEM_FIELD_MASK = 6,   /* Dirichlet mask 0/1 (n_L) */
+       SEM_FIELD_GID = 7,    /* global number (n_L), written as int64 whatever dtype says */
+       SEM_FIELD_DINV = 8    /* Jacobi inverse diagonal of the last solve's operator (n_L) */
+};
+
+/*
+ * Mesh description: a structured nelx x nely x nelz box of hexahedra
+ * (§2: "E non-overlapping hexahedral elements").  GLL nodes are placed at
+ * x0 + (ex + (xi+1)/2) len/nelx, then, if deform_amp != 0, moved by
+ * x += a sin(y) sin(z), y += a sin(z) sin(x), z += a sin(x) sin(y) evaluated
+ * at the undeformed position.  xyz_gll, if not NULL, is a HOST array of
+ * 3 * n_L doubles ([x | y | z], each an L-vector) that replaces the generated
+ * coordinates (same box topology).  dirichlet_faces selects the faces with
+ * u = 0 (§2, Eq. 5).
+ */
+typedef struct {
+  int nelx, nely, nelz;
+  double x0[3];
+  double len[3];
+  double deform_amp;
+  const double* xyz_gll;
+  int dirichlet_faces;
+} sem_mesh_desc;
+
+/*
+ * sem_setup -- build a handle for polynomial order N (1 <= N <= 10).
+ * Host: GLL nodes/weights, derivative matrix D (§2, Eq. 7-9), global
+ * numbering, multiplicity, Dirichlet mask and the gather-scatter segment
+ * lists (§3.2).  Device: GLL coordinates, geometric factors G (6 per point)
+ * and mass B (§2, Eq. 9) in the precisions named by precision_flags.
+ * Synchronises the stream before returning.  *out receives the handle;
+ * release it with sem_destroy.  Errors: SEM_ERR_ARG (bad sizes or N, a
+ * non-positive Jacobian), SEM_ERR_OOM, SEM_ERR_CUDA.
+ */
+sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_flags,
+                     void* stream, sem_handle** out);
+
+/* Release every device and host resource of the handle (NULL is a no-op). */
+sem_status sem_destroy(sem_handle* h);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* sem_last_error(void);
+
+/* Sizes: local points n_L, unique global points, order N, elements E. */
+sem_status sem_get_sizes(const sem_handle* h, int64_t* n_local, int64_t* n_global,
+                         int* N, int64_t* E);
+
+/*
+ * Copy one setup field (SEM_FIELD_*) into the device buffer dst, converted
+ * to dtype (SEM_FIELD_GID is always int64).  dst holds n_L values (6 n_L for
+ * SEM_FIELD_G).  SEM_ERR_STATE if the field is not kept in that precision.
+ */
+sem_status sem_get_field(sem_handle* h, int which, void* dst, int dtype, void* stream);
+
+/*
+ * sem_ax -- w_L = (h1 A_L + h2 B_L) u_L element by element, no gather-scatter
+ * (§2, Eq. 9; the ax_t compute of Listing 1).  If h1_field is not NULL it is
+ * an L-vector of per-point coefficients (same dtype) that replaces h1 at
+ * every GLL point.  u_L and w_L are distinct L-vectors of the given dtype.
+ */
+sem_status sem_ax(sem_handle* h, const void* u_L, void* w_L, double h1, double h2,
+                  const void* h1_field, int dtype, void* stream);
+
+/*
+ * sem_dssum -- in place w_L <- QQ^T w_L: every local copy of a global point
+ * receives the sum of all its copies, summed in increasing local index
+ * (§2, Eq. 10; §3.2).  With apply_mask != 0 the Dirichlet points are then
+ * set to 0.
+ */
+sem_status sem_dssum(sem_handle* h, void* w_L, int apply_mask, int dtype, void* stream);
+
+/* b_L = mask o QQ^T (B f_L): the discrete right-hand side of §2, Eq. 6 for a
+ * nodal source f (FP64 device L-vectors). */
+sem_status sem_rhs(sem_handle* h, const double* f_L, double* b_L, void* stream);
+
+/* Solver options; sem_solve_opts_default fills the defaults noted here. */
+typedef struct {
+  double h1;              /* constant diffusion coefficient (1.0) */
+  double h2;              /* mass coefficient (0.0) */
+  const double* h1_field; /* device L-vector of per-point h1 or NULL (NULL) */
+  double tol;             /* relative residual ||b - Hx|| / ||b|| (1e-8) */
+  int maxit;              /* CG iteration limit, counted over inner iterations (20000) */
+  int precision;          /* SEM_SOLVE_F64 or SEM_SOLVE_MIXED (SEM_SOLVE_F64) */
+  double inner_tol;       /* mixed: FP32 inner relative tolerance (1e-4) */
+  int max_outer;          /* mixed: refinement steps limit (30) */
+  int check_every;        /* iterations per host convergence check (16) */
+  int use_graph;          /* capture check_every iterations in a CUDA graph (1) */
+  int x0_is_zero;         /* 1: ignore x_L on input and start from 0 (1) */
+  void* stream;           /* stream of the solve (NULL) */
+} sem_solve_opts;
+
+typedef struct {
+  int iters;          /* CG iterations (all inner iterations for mixed) */
+  int outer_iters;    /* refinement steps (0 for SEM_SOLVE_F64) */
+  double rel_res;     /* final FP64 relative residual in the unique-dof norm */
+  int status;         /* sem_status of the solve */
+} sem_solve_info;
+
+void sem_solve_opts_default(sem_solve_opts* o);
+
+/*
+ * sem_cg_solve -- solve mask o QQ^T (h1 A_L + h2 B_L) x = b by Jacobi-
+ * preconditioned CG (§2 end; §4 uses PCG for the Helmholtz solves).  b_L is
+ * an assembled, masked FP64 L-vector (as from sem_rhs); x_L (FP64) receives
+ * the continuous solution.  Dots are the unique-dof inner products
+ * sum_L a b / mult accumulated in FP64.  SEM_SOLVE_MIXED runs FP32 inner PCG
+ * (FP32 G, B and vectors) inside an FP64 iterative-refinement loop whose
+ * residual r = b - Hx and update x += d are FP64.  Stops when the FP64
+ * relative residual <= tol.  Synchronises the stream once per check_every
+ * iterations and at the end.  Returns SEM_ERR_NOCONV / SEM_ERR_BREAKDOWN
+ * (with info filled) when the solve fails.
+ */
+sem_status sem_cg_solve(sem_handle* h, const double* b_L, double* x_L,
+                        const sem_solve_opts* opts, sem_solve_info* info);
+
+/*
+ * sem_helmholtz_grad -- g_L = -(D^ lambda)^T G (D^ u) at every local point,
+ * D^ the reference gradient: the derivative of lambda^T H(h1) u with
+ * respect to each local h1 value, negated -- the adjoint gradient dL/dh1 when
+ * lambda solves H lambda = mask o QQ^T dL/du (structure of §2, Eq. 9).
+ * FP64 device L-vectors.
+ */
+sem_status sem_helmholtz_grad(sem_handle* h, const double* u_L, const double* lambda_L,
+                              double* g_L, void* stream);
+
+/*
+ * sem_apply_host -- w = mask o QQ^T A_L u with HOST buffers: copies u_host
+ * (n_L values of dtype) to the device, applies Ax and dssum with the mask,
+ * copies the result to w_host and synchronises the stream.  Pinned host
+ * memory gives full copy bandwidth.
+ */
+sem_status sem_apply_host(sem_handle* h, const void* u_host, void* w_host, int dtype,
+                          void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

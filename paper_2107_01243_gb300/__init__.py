@@ -1,0 +1,17 @@
+"""GB300-native matrix-free spectral-element operator and solver.
+
+Implements the data-parallel hot path of the SEM described in arXiv
+2107.01243 (Neko): the element operator w_e = D^T G_e D u_e on hexahedra with
+(N+1)^3 GLL points, the gather-scatter QQ^T with a Dirichlet mask, Jacobi-
+preconditioned CG with FP32-inner / FP64 refinement, and the adjoint
+gradient with respect to a per-point diffusion coefficient.  All compute runs
+in the hand-written sm_103a kernels of ``lib/libsem_gb300.so`` (C ABI in
+include/sem.h); this package is its Python binding.
+"""
+from ._lib import (SemError, SEM_F64, SEM_F32, SEM_PREC_F64, SEM_PREC_F32, SEM_SOLVE_F64,
+                   SEM_SOLVE_MIXED, SEM_FACE_ALL, SEM_FIELD_X, SEM_FIELD_Y, SEM_FIELD_Z,
+                   SEM_FIELD_G, SEM_FIELD_B, SEM_FIELD_MULT, SEM_FIELD_MASK, SEM_FIELD_GID,
+                   SEM_FIELD_DINV, LIB_PATH)
+from .api import (Handle, sem_setup, sem_destroy, sem_get_sizes, sem_get_field, sem_ax,
+                  sem_dssum, sem_rhs, sem_cg_solve, sem_helmholtz_grad, sem_apply_host)
+from .autograd import HelmholtzSolve, helmholtz_solve

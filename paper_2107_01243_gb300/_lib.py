@@ -1,0 +1,99 @@
+"""ctypes binding of libsem_gb300.so (include/sem.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Importing this module does not need a GPU; the first call that
+reaches the library raises ``SemError`` when the library is missing or a
+call fails.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libsem_gb300.so")
+
+# status codes (sem_status)
+SEM_OK, SEM_ERR_ARG, SEM_ERR_CUDA, SEM_ERR_NOCONV = 0, 1, 2, 3
+SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_OOM, SEM_ERR_STATE = 4, 5, 6, 7
+STATUS_NAMES = {0: "SEM_OK", 1: "SEM_ERR_ARG", 2: "SEM_ERR_CUDA", 3: "SEM_ERR_NOCONV",
+                4: "SEM_ERR_BREAKDOWN", 5: "SEM_ERR_TIMEOUT", 6: "SEM_ERR_OOM",
+                7: "SEM_ERR_STATE"}
+SEM_F64, SEM_F32 = 0, 1
+SEM_PREC_F64, SEM_PREC_F32 = 1, 2
+SEM_SOLVE_F64, SEM_SOLVE_MIXED = 0, 1
+SEM_FACE_ALL = 63
+(SEM_FIELD_X, SEM_FIELD_Y, SEM_FIELD_Z, SEM_FIELD_G, SEM_FIELD_B, SEM_FIELD_MULT,
+ SEM_FIELD_MASK, SEM_FIELD_GID, SEM_FIELD_DINV) = range(9)
+
+
+class SemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("nelx", ctypes.c_int), ("nely", ctypes.c_int), ("nelz", ctypes.c_int),
+                ("x0", ctypes.c_double * 3), ("len", ctypes.c_double * 3),
+                ("deform_amp", ctypes.c_double), ("xyz_gll", ctypes.c_void_p),
+                ("dirichlet_faces", ctypes.c_int)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("h1", ctypes.c_double), ("h2", ctypes.c_double),
+                ("h1_field", ctypes.c_void_p), ("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("x0_is_zero", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("rel_res", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+# name -> (restype, argtypes); every symbol declared in include/sem.h
+SIGNATURES = {
+    "sem_setup": (ctypes.c_int, [ctypes.POINTER(MeshDesc), ctypes.c_int, ctypes.c_int, _P,
+                                 ctypes.POINTER(_P)]),
+    "sem_destroy": (ctypes.c_int, [_P]),
+    "sem_last_error": (ctypes.c_char_p, []),
+    "sem_get_sizes": (ctypes.c_int, [_P, _I64P, _I64P, ctypes.POINTER(ctypes.c_int), _I64P]),
+    "sem_get_field": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, _P]),
+    "sem_ax": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P, ctypes.c_int,
+                              _P]),
+    "sem_dssum": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P]),
+    "sem_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
+    "sem_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
+    "sem_cg_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(SolveOpts),
+                                    ctypes.POINTER(SolveInfo)]),
+    "sem_helmholtz_grad": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "sem_apply_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+}
+
+_lib = None
+
+
+def load():
+    """Load the library (once).  Raises SemError if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise SemError(SEM_ERR_STATE, f"CUDA library not built: {LIB_PATH} is missing "
+                       "(run __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status):
+    if status != SEM_OK:
+        msg = load().sem_last_error().decode(errors="replace")
+        raise SemError(status, msg)

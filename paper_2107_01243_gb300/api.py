@@ -1,0 +1,187 @@
+"""Python entry points with the names of the C ABI (include/sem.h).
+
+Vectors are torch tensors: L-vectors of n_L = E (N+1)^3 values on the CUDA
+device, contiguous, float64 or float32.  These functions only check and
+marshal arguments; the work is done by the library's kernels on the current
+torch stream (or the stream given).
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (SemError, MeshDesc, SolveOpts, SolveInfo, check, SEM_F64, SEM_F32,
+                   SEM_PREC_F64, SEM_PREC_F32, SEM_SOLVE_F64, SEM_SOLVE_MIXED, SEM_FACE_ALL,
+                   SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN, STATUS_NAMES)
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dtype_code(t):
+    if t.dtype == torch.float64:
+        return SEM_F64
+    if t.dtype == torch.float32:
+        return SEM_F32
+    raise SemError(1, f"unsupported dtype {t.dtype}")
+
+
+class Handle:
+    """Owns a sem_handle*; sizes cached at creation."""
+
+    def __init__(self, ptr, nel, N):
+        self.ptr = ptr
+        self.nel = tuple(nel)
+        n_local, n_global, n_ord, E = (ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(),
+                                       ctypes.c_int64())
+        check(_lib.load().sem_get_sizes(ptr, ctypes.byref(n_local), ctypes.byref(n_global),
+                                        ctypes.byref(n_ord), ctypes.byref(E)))
+        self.n_local = n_local.value
+        self.n_global = n_global.value
+        self.N = n_ord.value
+        self.E = E.value
+        self.shape = (self.E, N + 1, N + 1, N + 1)
+
+    def __del__(self):
+        try:
+            sem_destroy(self)
+        except Exception:
+            pass
+
+    def _vec(self, t, name, dtype=None):
+        if not isinstance(t, torch.Tensor):
+            raise SemError(1, f"{name} must be a torch tensor")
+        if not t.is_cuda:
+            raise SemError(1, f"{name} must be on the CUDA device")
+        if not t.is_contiguous():
+            raise SemError(1, f"{name} must be contiguous")
+        if t.numel() != self.n_local:
+            raise SemError(1, f"{name} has {t.numel()} values, expected n_L = {self.n_local}")
+        if dtype is not None and t.dtype != dtype:
+            raise SemError(1, f"{name} must be {dtype}")
+        return ctypes.c_void_p(t.data_ptr())
+
+
+def sem_setup(nel, N, x0=(0.0, 0.0, 0.0), length=(1.0, 1.0, 1.0), deform=0.0,
+              faces=SEM_FACE_ALL, precision=SEM_PREC_F64 | SEM_PREC_F32, xyz=None,
+              stream=None):
+    """Build the operator data for a nelx x nely x nelz box of order N."""
+    lib = _lib.load()
+    m = MeshDesc()
+    m.nelx, m.nely, m.nelz = (int(v) for v in nel)
+    for a in range(3):
+        m.x0[a] = float(x0[a])
+        m.len[a] = float(length[a])
+    m.deform_amp = float(deform)
+    m.dirichlet_faces = int(faces)
+    keep = None
+    if xyz is not None:
+        import numpy as np
+        keep = np.ascontiguousarray(xyz, dtype=np.float64)
+        m.xyz_gll = keep.ctypes.data
+    out = ctypes.c_void_p()
+    check(lib.sem_setup(ctypes.byref(m), int(N), int(precision), _stream(stream),
+                        ctypes.byref(out)))
+    return Handle(out, nel, N)
+
+
+def sem_destroy(h):
+    if h is not None and h.ptr:
+        ptr, h.ptr = h.ptr, None
+        check(_lib.load().sem_destroy(ptr))
+
+
+def sem_get_sizes(h):
+    return dict(n_local=h.n_local, n_global=h.n_global, N=h.N, E=h.E)
+
+
+def sem_get_field(h, which, dst, stream=None):
+    n = h.n_local * (6 if which == _lib.SEM_FIELD_G else 1)
+    if not dst.is_cuda or not dst.is_contiguous() or dst.numel() != n:
+        raise SemError(1, "sem_get_field: dst must be a contiguous CUDA tensor of the field size")
+    if which == _lib.SEM_FIELD_GID and dst.dtype != torch.int64:
+        raise SemError(1, "sem_get_field: gid needs an int64 tensor")
+    code = SEM_F64 if dst.dtype in (torch.float64, torch.int64) else _dtype_code(dst)
+    check(_lib.load().sem_get_field(h.ptr, int(which), ctypes.c_void_p(dst.data_ptr()), code,
+                                    _stream(stream)))
+    return dst
+
+
+def sem_ax(h, u, w, h1=1.0, h2=0.0, h1_field=None, stream=None):
+    """w = (h1 A_L + h2 B_L) u, element by element (no gather-scatter)."""
+    pu = h._vec(u, "u")
+    pw = h._vec(w, "w", u.dtype)
+    pf = h._vec(h1_field, "h1_field", u.dtype) if h1_field is not None else None
+    check(_lib.load().sem_ax(h.ptr, pu, pw, float(h1), float(h2), pf, _dtype_code(u),
+                             _stream(stream)))
+    return w
+
+
+def sem_dssum(h, w, apply_mask=True, stream=None):
+    """In place w <- QQ^T w (then the Dirichlet mask if apply_mask)."""
+    pw = h._vec(w, "w")
+    check(_lib.load().sem_dssum(h.ptr, pw, int(bool(apply_mask)), _dtype_code(w),
+                                _stream(stream)))
+    return w
+
+
+def sem_rhs(h, f, b, stream=None):
+    """b = mask o QQ^T (B f)."""
+    check(_lib.load().sem_rhs(h.ptr, h._vec(f, "f", torch.float64),
+                              h._vec(b, "b", torch.float64), _stream(stream)))
+    return b
+
+
+def sem_cg_solve(h, b, x, h1=1.0, h2=0.0, h1_field=None, tol=1e-8, maxit=20000,
+                 precision=SEM_SOLVE_F64, inner_tol=1e-4, max_outer=30, check_every=16,
+                 use_graph=True, x0=None, stream=None, raise_on_fail=True):
+    """Jacobi-PCG solve of mask o QQ^T H x = b; returns the info dict."""
+    lib = _lib.load()
+    o = SolveOpts()
+    lib.sem_solve_opts_default(ctypes.byref(o))
+    o.h1, o.h2 = float(h1), float(h2)
+    o.h1_field = (h._vec(h1_field, "h1_field", torch.float64).value
+                  if h1_field is not None else None)
+    o.tol, o.maxit = float(tol), int(maxit)
+    o.precision = int(precision)
+    o.inner_tol, o.max_outer = float(inner_tol), int(max_outer)
+    o.check_every, o.use_graph = int(check_every), int(bool(use_graph))
+    pb = h._vec(b, "b", torch.float64)
+    px = h._vec(x, "x", torch.float64)
+    if x0 is not None:
+        x.copy_(x0)
+        o.x0_is_zero = 0
+    o.stream = _stream(stream).value
+    info = SolveInfo()
+    st = lib.sem_cg_solve(h.ptr, pb, px, ctypes.byref(o), ctypes.byref(info))
+    res = dict(iters=info.iters, outer_iters=info.outer_iters, rel_res=info.rel_res,
+               status=STATUS_NAMES.get(info.status, info.status))
+    if st != 0 and (raise_on_fail or st not in (SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN)):
+        check(st)
+    return res
+
+
+def sem_helmholtz_grad(h, u, lam, g, stream=None):
+    """g = -(D^ lam)^T G (D^ u) at every local point (FP64)."""
+    check(_lib.load().sem_helmholtz_grad(h.ptr, h._vec(u, "u", torch.float64),
+                                         h._vec(lam, "lambda", torch.float64),
+                                         h._vec(g, "g", torch.float64), _stream(stream)))
+    return g
+
+
+def sem_apply_host(h, u_host, w_host, stream=None):
+    """w = mask o QQ^T A_L u with host tensors (copies inside the call)."""
+    for t, name in ((u_host, "u_host"), (w_host, "w_host")):
+        if t.is_cuda or not t.is_contiguous() or t.numel() != h.n_local:
+            raise SemError(1, f"{name} must be a contiguous host tensor of n_L values")
+    if u_host.dtype != w_host.dtype:
+        raise SemError(1, "u_host and w_host must share a dtype")
+    check(_lib.load().sem_apply_host(h.ptr, ctypes.c_void_p(u_host.data_ptr()),
+                                     ctypes.c_void_p(w_host.data_ptr()), _dtype_code(u_host),
+                                     _stream(stream)))
+    return w_host

@@ -1,0 +1,202 @@
+// Matrix-free element operator w_e = (h1 D^T G_e D + h2 B_e) u_e
+// (arXiv 2107.01243 §2, Eq. 9; the ax_t compute of Listing 1).
+//
+// Layout: one CTA works on EPB elements at a time; inside an element a
+// P x P thread plane owns the k-columns (i, j, 0..P-1).  The column of u
+// stays in registers (t-derivative and its transpose in registers), the
+// element is staged in shared memory for the r- and s-derivatives, rows are
+// padded to P+1 to spread the banks.  The 6 geometric factors of an element
+// are stored [6][P^3] so each factor streams coalesced along (i, j).
+#include "sem_internal.cuh"
+
+namespace sem {
+
+template <int P, class T>
+struct AxCfg {
+  static constexpr int P2 = P * P;
+  static constexpr int PP = P + 1;
+  static constexpr int VOL = P * P * PP;
+  static constexpr int smem_per_el = 2 * VOL * (int)sizeof(T);
+  static constexpr int by_threads = (256 / P2) < 1 ? 1 : (256 / P2);
+  static constexpr int by_smem = (40 * 1024) / smem_per_el < 1 ? 1 : (40 * 1024) / smem_per_el;
+  static constexpr int EPB0 = by_threads < by_smem ? by_threads : by_smem;
+  static constexpr int EPB = EPB0 > 32 ? 32 : EPB0;
+};
+
+template <int P, class T>
+__global__ void __launch_bounds__(AxCfg<P, T>::P2 * AxCfg<P, T>::EPB)
+ax_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ G,
+          const T* __restrict__ B, const T* __restrict__ h1f, T h1, T h2,
+          const T* __restrict__ Dg, int E, const CGState* __restrict__ st) {
+  using C = AxCfg<P, T>;
+  constexpr int P2 = C::P2, P3 = P2 * P, PP = C::PP, PL = P * PP, EPB = C::EPB;
+  if (st && st->done) return;
+  __shared__ T sD[P][PP];    // sD[a][b]  = D[a][b]
+  __shared__ T sDt[P][PP];   // sDt[a][b] = D[b][a]
+  __shared__ T s1[EPB][C::VOL];
+  __shared__ T s2[EPB][C::VOL];
+  const int tid = threadIdx.x;
+  const int el = threadIdx.y;
+  const int i = tid % P, j = tid / P;
+  for (int q = tid + el * P2; q < P2; q += P2 * EPB) {
+    T d = Dg[q];
+    sD[q / P][q % P] = d;
+    sDt[q % P][q / P] = d;
+  }
+  __syncthreads();
+  const bool helm = h2 != T(0);
+  for (int e0 = blockIdx.x * EPB; e0 < E; e0 += gridDim.x * EPB) {
+    const int e = e0 + el;
+    const bool act = e < E;
+    const size_t base = (size_t)(act ? e : 0) * P3 + tid;
+    T uc[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      uc[k] = act ? u[base + k * P2] : T(0);
+      s1[el][k * PL + j * PP + i] = uc[k];
+    }
+    __syncthreads();
+    T rr[P], rs[P], rt[P];
+    const T* g = G + (size_t)(act ? e : 0) * 6 * P3 + tid;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      T ur = T(0), us = T(0), ut = T(0);
+#pragma unroll
+      for (int l = 0; l < P; ++l) {
+        ur += sD[i][l] * s1[el][k * PL + j * PP + l];
+        us += sD[j][l] * s1[el][k * PL + l * PP + i];
+        ut += sD[k][l] * uc[l];
+      }
+      T g11 = g[0 * P3 + k * P2], g22 = g[1 * P3 + k * P2], g33 = g[2 * P3 + k * P2];
+      T g12 = g[3 * P3 + k * P2], g13 = g[4 * P3 + k * P2], g23 = g[5 * P3 + k * P2];
+      T c = h1f ? h1f[base + k * P2] : h1;
+      rr[k] = c * (g11 * ur + g12 * us + g13 * ut);
+      rs[k] = c * (g12 * ur + g22 * us + g23 * ut);
+      rt[k] = c * (g13 * ur + g23 * us + g33 * ut);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      s1[el][k * PL + j * PP + i] = rr[k];
+      s2[el][k * PL + j * PP + i] = rs[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      T acc = T(0);
+#pragma unroll
+      for (int l = 0; l < P; ++l) {
+        acc += sDt[i][l] * s1[el][k * PL + j * PP + l];
+        acc += sDt[j][l] * s2[el][k * PL + l * PP + i];
+        acc += sDt[k][l] * rt[l];
+      }
+      if (helm) acc += h2 * B[base + k * P2] * uc[k];
+      if (act) w[base + k * P2] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// diag(H^e) at every local point: the rr, ss, tt terms run along the line
+// through the point, the mixed terms only see the point (D_ii D_jj ...).
+template <class T>
+__global__ void local_diag_kernel(int P, int64_t nL, const T* __restrict__ G,
+                                  const T* __restrict__ B, const T* __restrict__ h1f, T h1,
+                                  T h2, const T* __restrict__ Dg, T* __restrict__ d) {
+  const int P2 = P * P, P3 = P2 * P;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nL;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t e = q / P3;
+    int r = (int)(q - e * P3);
+    int i = r % P, j = (r / P) % P, k = r / P2;
+    const T* g = G + e * 6 * P3;
+    const T* c = h1f ? h1f + e * P3 : nullptr;
+    auto cf = [&](int idx) { return c ? c[idx] : h1; };
+    T acc = T(0);
+    for (int l = 0; l < P; ++l) {
+      int a = k * P2 + j * P + l, b = k * P2 + l * P + i, t = l * P2 + j * P + i;
+      T dli = Dg[l * P + i], dlj = Dg[l * P + j], dlk = Dg[l * P + k];
+      acc += dli * dli * cf(a) * g[0 * P3 + a];
+      acc += dlj * dlj * cf(b) * g[1 * P3 + b];
+      acc += dlk * dlk * cf(t) * g[2 * P3 + t];
+    }
+    T dii = Dg[i * P + i], djj = Dg[j * P + j], dkk = Dg[k * P + k];
+    T cr = cf(r);
+    acc += T(2) * cr * (dii * djj * g[3 * P3 + r] + dii * dkk * g[4 * P3 + r] +
+                        djj * dkk * g[5 * P3 + r]);
+    if (h2 != T(0)) acc += h2 * B[q];
+    d[q] = acc;
+  }
+}
+
+template <int P, class T>
+static void launch_ax_p(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
+                        const T* h1f, const CGState* st, cudaStream_t s) {
+  using C = AxCfg<P, T>;
+  const int E = (int)h->E;
+  int blocks = (E + C::EPB - 1) / C::EPB;
+  dim3 block(C::P2, C::EPB);
+  ax_kernel<P, T><<<blocks, block, 0, s>>>(u, w, op.G.ptr, op.B.ptr, h1f, h1, h2, op.D.ptr, E,
+                                           st);
+  SEM_CHECK_LAUNCH();
+}
+
+template <class T>
+void launch_ax(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
+               const T* h1f, const CGState* st, cudaStream_t s) {
+  switch (h->P) {
+    case 2: launch_ax_p<2, T>(h, op, u, w, h1, h2, h1f, st, s); break;
+    case 3: launch_ax_p<3, T>(h, op, u, w, h1, h2, h1f, st, s); break;
+    case 4: launch_ax_p<4, T>(h, op, u, w, h1, h2, h1f, st, s); break;
+    case 5: launch_ax_p<5, T>(h, op, u, w, h1, h2, h1f, st, s); break;
+    case 6: launch_ax_p<6, T>(h, op, u, w, h1, h2, h1f, st, s); break;
+    case 7: launch_ax_p<7, T>(h, op, u, w, h1, h2, h1f, st, s); break;
+    case 8: launch_ax_p<8, T>(h, op, u, w, h1, h2, h1f, st, s); break;
+    case 9: launch_ax_p<9, T>(h, op, u, w, h1, h2, h1f, st, s); break;
+    case 10: launch_ax_p<10, T>(h, op, u, w, h1, h2, h1f, st, s); break;
+    case 11: launch_ax_p<11, T>(h, op, u, w, h1, h2, h1f, st, s); break;
+    default: throw Error(SEM_ERR_ARG, "launch_ax: unsupported order");
+  }
+}
+
+template <class T>
+void launch_local_diag(const sem_handle* h, const OpData<T>& op, T* d, T h1, T h2, const T* h1f,
+                       cudaStream_t s) {
+  int64_t nL = h->nL;
+  int blocks = (int)std::min<int64_t>((nL + 255) / 256, 16 * kNumSMs);
+  local_diag_kernel<T><<<blocks, 256, 0, s>>>(h->P, nL, op.G.ptr, op.B.ptr, h1f, h1, h2,
+                                              op.D.ptr, d);
+  SEM_CHECK_LAUNCH();
+}
+
+template void launch_ax<double>(const sem_handle*, const OpData<double>&, const double*, double*,
+                                double, double, const double*, const CGState*, cudaStream_t);
+template void launch_ax<float>(const sem_handle*, const OpData<float>&, const float*, float*,
+                               float, float, const float*, const CGState*, cudaStream_t);
+template void launch_local_diag<double>(const sem_handle*, const OpData<double>&, double*, double,
+                                        double, const double*, cudaStream_t);
+template void launch_local_diag<float>(const sem_handle*, const OpData<float>&, float*, float,
+                                       float, const float*, cudaStream_t);
+
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" sem_status sem_ax(sem_handle* h, const void* u_L, void* w_L, double h1, double h2,
+                             const void* h1_field, int dtype, void* stream) {
+  return guarded([&] {
+    SEM_REQUIRE(h && u_L && w_L, "sem_ax: null handle or vector");
+    SEM_REQUIRE(u_L != w_L, "sem_ax: u_L and w_L must be distinct");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == SEM_F64) {
+      launch_ax<double>(h, h->f64, (const double*)u_L, (double*)w_L, h1, h2,
+                        (const double*)h1_field, nullptr, s);
+    } else if (dtype == SEM_F32) {
+      if (!h->f32.G.ptr) throw Error(SEM_ERR_STATE, "sem_ax: handle keeps no FP32 geometry");
+      launch_ax<float>(h, h->f32, (const float*)u_L, (float*)w_L, (float)h1, (float)h2,
+                       (const float*)h1_field, nullptr, s);
+    } else {
+      throw Error(SEM_ERR_ARG, "sem_ax: bad dtype");
+    }
+  });
+}

@@ -1,0 +1,484 @@
+// Jacobi-preconditioned CG on the matrix-free operator and FP32-inner / FP64
+// iterative refinement (arXiv 2107.01243 §2 end: matrix-free Krylov
+// solvers; §4: PCG for the Helmholtz systems; Table 1: variable precision).
+//
+// Iteration (unique-dof inner products <a,b> = sum_L a b / mult):
+//   w = mask o QQ^T H_L p;  alpha = <r,z>/<p,w>;  x += alpha p;  r -= alpha w;
+//   stop if <r,r> <= tol^2 <b,b>;  z = dinv r;  beta = <r,z>_new/<r,z>;  p = z + beta p
+// alpha, beta and the stop flag live on the device (CGState); every kernel
+// returns at once when the flag is set, so a batch of iterations can be
+// captured in a CUDA graph and the host reads the state once per batch.
+#include <cmath>
+#include <algorithm>
+
+#include "sem_internal.cuh"
+#include "reduce.cuh"
+
+namespace sem {
+
+// ------------------------------------------------------------------ kernels
+template <class T>
+__global__ void __launch_bounds__(kRedThreads)
+k_init(int64_t n, const T* __restrict__ r, const T* __restrict__ dinv,
+       const float* __restrict__ imult, T* __restrict__ p, T* __restrict__ xzero,
+       CGState* __restrict__ st, double* __restrict__ partials, double tol, int maxit,
+       int bb_from_rr) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    T rq = r[q];
+    T z = dinv[q] * rq;
+    p[q] = z;
+    if (xzero) xzero[q] = T(0);
+    double im = (double)imult[q];
+    v[0] += (double)rq * (double)z * im;
+    v[1] += (double)rq * (double)rq * im;
+  }
+  double tot[2];
+  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    st->rz = tot[0];
+    st->rr = tot[1];
+    if (bb_from_rr) st->bb = tot[1];
+    st->tol2 = tol * tol * st->bb;
+    st->iter = 0;
+    st->status = SEM_OK;
+    st->maxit = maxit;
+    st->alpha = st->beta = 0.0;
+    st->done = (tot[1] <= st->tol2 || st->bb == 0.0 || maxit <= 0) ? 1 : 0;
+    if (st->done && !(tot[1] <= st->tol2 || st->bb == 0.0)) st->status = SEM_ERR_NOCONV;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kRedThreads)
+k_pw(int64_t n, const T* __restrict__ p, const T* __restrict__ w, const float* __restrict__ imult,
+     CGState* __restrict__ st, double* __restrict__ partials) {
+  if (st->done) return;
+  double v[1] = {0.0};
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    v[0] += (double)p[q] * (double)w[q] * (double)imult[q];
+  double tot[1];
+  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    st->pw = tot[0];
+    if (!(tot[0] > 0.0)) {
+      st->status = SEM_ERR_BREAKDOWN;
+      st->done = 1;
+    } else {
+      st->alpha = st->rz / tot[0];
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kRedThreads)
+k_update(int64_t n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+         const T* __restrict__ w, const T* __restrict__ dinv, const float* __restrict__ imult,
+         CGState* __restrict__ st, double* __restrict__ partials) {
+  if (st->done) return;
+  const T alpha = (T)st->alpha;
+  double v[2] = {0.0, 0.0};
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    x[q] += alpha * p[q];
+    T rq = r[q] - alpha * w[q];
+    r[q] = rq;
+    T z = dinv[q] * rq;
+    double im = (double)imult[q];
+    v[0] += (double)rq * (double)z * im;
+    v[1] += (double)rq * (double)rq * im;
+  }
+  double tot[2];
+  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    st->iter += 1;
+    st->rr = tot[1];
+    if (!(tot[1] == tot[1]) || !(tot[0] == tot[0])) {
+      st->status = SEM_ERR_BREAKDOWN;
+      st->done = 1;
+    } else if (tot[1] <= st->tol2) {
+      st->done = 1;
+    } else if (st->iter >= st->maxit) {
+      st->status = SEM_ERR_NOCONV;
+      st->done = 1;
+    } else {
+      st->beta = tot[0] / st->rz;
+      st->rz = tot[0];
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kRedThreads)
+k_pupd(int64_t n, T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ dinv,
+       const CGState* __restrict__ st) {
+  if (st->done) return;
+  const T beta = (T)st->beta;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    p[q] = dinv[q] * r[q] + beta * p[q];
+}
+
+// r64 = b - w64 (FP64 residual), optional FP32 copy, <r,r> into st->rr
+__global__ void __launch_bounds__(kRedThreads)
+k_resid(int64_t n, const double* __restrict__ b, const double* __restrict__ w,
+        double* __restrict__ r, float* __restrict__ r32, const float* __restrict__ imult,
+        CGState* __restrict__ st, double* __restrict__ partials) {
+  double v[1] = {0.0};
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    double rq = b[q] - w[q];
+    r[q] = rq;
+    if (r32) r32[q] = (float)rq;
+    v[0] += rq * rq * (double)imult[q];
+  }
+  double tot[1];
+  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) st->rr = tot[0];
+}
+
+// <a, a> into st->bb
+__global__ void __launch_bounds__(kRedThreads)
+k_norm_bb(int64_t n, const double* __restrict__ a, const float* __restrict__ imult,
+          CGState* __restrict__ st, double* __restrict__ partials) {
+  double v[1] = {0.0};
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    v[0] += a[q] * a[q] * (double)imult[q];
+  double tot[1];
+  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) st->bb = tot[0];
+}
+
+__global__ void k_addx(int64_t n, double* __restrict__ x, const float* __restrict__ d) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    x[q] += (double)d[q];
+}
+
+__global__ void k_dinv(int64_t n, const double* __restrict__ dg, const uint8_t* __restrict__ mask,
+                       double* __restrict__ dinv, float* __restrict__ dinv32) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    double v = mask[q] ? 1.0 / dg[q] : 0.0;
+    dinv[q] = v;
+    if (dinv32) dinv32[q] = (float)v;
+  }
+}
+
+__global__ void k_mul(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                      double* __restrict__ c) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    c[q] = a[q] * b[q];
+}
+
+__global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    b[q] = (float)a[q];
+}
+
+static int ew_grid(int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * kNumSMs));
+}
+
+// ------------------------------------------------------------------ host drivers
+struct Pinned {
+  CGState* p = nullptr;
+  Pinned() { SEM_CUDA(cudaMallocHost(&p, 2 * sizeof(CGState))); }
+  ~Pinned() { if (p) cudaFreeHost(p); }
+};
+
+static CGState read_state(const CGState* d, cudaStream_t s) {
+  static thread_local Pinned pin;
+  SEM_CUDA(cudaMemcpyAsync(pin.p, d, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  return *pin.p;
+}
+
+template <class T>
+struct PcgArgs {
+  const OpData<T>* op;
+  T* x;
+  T* r;
+  T* p;
+  T* w;
+  const T* dinv;
+  const T* h1f;
+  T h1, h2;
+  CGState* st;
+};
+
+template <class T>
+static void pcg_iterations(sem_handle* h, const PcgArgs<T>& a, int count, cudaStream_t s) {
+  const int64_t n = h->nL;
+  for (int c = 0; c < count; ++c) {
+    launch_ax<T>(h, *a.op, a.p, a.w, a.h1, a.h2, a.h1f, a.st, s);
+    launch_dssum<T>(h, a.w, true, a.st, s);
+    k_pw<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, a.p, a.w, h->imult.ptr, a.st, h->partials.ptr);
+    SEM_CHECK_LAUNCH();
+    k_update<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, a.x, a.r, a.p, a.w, a.dinv, h->imult.ptr,
+                                                   a.st, h->partials.ptr);
+    SEM_CHECK_LAUNCH();
+    k_pupd<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, a.p, a.r, a.dinv, a.st);
+    SEM_CHECK_LAUNCH();
+  }
+}
+
+// Runs iterations until the device state says done; returns the final state.
+template <class T>
+static CGState run_pcg(sem_handle* h, const PcgArgs<T>& a, const sem_solve_opts& o,
+                       cudaStream_t s) {
+  CGState hs = read_state(a.st, s);
+  if (hs.done) return hs;
+  const int batch = std::max(1, o.check_every);
+  cudaGraphExec_t exec = nullptr;
+  if (o.use_graph) {
+    cudaGraph_t graph = nullptr;
+    SEM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+      pcg_iterations<T>(h, a, batch, s);
+    } catch (...) {
+      cudaStreamEndCapture(s, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    SEM_CUDA(cudaStreamEndCapture(s, &graph));
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) throw Error(SEM_ERR_CUDA, std::string("cudaGraphInstantiate: ") +
+                                                        cudaGetErrorString(e));
+  }
+  try {
+    while (true) {
+      if (exec) SEM_CUDA(cudaGraphLaunch(exec, s));
+      else pcg_iterations<T>(h, a, batch, s);
+      hs = read_state(a.st, s);
+      if (hs.done) break;
+    }
+  } catch (...) {
+    if (exec) cudaGraphExecDestroy(exec);
+    throw;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  return hs;
+}
+
+static void ensure(DevBuf<double>& b, int64_t n) { if (b.n < (size_t)n) b.alloc(n); }
+static void ensure(DevBuf<float>& b, int64_t n) { if (b.n < (size_t)n) b.alloc(n); }
+
+// Jacobi inverse diagonal for (h1 | h1_field, h2): mask / QQ^T diag(H_L)
+static void ensure_dinv(sem_handle* h, double h1, double h2, const double* h1f, bool need32,
+                        cudaStream_t s) {
+  const int64_t n = h->nL;
+  bool same = h->dinv_valid && h->dinv_h1 == h1 && h->dinv_h2 == h2 && h->dinv_h1f == h1f &&
+              (!need32 || h->f32.dinv.ptr);
+  if (same && !h1f) return;      // a field may have changed in place: recompute
+  ensure(h->f64.dinv, n);
+  if (need32) ensure(h->f32.dinv, n);
+  ensure(h->tmp64, n);
+  launch_local_diag<double>(h, h->f64, h->tmp64.ptr, h1, h2, h1f, s);
+  launch_dssum<double>(h, h->tmp64.ptr, false, nullptr, s);
+  k_dinv<<<ew_grid(n), 256, 0, s>>>(n, h->tmp64.ptr, h->mask.ptr, h->f64.dinv.ptr,
+                                   need32 ? h->f32.dinv.ptr : nullptr);
+  SEM_CHECK_LAUNCH();
+  h->dinv_h1 = h1;
+  h->dinv_h2 = h2;
+  h->dinv_h1f = h1f;
+  h->dinv_valid = 1;
+}
+
+// H x -> w (FP64, masked, assembled), then r = b - w and <r,r> into st->rr
+static void residual64(sem_handle* h, const double* b, const double* x, double h1, double h2,
+                       const double* h1f, float* r32, CGState* st, cudaStream_t s) {
+  const int64_t n = h->nL;
+  launch_ax<double>(h, h->f64, x, h->w.ptr, h1, h2, h1f, nullptr, s);
+  launch_dssum<double>(h, h->w.ptr, true, nullptr, s);
+  k_resid<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, h->w.ptr, h->r.ptr, r32, h->imult.ptr, st,
+                                             h->partials.ptr);
+  SEM_CHECK_LAUNCH();
+}
+
+static void solve_fp64(sem_handle* h, const double* b, double* x, const sem_solve_opts& o,
+                       sem_solve_info& info, cudaStream_t s) {
+  const int64_t n = h->nL;
+  ensure(h->r, n); ensure(h->p, n); ensure(h->w, n);
+  ensure_dinv(h, o.h1, o.h2, o.h1_field, false, s);
+  CGState* st = h->state.ptr;
+  k_norm_bb<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, h->imult.ptr, st, h->partials.ptr);
+  SEM_CHECK_LAUNCH();
+  double* xz = nullptr;
+  if (o.x0_is_zero) {
+    SEM_CUDA(cudaMemcpyAsync(h->r.ptr, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    xz = x;
+  } else {
+    residual64(h, b, x, o.h1, o.h2, o.h1_field, nullptr, st, s);
+  }
+  k_init<double><<<kRedBlocks, kRedThreads, 0, s>>>(n, h->r.ptr, h->f64.dinv.ptr, h->imult.ptr,
+                                                    h->p.ptr, xz, st, h->partials.ptr, o.tol,
+                                                    o.maxit, 0);
+  SEM_CHECK_LAUNCH();
+  PcgArgs<double> a{&h->f64, x, h->r.ptr, h->p.ptr, h->w.ptr, h->f64.dinv.ptr, o.h1_field,
+                    o.h1, o.h2, st};
+  CGState fin = run_pcg<double>(h, a, o, s);
+  // true residual of the returned x
+  residual64(h, b, x, o.h1, o.h2, o.h1_field, nullptr, st, s);
+  CGState chk = read_state(st, s);
+  info.iters = fin.iter;
+  info.outer_iters = 0;
+  info.rel_res = chk.bb > 0 ? std::sqrt(chk.rr / chk.bb) : 0.0;
+  info.status = fin.status;
+}
+
+static void solve_mixed(sem_handle* h, const double* b, double* x, const sem_solve_opts& o,
+                        sem_solve_info& info, cudaStream_t s) {
+  const int64_t n = h->nL;
+  if (!h->f32.G.ptr) throw Error(SEM_ERR_STATE, "mixed solve needs FP32 geometry (SEM_PREC_F32)");
+  ensure(h->r, n); ensure(h->w, n);
+  ensure(h->r32, n); ensure(h->p32, n); ensure(h->w32, n); ensure(h->x32, n);
+  ensure_dinv(h, o.h1, o.h2, o.h1_field, true, s);
+  const float* h1f32 = nullptr;
+  if (o.h1_field) {
+    ensure(h->f32.h1f, n);
+    k_d2f<<<ew_grid(n), 256, 0, s>>>(n, o.h1_field, h->f32.h1f.ptr);
+    SEM_CHECK_LAUNCH();
+    h1f32 = h->f32.h1f.ptr;
+  }
+  CGState* st0 = h->state.ptr;
+  CGState* st1 = h->state.ptr + 1;
+  k_norm_bb<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, h->imult.ptr, st0, h->partials.ptr);
+  SEM_CHECK_LAUNCH();
+  if (o.x0_is_zero) SEM_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  int total = 0, outer = 0;
+  int status = SEM_ERR_NOCONV;
+  double rel = 0.0;
+  for (;;) {
+    residual64(h, b, x, o.h1, o.h2, o.h1_field, h->r32.ptr, st0, s);
+    CGState hs = read_state(st0, s);
+    rel = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+    if (!(rel == rel)) { status = SEM_ERR_BREAKDOWN; break; }
+    if (rel <= o.tol) { status = SEM_OK; break; }
+    if (outer >= o.max_outer || total >= o.maxit) { status = SEM_ERR_NOCONV; break; }
+    // inner FP32 PCG on H d = r32, d = 0 initially, relative tolerance inner_tol
+    k_init<float><<<kRedBlocks, kRedThreads, 0, s>>>(n, h->r32.ptr, h->f32.dinv.ptr,
+                                                     h->imult.ptr, h->p32.ptr, h->x32.ptr, st1,
+                                                     h->partials.ptr, o.inner_tol,
+                                                     o.maxit - total, 1);
+    SEM_CHECK_LAUNCH();
+    PcgArgs<float> a{&h->f32, h->x32.ptr, h->r32.ptr, h->p32.ptr, h->w32.ptr, h->f32.dinv.ptr,
+                     h1f32, (float)o.h1, (float)o.h2, st1};
+    CGState in = run_pcg<float>(h, a, o, s);
+    total += in.iter;
+    ++outer;
+    if (in.status == SEM_ERR_BREAKDOWN && in.iter == 0) { status = SEM_ERR_BREAKDOWN; break; }
+    k_addx<<<ew_grid(n), 256, 0, s>>>(n, x, h->x32.ptr);
+    SEM_CHECK_LAUNCH();
+  }
+  info.iters = total;
+  info.outer_iters = outer;
+  info.rel_res = rel;
+  info.status = status;
+}
+
+// Runs fn on the handle's private stream, ordered after the caller's stream.
+struct StreamScope {
+  cudaStream_t user, own;
+  cudaEvent_t ev;
+  StreamScope(cudaStream_t u) : user(u) {
+    SEM_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    SEM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    SEM_CUDA(cudaEventRecord(ev, user));
+    SEM_CUDA(cudaStreamWaitEvent(own, ev, 0));
+  }
+  ~StreamScope() {
+    cudaEventRecord(ev, own);
+    cudaStreamWaitEvent(user, ev, 0);
+    cudaStreamSynchronize(own);
+    cudaEventDestroy(ev);
+    cudaStreamDestroy(own);
+  }
+};
+
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" void sem_solve_opts_default(sem_solve_opts* o) {
+  if (!o) return;
+  o->h1 = 1.0;
+  o->h2 = 0.0;
+  o->h1_field = nullptr;
+  o->tol = 1e-8;
+  o->maxit = 20000;
+  o->precision = SEM_SOLVE_F64;
+  o->inner_tol = 1e-4;
+  o->max_outer = 30;
+  o->check_every = 16;
+  o->use_graph = 1;
+  o->x0_is_zero = 1;
+  o->stream = nullptr;
+}
+
+extern "C" sem_status sem_cg_solve(sem_handle* h, const double* b_L, double* x_L,
+                                   const sem_solve_opts* opts, sem_solve_info* info) {
+  sem_solve_info local{};
+  sem_status st = guarded([&] {
+    SEM_REQUIRE(h && b_L && x_L, "sem_cg_solve: null handle or vector");
+    sem_solve_opts o;
+    if (opts) o = *opts; else sem_solve_opts_default(&o);
+    SEM_REQUIRE(o.tol >= 0.0 && o.maxit >= 0, "sem_cg_solve: bad tol or maxit");
+    SEM_REQUIRE(o.precision == SEM_SOLVE_F64 || o.precision == SEM_SOLVE_MIXED,
+                "sem_cg_solve: bad precision");
+    SEM_REQUIRE(o.precision == SEM_SOLVE_F64 || (o.inner_tol > 0.0 && o.inner_tol < 1.0),
+                "sem_cg_solve: inner_tol must be in (0, 1)");
+    StreamScope sc((cudaStream_t)o.stream);
+    if (o.precision == SEM_SOLVE_F64) solve_fp64(h, b_L, x_L, o, local, sc.own);
+    else solve_mixed(h, b_L, x_L, o, local, sc.own);
+  });
+  if (info) *info = local;
+  if (st != SEM_OK) {
+    if (info) info->status = st;
+    return st;
+  }
+  if (local.status != SEM_OK) {
+    set_last_error(local.status == SEM_ERR_NOCONV ? "sem_cg_solve: no convergence within maxit"
+                                                  : "sem_cg_solve: breakdown (<p,Hp> <= 0 or NaN)");
+    return (sem_status)local.status;
+  }
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_rhs(sem_handle* h, const double* f_L, double* b_L, void* stream) {
+  return guarded([&] {
+    SEM_REQUIRE(h && f_L && b_L, "sem_rhs: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = h->nL;
+    k_mul<<<ew_grid(n), 256, 0, s>>>(n, h->f64.B.ptr, f_L, b_L);
+    SEM_CHECK_LAUNCH();
+    launch_dssum<double>(h, b_L, true, nullptr, s);
+  });
+}
+
+extern "C" sem_status sem_apply_host(sem_handle* h, const void* u_host, void* w_host, int dtype,
+                                     void* stream) {
+  return guarded([&] {
+    SEM_REQUIRE(h && u_host && w_host, "sem_apply_host: null argument");
+    SEM_REQUIRE(dtype == SEM_F64 || dtype == SEM_F32, "sem_apply_host: bad dtype");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = h->nL;
+    ensure(h->stage_in, n);
+    ensure(h->stage_out, n);
+    const size_t bytes = n * (dtype == SEM_F64 ? sizeof(double) : sizeof(float));
+    SEM_CUDA(cudaMemcpyAsync(h->stage_in.ptr, u_host, bytes, cudaMemcpyHostToDevice, s));
+    if (dtype == SEM_F64) {
+      launch_ax<double>(h, h->f64, h->stage_in.ptr, h->stage_out.ptr, 1.0, 0.0, nullptr, nullptr, s);
+      launch_dssum<double>(h, h->stage_out.ptr, true, nullptr, s);
+    } else {
+      if (!h->f32.G.ptr) throw Error(SEM_ERR_STATE, "sem_apply_host: no FP32 geometry");
+      float* in = (float*)h->stage_in.ptr;
+      float* out = (float*)h->stage_out.ptr;
+      launch_ax<float>(h, h->f32, in, out, 1.0f, 0.0f, nullptr, nullptr, s);
+      launch_dssum<float>(h, out, true, nullptr, s);
+    }
+    SEM_CUDA(cudaMemcpyAsync(w_host, h->stage_out.ptr, bytes, cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+  });
+}

@@ -1,0 +1,172 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+#include <algorithm>
+#include <cmath>
+#include <stdexcept>
+
+#include "../../include/sem.h"
+
+namespace sem {
+
+constexpr int kMaxN = 10;            // highest supported polynomial order
+constexpr int kMaxP = kMaxN + 1;
+constexpr int kNumSMs = 152;         // GB300: 2 dies x 76 SMs
+constexpr int kRedBlocks = 4 * kNumSMs;   // blocks of every reduction kernel
+constexpr int kRedThreads = 256;
+
+// ------------------------------------------------------------------ errors
+struct Error : std::runtime_error {
+  sem_status code;
+  Error(sem_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void set_last_error(const std::string& msg);
+
+#define SEM_CUDA(call)                                                          \
+  do {                                                                          \
+    cudaError_t e__ = (call);                                                   \
+    if (e__ != cudaSuccess)                                                     \
+      throw ::sem::Error(e__ == cudaErrorMemoryAllocation ? SEM_ERR_OOM         \
+                                                         : SEM_ERR_CUDA,       \
+                         std::string(#call) + ": " + cudaGetErrorString(e__));  \
+  } while (0)
+
+#define SEM_CHECK_LAUNCH() SEM_CUDA(cudaGetLastError())
+
+#define SEM_REQUIRE(cond, msg)                                                  \
+  do {                                                                          \
+    if (!(cond)) throw ::sem::Error(SEM_ERR_ARG, msg);                          \
+  } while (0)
+
+// Run a body, translating exceptions into a status + thread-local message.
+template <class F>
+sem_status guarded(F&& f) {
+  try {
+    f();
+    set_last_error("");
+    return SEM_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return SEM_ERR_CUDA;
+  }
+}
+
+// ------------------------------------------------------------------ device buffers
+template <class T>
+struct DevBuf {
+  T* ptr = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) return;
+    SEM_CUDA(cudaMalloc(&ptr, count * sizeof(T)));
+    n = count;
+  }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    n = 0;
+  }
+  void upload(const T* h, size_t count, cudaStream_t s) {
+    SEM_CUDA(cudaMemcpyAsync(ptr, h, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+};
+
+// CG scalars kept on the device so that iterations need no host round trip.
+struct CGState {
+  double rz;        // <r, z> of the current residual
+  double pw;        // <p, H p>
+  double rr;        // <r, r>
+  double bb;        // <b, b>
+  double alpha, beta;
+  double tol2;      // (tol)^2 * <b,b>: convergence threshold on <r,r>
+  int iter;         // completed iterations
+  int done;         // 1 once converged or failed
+  int status;       // SEM_OK / SEM_ERR_BREAKDOWN
+  int maxit;
+  unsigned int counter;   // last-block-done ticket for the reductions
+  int pad;
+};
+
+// Precision-specific operator data (geometry in one float type).
+template <class T>
+struct OpData {
+  DevBuf<T> G;      // [E][6][p^3]
+  DevBuf<T> B;      // [E][p^3]
+  DevBuf<T> D;      // [p][p] row-major D[i][l] = l_l'(xi_i)
+  DevBuf<T> dinv;   // Jacobi inverse diagonal (mask folded in)
+  DevBuf<T> h1f;    // per-point h1 in this precision (mixed solves)
+};
+
+}  // namespace sem
+
+struct sem_handle {
+  int N = 0, P = 0, P3 = 0;
+  int nelx = 0, nely = 0, nelz = 0;
+  int64_t E = 0, nL = 0, nG = 0;
+  int prec_flags = 0;
+  int faces = 0;
+  std::vector<double> xi, wq, Dh;          // host GLL nodes, weights, D
+
+  sem::DevBuf<double> coords;               // [3][nL]
+  sem::OpData<double> f64;
+  sem::OpData<float> f32;
+  sem::DevBuf<float> imult;                 // 1 / multiplicity (exact)
+  sem::DevBuf<uint8_t> mask;                // 0 on Dirichlet points
+  sem::DevBuf<int64_t> gid;                 // global numbers
+
+  // gather-scatter: segments of >= 2 local copies of one global point,
+  // unmasked ones first; masked local points listed separately
+  int64_t nseg_all = 0, nseg_free = 0, nmasked = 0;
+  sem::DevBuf<int> seg_ptr;                 // [nseg_all + 1]
+  sem::DevBuf<int> seg_idx;                 // local indices
+  sem::DevBuf<int> masked_idx;              // local indices with mask 0
+
+  // solver scratch (allocated on first use)
+  sem::DevBuf<double> r, p, w, x64, tmp64;
+  sem::DevBuf<float> r32, p32, w32, x32;
+  sem::DevBuf<double> partials;             // reduction partials
+  sem::DevBuf<sem::CGState> state;          // [2]: outer/FP64 and inner/FP32
+  // host staging for sem_apply_host
+  sem::DevBuf<double> stage_in, stage_out;
+  double dinv_h1 = NAN, dinv_h2 = NAN;
+  const void* dinv_h1f = nullptr;
+  int dinv_valid = 0;
+};
+
+namespace sem {
+
+// ---- setup.cu
+void gll_host(int N, std::vector<double>& xi, std::vector<double>& w, std::vector<double>& D);
+
+// ---- ax.cu: w = (h1 A + h2 B) u (no dssum).  state may be null.
+template <class T>
+void launch_ax(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
+               const T* h1f, const CGState* state, cudaStream_t s);
+// diag(H_L) at every local point
+template <class T>
+void launch_local_diag(const sem_handle* h, const OpData<T>& op, T* d, T h1, T h2,
+                       const T* h1f, cudaStream_t s);
+
+// ---- dssum.cu
+template <class T>
+void launch_dssum(const sem_handle* h, T* w, bool apply_mask, const CGState* state,
+                  cudaStream_t s);
+
+// ---- grad.cu
+void launch_grad(const sem_handle* h, const double* u, const double* lam, double* g,
+                 cudaStream_t s);
+
+}  // namespace sem

@@ -1,0 +1,157 @@
+"""GPU parity: the CUDA path against the oracle, element by element, through
+the C ABI, on meshes that span several CTAs and end in a ragged tail."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2107_01243_gb300 as sem
+import seeded_inputs as si
+from tests.helpers import OracleProblem, rel_inf, TWO_PI
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+TOL64 = 1e-12          # FP64 Ax / dssum / geometry: relative to the max norm
+TOL32 = 2e-5           # FP32 Ax against the FP64 oracle (24-bit significand, ~3P-term sums)
+
+
+def to_dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+def to_np(t):
+    return t.detach().double().cpu().numpy()
+
+
+def make(nel, N, deform=0.1, length=(TWO_PI,) * 3, faces=63):
+    h = sem.sem_setup(nel, N, length=length, deform=deform, faces=faces)
+    o = OracleProblem(nel, N, length=length, deform=deform, faces=faces)
+    return h, o
+
+
+CASES = [((5, 3, 3), 7), ((3, 2, 1), 2), ((2, 3, 2), 5), ((3, 3, 1), 9), ((1, 2, 2), 10),
+         ((4, 1, 1), 1), ((2, 2, 2), 4), ((1, 1, 1), 7)]
+
+
+@pytest.mark.parametrize("nel,N", CASES)
+def test_geometry(nel, N):
+    h, o = make(nel, N)
+    n = h.n_local
+    for which, ref in ((sem.SEM_FIELD_X, o.x), (sem.SEM_FIELD_Y, o.y), (sem.SEM_FIELD_Z, o.z),
+                       (sem.SEM_FIELD_B, o.B)):
+        t = torch.empty(n, dtype=torch.float64, device=DEV)
+        sem.sem_get_field(h, which, t)
+        assert rel_inf(to_np(t).reshape(o.shape), ref) < TOL64
+    g = torch.empty(6 * n, dtype=torch.float64, device=DEV)
+    sem.sem_get_field(h, sem.SEM_FIELD_G, g)
+    gg = to_np(g).reshape(o.shape[0], 6, *o.shape[1:]).transpose(1, 0, 2, 3, 4)
+    assert rel_inf(gg, o.G) < TOL64
+    gid = torch.empty(n, dtype=torch.int64, device=DEV)
+    sem.sem_get_field(h, sem.SEM_FIELD_GID, gid)
+    np.testing.assert_array_equal(gid.cpu().numpy().reshape(o.shape), o.gid)
+    m = torch.empty(n, dtype=torch.float64, device=DEV)
+    sem.sem_get_field(h, sem.SEM_FIELD_MULT, m)
+    np.testing.assert_array_equal(to_np(m).reshape(o.shape), o.mult)
+    sem.sem_get_field(h, sem.SEM_FIELD_MASK, m)
+    np.testing.assert_array_equal(to_np(m).reshape(o.shape), o.mask)
+
+
+@pytest.mark.parametrize("nel,N", CASES)
+@pytest.mark.parametrize("h1,h2", [(1.0, 0.0), (0.8, 2.5)])
+def test_ax_fp64(nel, N, h1, h2):
+    h, o = make(nel, N)
+    u = si.uniform(o.shape, 42)
+    w = torch.empty(h.n_local, dtype=torch.float64, device=DEV)
+    sem.sem_ax(h, to_dev(u).view(-1), w, h1, h2)
+    torch.cuda.synchronize()
+    assert rel_inf(to_np(w).reshape(o.shape), o.ax(u, h1, h2)) < TOL64
+
+
+@pytest.mark.parametrize("nel,N", [((5, 3, 3), 7), ((2, 3, 2), 5), ((3, 3, 1), 9)])
+def test_ax_variable_coefficient(nel, N):
+    h, o = make(nel, N)
+    u = si.uniform(o.shape, 7)
+    h1 = si.smooth_coefficient(o.x, o.y, o.z, 77)
+    for dtype, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
+        w = torch.empty(h.n_local, dtype=dtype, device=DEV)
+        sem.sem_ax(h, to_dev(u, dtype).view(-1), w, 0.0, 1.0, h1_field=to_dev(h1, dtype).view(-1))
+        assert rel_inf(to_np(w).reshape(o.shape), o.ax(u, 0.0, 1.0, h1)) < tol
+
+
+@pytest.mark.parametrize("nel,N", CASES)
+def test_ax_fp32(nel, N):
+    h, o = make(nel, N)
+    u = si.uniform(o.shape, 43)
+    w = torch.empty(h.n_local, dtype=torch.float32, device=DEV)
+    sem.sem_ax(h, to_dev(u, torch.float32).view(-1), w)
+    # the oracle sees the same FP32-rounded input
+    ref = o.ax(u.astype(np.float32).astype(np.float64))
+    assert rel_inf(to_np(w).reshape(o.shape), ref) < TOL32
+
+
+@pytest.mark.parametrize("nel,N", CASES)
+@pytest.mark.parametrize("apply_mask", [False, True])
+def test_dssum_fp64_bitexact(nel, N, apply_mask):
+    from oracle import operator
+    h, o = make(nel, N)
+    w0 = si.uniform(o.shape, 44)
+    w = to_dev(w0).view(-1).clone()
+    sem.sem_dssum(h, w, apply_mask=apply_mask)
+    ref = operator.dssum(w0, o.gid)
+    if apply_mask:
+        ref = operator.apply_dirichlet(ref, o.mask)
+    # same summation order (increasing local index) on both sides: bitwise equal
+    np.testing.assert_array_equal(to_np(w).reshape(o.shape), ref)
+
+
+@pytest.mark.parametrize("nel,N", [((5, 3, 3), 7), ((3, 3, 1), 9)])
+def test_dssum_fp32(nel, N):
+    from oracle import operator
+    h, o = make(nel, N)
+    w0 = si.uniform(o.shape, 45).astype(np.float32)
+    w = to_dev(w0, torch.float32).view(-1).clone()
+    sem.sem_dssum(h, w, apply_mask=True)
+    ref = operator.apply_dirichlet(operator.dssum(w0.astype(np.float64), o.gid), o.mask)
+    assert rel_inf(to_np(w).reshape(o.shape), ref) < 1e-6
+
+
+def test_dirichlet_faces_subset():
+    from oracle import operator
+    faces = 1 | 8 | 32
+    h, o = make((3, 2, 2), 3, faces=faces)
+    w0 = si.uniform(o.shape, 46)
+    w = to_dev(w0).view(-1).clone()
+    sem.sem_dssum(h, w, apply_mask=True)
+    ref = operator.apply_dirichlet(operator.dssum(w0, o.gid), o.mask)
+    np.testing.assert_array_equal(to_np(w).reshape(o.shape), ref)
+
+
+@pytest.mark.parametrize("nel,N", [((5, 3, 3), 7), ((2, 2, 3), 4)])
+def test_rhs(nel, N):
+    h, o = make(nel, N)
+    f = si.eval_fourier(si.fourier_modes(3), o.x, o.y, o.z)
+    b = torch.empty(h.n_local, dtype=torch.float64, device=DEV)
+    sem.sem_rhs(h, to_dev(f).view(-1), b)
+    assert rel_inf(to_np(b).reshape(o.shape), o.rhs(f)) < TOL64
+
+
+@pytest.mark.parametrize("nel,N", [((5, 3, 3), 7), ((3, 3, 1), 9), ((2, 2, 3), 3)])
+def test_gradient_kernel(nel, N):
+    from oracle import adjoint
+    h, o = make(nel, N)
+    u = si.uniform(o.shape, 47)
+    lam = si.uniform(o.shape, 48)
+    g = torch.empty(h.n_local, dtype=torch.float64, device=DEV)
+    sem.sem_helmholtz_grad(h, to_dev(u).view(-1), to_dev(lam).view(-1), g)
+    assert rel_inf(to_np(g).reshape(o.shape), adjoint.grad_h1(u, lam, o.G, o.D)) < TOL64
+
+
+def test_apply_host_matches_device():
+    h, o = make((5, 3, 3), 7)
+    u = si.uniform(o.shape, 49)
+    for dtype, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
+        uh = torch.from_numpy(u.astype(np.float64)).to(dtype).view(-1).pin_memory()
+        wh = torch.empty_like(uh).pin_memory()
+        sem.sem_apply_host(h, uh, wh)
+        ref = o.matvec(uh.double().numpy().reshape(o.shape))
+        assert rel_inf(wh.double().numpy().reshape(o.shape), ref) < tol
