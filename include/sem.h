@@ -191,6 +191,17 @@ sem_status sem_helmholtz_grad(sem_handle* h, const double* u_L, const double* la
                               double* g_L, void* stream);
 
 /*
+ * sem_dot -- *out = sum_L a b / mult: the inner product on the unique degrees
+ * of freedom (every global point counted once for continuous a, b), i.e. the
+ * dot product of the Krylov solvers (§2 end; on one device it replaces the
+ * MPI_Allreduce of every CG dot, §8 Eq. 14).  a, b: FP64 device L-vectors;
+ * out: one device double.  Accumulated in FP64 with a fixed reduction order
+ * (bitwise reproducible).  Uses the handle's reduction scratch: do not
+ * overlap it with other calls on the same handle.
+ */
+sem_status sem_dot(sem_handle* h, const double* a, const double* b, double* out, void* stream);
+
+/*
  * sem_apply_host -- w = mask o QQ^T A_L u with HOST buffers: copies u_host
  * (n_L values of dtype) to the device, applies Ax and dssum with the mask,
  * copies the result to w_host and synchronises the stream.  Pinned host

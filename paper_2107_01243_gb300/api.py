@@ -185,3 +185,13 @@ def sem_apply_host(h, u_host, w_host, stream=None):
                                      ctypes.c_void_p(w_host.data_ptr()), _dtype_code(u_host),
                                      _stream(stream)))
     return w_host
+
+
+def sem_dot(h, a, b, out, stream=None):
+    """out[0] = sum_L a b / mult (unique-dof inner product), FP64, on the device."""
+    if not out.is_cuda or out.dtype != torch.float64 or out.numel() < 1:
+        raise SemError(1, "sem_dot: out must be a CUDA float64 tensor")
+    check(_lib.load().sem_dot(h.ptr, h._vec(a, "a", torch.float64), h._vec(b, "b", torch.float64),
+                              ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+

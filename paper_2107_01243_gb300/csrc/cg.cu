@@ -147,6 +147,19 @@ k_norm_bb(int64_t n, const double* __restrict__ a, const float* __restrict__ imu
   if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) st->bb = tot[0];
 }
 
+// sum a b / mult into *out (fixed grid, fixed order)
+__global__ void __launch_bounds__(kRedThreads)
+k_wdot(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+       const float* __restrict__ imult, double* __restrict__ out, double* __restrict__ partials,
+       unsigned int* __restrict__ counter) {
+  double v[1] = {0.0};
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    v[0] += a[q] * b[q] * (double)imult[q];
+  double tot[1];
+  if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) *out = tot[0];
+}
+
 __global__ void k_addx(int64_t n, double* __restrict__ x, const float* __restrict__ d) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x)
@@ -454,6 +467,18 @@ extern "C" sem_status sem_rhs(sem_handle* h, const double* f_L, double* b_L, voi
     k_mul<<<ew_grid(n), 256, 0, s>>>(n, h->f64.B.ptr, f_L, b_L);
     SEM_CHECK_LAUNCH();
     launch_dssum<double>(h, b_L, true, nullptr, s);
+  });
+}
+
+extern "C" sem_status sem_dot(sem_handle* h, const double* a, const double* b, double* out,
+                              void* stream) {
+  return guarded([&] {
+    SEM_REQUIRE(h && a && b && out, "sem_dot: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    k_wdot<<<kRedBlocks, kRedThreads, 0, s>>>(h->nL, a, b, h->imult.ptr, out,
+                                              h->partials.ptr + 2 * kRedBlocks,
+                                              &h->state.ptr[2].counter);
+    SEM_CHECK_LAUNCH();
   });
 }
 

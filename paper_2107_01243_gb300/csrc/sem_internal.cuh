@@ -137,8 +137,8 @@ struct sem_handle {
   // solver scratch (allocated on first use)
   sem::DevBuf<double> r, p, w, x64, tmp64;
   sem::DevBuf<float> r32, p32, w32, x32;
-  sem::DevBuf<double> partials;             // reduction partials
-  sem::DevBuf<sem::CGState> state;          // [2]: outer/FP64 and inner/FP32
+  sem::DevBuf<double> partials;             // reduction partials: [0,2B) solves, [2B,3B) sem_dot
+  sem::DevBuf<sem::CGState> state;          // [3]: outer/FP64, inner/FP32, sem_dot ticket
   // host staging for sem_apply_host
   sem::DevBuf<double> stage_in, stage_out;
   double dinv_h1 = NAN, dinv_h2 = NAN;

@@ -349,8 +349,8 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
     SEM_CUDA(cudaMemcpyAsync(&hbad, bad.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     SEM_CUDA(cudaStreamSynchronize(s));
     SEM_REQUIRE(!hbad, "sem_setup: element map has detJ <= 0 at some GLL point");
-    h->state.alloc(2);
-    SEM_CUDA(cudaMemsetAsync(h->state.ptr, 0, 2 * sizeof(CGState), s));
+    h->state.alloc(3);
+    SEM_CUDA(cudaMemsetAsync(h->state.ptr, 0, 3 * sizeof(CGState), s));
     h->partials.alloc(4 * kRedBlocks);
     SEM_CUDA(cudaStreamSynchronize(s));
     *out = h.release();

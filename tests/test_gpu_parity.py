@@ -155,3 +155,24 @@ def test_apply_host_matches_device():
         sem.sem_apply_host(h, uh, wh)
         ref = o.matvec(uh.double().numpy().reshape(o.shape))
         assert rel_inf(wh.double().numpy().reshape(o.shape), ref) < tol
+
+
+@pytest.mark.parametrize("nel,N", [((5, 3, 3), 7), ((3, 3, 1), 9), ((1, 1, 1), 2)])
+def test_dot_unique_dof(nel, N):
+    from oracle import operator
+    h, o = make(nel, N)
+    a = si.uniform(o.shape, 50)
+    b = si.uniform(o.shape, 51)
+    out = torch.empty(1, dtype=torch.float64, device=DEV)
+    sem.sem_dot(h, to_dev(a).view(-1), to_dev(b).view(-1), out)
+    ref = operator.weighted_dot(a, b, o.mult)
+    assert abs(float(out) - ref) <= 1e-13 * np.sum(np.abs(a * b / o.mult))
+    # continuous fields: equals the plain sum over unique points
+    ga = si.uniform(int(o.gid.max()) + 1, 52)
+    gb = si.uniform(int(o.gid.max()) + 1, 53)
+    sem.sem_dot(h, to_dev(ga[o.gid]).view(-1), to_dev(gb[o.gid]).view(-1), out)
+    assert abs(float(out) - float(np.dot(ga, gb))) <= 1e-13 * float(np.sum(np.abs(ga * gb)))
+    # reproducible bit for bit
+    first = float(out)
+    sem.sem_dot(h, to_dev(ga[o.gid]).view(-1), to_dev(gb[o.gid]).view(-1), out)
+    assert float(out) == first
