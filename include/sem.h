@@ -202,6 +202,21 @@ sem_status sem_helmholtz_grad(sem_handle* h, const double* u_L, const double* la
 sem_status sem_dot(sem_handle* h, const double* a, const double* b, double* out, void* stream);
 
 /*
+ * sem_dot_noalloc -- the same inner product as sem_dot, for callers that must
+ * not allocate device memory at the call site (for example while a stream is
+ * being captured into a CUDA graph, or under a device-memory budget fixed up
+ * front).  The paper has no counterpart; this is a library convenience.
+ * Allocates nothing: the partial sums live in a static device array of the
+ * library (128 KiB, held by every GPU that loads the library until exit), so
+ * n_L may be at most 67,108,864 local points (SEM_ERR_ARG beyond that).  All
+ * calls share the array; calls whose kernels overlap on the GPU race, so
+ * order them on one stream.  The first call on each device looks up the
+ * array's address; make it before any stream capture.
+ */
+sem_status sem_dot_noalloc(sem_handle* h, const double* a, const double* b, double* out,
+                           void* stream);
+
+/*
  * sem_apply_host -- w = mask o QQ^T A_L u with HOST buffers: copies u_host
  * (n_L values of dtype) to the device, applies Ax and dssum with the mask,
  * copies the result to w_host and synchronises the stream.  Pinned host

@@ -195,3 +195,13 @@ def sem_dot(h, a, b, out, stream=None):
                               ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
 
+
+def sem_dot_noalloc(h, a, b, out, stream=None):
+    """Same as sem_dot, but the library allocates nothing for the call (its
+    scratch is a static device array); for callers that cannot allocate."""
+    if not out.is_cuda or out.dtype != torch.float64 or out.numel() < 1:
+        raise SemError(1, "sem_dot_noalloc: out must be a CUDA float64 tensor")
+    check(_lib.load().sem_dot_noalloc(h.ptr, h._vec(a, "a", torch.float64),
+                                      h._vec(b, "b", torch.float64),
+                                      ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out

@@ -1,0 +1,96 @@
+// sem_dot_noalloc: the unique-dof inner product with no device allocation.
+//
+// Who needs it: callers that cannot call cudaMalloc where they need a dot
+// product -- code that records work into a CUDA graph while a stream is being
+// captured (an allocation there is not captured and breaks the capture), hosts
+// that must not block on the allocator inside a latency-critical loop, and
+// applications that hand the library a fixed device-memory budget up front
+// and forbid allocations afterwards.  sem_dot keeps its partial sums in the
+// handle's scratch; this variant keeps them in one file-scope device array
+// that is part of the loaded library instead, so a call allocates nothing.
+//
+// Limits and sharing:
+//  * The array holds kNoAllocMaxBlocks partial sums (128 KiB) plus one
+//    completion ticket; every block sums kNoAllocPointsPerBlock points, so
+//    n_L may be at most kNoAllocMaxPoints = 67,108,864 local points.
+//  * Every GPU that loads the library holds the array until the process exits.
+//  * All calls on a device share the array and it keeps the last call's
+//    contents; each call clears the ticket before its kernel runs.  Calls
+//    whose kernels overlap on the GPU (different streams, no ordering) race
+//    on the array and give wrong results: order them on one stream.
+//  * The first call on each device looks up the array's device address with
+//    cudaGetSymbolAddress (with that device current) and caches it; make that
+//    first call before any stream capture.
+#include <mutex>
+
+#include "sem_internal.cuh"
+#include "reduce.cuh"
+
+namespace sem {
+
+constexpr int kNoAllocThreads = 256;
+constexpr int kNoAllocPointsPerBlock = 4096;                // 16 points per thread
+constexpr int kNoAllocMaxBlocks = 16384;
+constexpr int64_t kNoAllocMaxPoints = (int64_t)kNoAllocMaxBlocks * kNoAllocPointsPerBlock;
+constexpr int kNoAllocMaxDevices = 64;
+
+// [0, kNoAllocMaxBlocks): block partial sums; word kNoAllocMaxBlocks: ticket
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxBlocks + 32];
+
+// One block per kNoAllocPointsPerBlock consecutive points (coalesced strides of
+// the block size), then the shared grid reduction: fixed order, reproducible.
+__global__ void __launch_bounds__(kNoAllocThreads)
+k_wdot_static(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+              const float* __restrict__ imult, double* __restrict__ out,
+              double* __restrict__ scratch) {
+  const int64_t base = (int64_t)blockIdx.x * kNoAllocPointsPerBlock;
+  double v[1] = {0.0};
+#pragma unroll 4
+  for (int m = threadIdx.x; m < kNoAllocPointsPerBlock; m += kNoAllocThreads) {
+    const int64_t q = base + m;
+    if (q < n) v[0] += a[q] * b[q] * (double)imult[q];
+  }
+  unsigned int* ticket = reinterpret_cast<unsigned int*>(scratch + kNoAllocMaxBlocks);
+  double tot[1];
+  if (grid_sum<1>(v, scratch, ticket, tot) && threadIdx.x == 0) *out = tot[0];
+}
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per device.
+static double* noalloc_scratch() {
+  int dev = -1;
+  SEM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    throw Error(SEM_ERR_STATE, "sem_dot_noalloc: device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    SEM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  return g_noalloc_addr[dev];
+}
+
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" sem_status sem_dot_noalloc(sem_handle* h, const double* a, const double* b,
+                                      double* out, void* stream) {
+  return guarded([&] {
+    SEM_REQUIRE(h && a && b && out, "sem_dot_noalloc: null argument");
+    if (h->nL > kNoAllocMaxPoints)
+      throw Error(SEM_ERR_ARG, "sem_dot_noalloc: n_L = " + std::to_string(h->nL) +
+                                   " local points exceeds the maximum of " +
+                                   std::to_string(kNoAllocMaxPoints) + "; use sem_dot");
+    double* scratch = noalloc_scratch();
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = (int)((h->nL + kNoAllocPointsPerBlock - 1) / kNoAllocPointsPerBlock);
+    SEM_CUDA(cudaMemsetAsync(scratch + kNoAllocMaxBlocks, 0, sizeof(double), s));
+    k_wdot_static<<<blocks < 1 ? 1 : blocks, kNoAllocThreads, 0, s>>>(h->nL, a, b,
+                                                                       h->imult.ptr, out, scratch);
+    SEM_CHECK_LAUNCH();
+  });
+}
