@@ -108,6 +108,24 @@ sem_status sem_destroy(sem_handle* h);
 /* Message of the last failed call on this host thread ("" if none). */
 const char* sem_last_error(void);
 
+/*
+ * sem_sync -- synchronise the stream, then report a device-side failure
+ * recorded by an earlier asynchronous call on this handle: SEM_ERR_TIMEOUT if
+ * a bounded wait inside a kernel gave up (the kernel then returned early and
+ * its output is incomplete).  Clears the record.
+ */
+sem_status sem_sync(sem_handle* h, void* stream);
+
+/*
+ * sem_selftest_timeout -- diagnostic: launches the bulk-copy Ax kernel with
+ * an mbarrier that expects 16 bytes more than its copies deliver, so its
+ * wait can never complete, with the given limit (0 < timeout_ms <= 2000).
+ * Returns SEM_ERR_TIMEOUT when the kernel gave up, recorded the failure and
+ * returned (the GPU context stays usable); SEM_OK would mean the wait was
+ * not bounded.  Needs FP32 geometry and even N+1.
+ */
+sem_status sem_selftest_timeout(sem_handle* h, double timeout_ms, void* stream);
+
 /* Sizes: local points n_L, unique global points, order N, elements E. */
 sem_status sem_get_sizes(const sem_handle* h, int64_t* n_local, int64_t* n_global,
                          int* N, int64_t* E);

@@ -72,6 +72,8 @@ SIGNATURES = {
     "sem_helmholtz_grad": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "sem_apply_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "sem_dot": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "sem_sync": (ctypes.c_int, [_P, _P]),
+    "sem_selftest_timeout": (ctypes.c_int, [_P, ctypes.c_double, _P]),
     "sem_dot_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P]),
 }
 

@@ -187,6 +187,17 @@ def sem_apply_host(h, u_host, w_host, stream=None):
     return w_host
 
 
+def sem_sync(h, stream=None):
+    """Synchronise and raise SemError(SEM_ERR_TIMEOUT) if a device wait gave up."""
+    check(_lib.load().sem_sync(h.ptr, _stream(stream)))
+
+
+def sem_selftest_timeout(h, timeout_ms=20.0, stream=None):
+    """Run the starved-barrier diagnostic; returns the status name it produced."""
+    st = _lib.load().sem_selftest_timeout(h.ptr, float(timeout_ms), _stream(stream))
+    return STATUS_NAMES.get(st, st)
+
+
 def sem_dot(h, a, b, out, stream=None):
     """out[0] = sum_L a b / mult (unique-dof inner product), FP64, on the device."""
     if not out.is_cuda or out.dtype != torch.float64 or out.numel() < 1:

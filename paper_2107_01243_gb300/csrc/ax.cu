@@ -7,6 +7,8 @@
 // element is staged in shared memory for the r- and s-derivatives, rows are
 // padded to P+1 to spread the banks.  The 6 geometric factors of an element
 // are stored [6][P^3] so each factor streams coalesced along (i, j).
+#include <type_traits>
+
 #include "sem_internal.cuh"
 
 namespace sem {
@@ -144,6 +146,12 @@ static void launch_ax_p(const sem_handle* h, const OpData<T>& op, const T* u, T*
 template <class T>
 void launch_ax(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
                const T* h1f, const CGState* st, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (tma_ax_supported<float>(h, u, w, h1f)) {
+      launch_ax_tma<float>(h, op, u, w, h1, h2, h1f, st, h->dev_err.ptr, kWaitTimeoutNs, 0u, s);
+      return;
+    }
+  }
   switch (h->P) {
     case 2: launch_ax_p<2, T>(h, op, u, w, h1, h2, h1f, st, s); break;
     case 3: launch_ax_p<3, T>(h, op, u, w, h1, h2, h1f, st, s); break;

@@ -1,0 +1,290 @@
+// Element operator w_e = (h1 D^T G_e D + h2 B_e) u_e (arXiv 2107.01243 §2,
+// Eq. 9) with bulk-copy staging: a persistent CTA of P x P threads walks its
+// elements; thread 0 keeps STAGES elements in flight, each one copied into
+// shared memory by cp.async.bulk (u_e, the 6 geometric factors, optionally B_e
+// and h1_e: contiguous runs of P^3 values) and completed on an mbarrier.  D
+// travels in the kernel parameters (constant bank); each thread keeps the
+// D rows and columns of its (i, j) in registers.
+//
+// Per element (thread (i, j) owns the k-column):
+//   u column -> registers, transposed plane copy -> sT;  sync
+//   r, s, t derivatives (rows of u, rows of sT, the register column),
+//   times G -> swr, swsT (transposed), wt in registers;  sync; stage released
+//   w = D^T-contractions of swr rows, swsT rows and the wt column (+ h2 B u)
+// Needs P^3 * sizeof(T) % 16 == 0 (even P) and 16-byte aligned vectors.
+#include "sem_internal.cuh"
+#include "tma.cuh"
+
+namespace sem {
+
+template <int P, class T>
+struct DMat {
+  T d[P * P];
+};
+
+template <int P, class T>
+__device__ __forceinline__ void load_row(const T* __restrict__ p, T (&v)[P]) {
+  constexpr int bytes = P * (int)sizeof(T);
+  if constexpr (bytes % 16 == 0) {
+    constexpr int nv = bytes / 16;
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int a = 0; a < nv; ++a) {
+      float4 f = q[a];
+      const T* t = reinterpret_cast<const T*>(&f);
+#pragma unroll
+      for (int b = 0; b < 16 / (int)sizeof(T); ++b) v[a * (16 / (int)sizeof(T)) + b] = t[b];
+    }
+  } else if constexpr (bytes % 8 == 0) {
+    constexpr int nv = bytes / 8;
+    const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+    for (int a = 0; a < nv; ++a) {
+      float2 f = q[a];
+      const T* t = reinterpret_cast<const T*>(&f);
+#pragma unroll
+      for (int b = 0; b < 8 / (int)sizeof(T); ++b) v[a * (8 / (int)sizeof(T)) + b] = t[b];
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < P; ++a) v[a] = p[a];
+  }
+}
+
+template <int P, class T, int STAGES>
+__global__ void __launch_bounds__(P * P)
+ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ G,
+              const T* __restrict__ B, const T* __restrict__ h1f, T h1, T h2, DMat<P, T> D,
+              int E, const CGState* __restrict__ st, int* __restrict__ err, uint64_t timeout_ns,
+              uint32_t starve_bytes) {
+  constexpr int P2 = P * P, P3 = P2 * P;
+  constexpr uint32_t FB = P3 * sizeof(T);          // bytes of one field of one element
+  if (st && st->done) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  T* stage0 = reinterpret_cast<T*>(smem_raw + 128);
+  const bool helm = h2 != T(0);
+  const bool var = h1f != nullptr;
+  const int nf = 7 + (helm ? 1 : 0) + (var ? 1 : 0);
+  const int SE = nf * P3;                              // stage size in values
+  T* sT = stage0 + STAGES * SE;
+  T* swr = sT + P3;
+  T* swsT = swr + P3;
+  const int tid = threadIdx.x, i = tid % P, j = tid / P;
+
+  T Di[P], Dj[P], DiT[P], DjT[P];
+#pragma unroll
+  for (int l = 0; l < P; ++l) {
+    Di[l] = D.d[i * P + l];
+    Dj[l] = D.d[j * P + l];
+    DiT[l] = D.d[l * P + i];
+    DjT[l] = D.d[l * P + j];
+  }
+
+  auto issue = [&](int e, int s) {
+    T* dst = stage0 + s * SE;
+    mbar_arrive_expect_tx(&bar[s], nf * FB + starve_bytes);
+    bulk_g2s(dst, u + (size_t)e * P3, FB, &bar[s]);
+    bulk_g2s(dst + P3, G + (size_t)e * 6 * P3, 6 * FB, &bar[s]);
+    int off = 7 * P3;
+    if (helm) {
+      bulk_g2s(dst + off, B + (size_t)e * P3, FB, &bar[s]);
+      off += P3;
+    }
+    if (var) bulk_g2s(dst + off, h1f + (size_t)e * P3, FB, &bar[s]);
+  };
+
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) {
+      int e = blockIdx.x + s * gridDim.x;
+      if (e < E) issue(e, s);
+    }
+  }
+
+  int n = 0;
+  for (int e = blockIdx.x; e < E; e += gridDim.x, ++n) {
+    const int s = n % STAGES;
+    const uint32_t par = (uint32_t)(n / STAGES) & 1u;
+    const bool ok = mbar_wait_bounded(&bar[s], par, err, timeout_ns);
+    const T* su = stage0 + s * SE;
+    const T* sg = su + P3;
+    const T* sb = su + 7 * P3;
+    const T* sh = su + (helm ? 8 : 7) * P3;
+    T uc[P], bk[P], ck[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      uc[k] = su[k * P2 + tid];
+      sT[k * P2 + i * P + j] = uc[k];
+      bk[k] = helm ? sb[k * P2 + tid] : T(0);
+      ck[k] = var ? sh[k * P2 + tid] : h1;
+    }
+    if (__syncthreads_or(!ok)) {
+      // a copy never completed: wait (bounded) for what is in flight, then leave
+      if (tid == 0) {
+        for (int m = 0; m < STAGES; ++m) {
+          int nn = n + m;
+          if (blockIdx.x + nn * gridDim.x < E)
+            mbar_wait_bounded(&bar[nn % STAGES], (uint32_t)(nn / STAGES) & 1u, err, timeout_ns);
+        }
+      }
+      return;
+    }
+    T wt[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      T row[P], col[P];
+      load_row<P, T>(su + k * P2 + j * P, row);
+      load_row<P, T>(sT + k * P2 + i * P, col);
+      T ur = T(0), us = T(0), ut = T(0);
+#pragma unroll
+      for (int l = 0; l < P; ++l) {
+        ur = fma(Di[l], row[l], ur);
+        us = fma(Dj[l], col[l], us);
+        ut = fma(D.d[k * P + l], uc[l], ut);
+      }
+      const int q = k * P2 + tid;
+      T g11 = sg[q], g22 = sg[P3 + q], g33 = sg[2 * P3 + q];
+      T g12 = sg[3 * P3 + q], g13 = sg[4 * P3 + q], g23 = sg[5 * P3 + q];
+      T c = ck[k];
+      swr[k * P2 + j * P + i] = c * (g11 * ur + g12 * us + g13 * ut);
+      swsT[k * P2 + i * P + j] = c * (g12 * ur + g22 * us + g23 * ut);
+      wt[k] = c * (g13 * ur + g23 * us + g33 * ut);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int en = e + STAGES * gridDim.x;
+      if (en < E) {
+        fence_proxy_async_smem();
+        issue(en, s);
+      }
+    }
+    T* we = w + (size_t)e * P3;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      T row[P], col[P];
+      load_row<P, T>(swr + k * P2 + j * P, row);
+      load_row<P, T>(swsT + k * P2 + i * P, col);
+      T acc = T(0);
+#pragma unroll
+      for (int l = 0; l < P; ++l) {
+        acc = fma(DiT[l], row[l], acc);
+        acc = fma(DjT[l], col[l], acc);
+        acc = fma(D.d[l * P + k], wt[l], acc);
+      }
+      if (helm) acc = fma(h2 * bk[k], uc[k], acc);
+      we[k * P2 + tid] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launch
+template <int P, class T, int STAGES>
+static size_t tma_smem_bytes(int nf) {
+  return 128 + (size_t)(STAGES * nf + 3) * P * P * P * sizeof(T);
+}
+
+static int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = kNumSMs;
+  }
+  return n;
+}
+
+template <int P, class T, int STAGES>
+static void launch_tma_p(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
+                         const T* h1f, const CGState* st, int* err, uint64_t timeout_ns,
+                         uint32_t starve, cudaStream_t s) {
+  const int nf = 7 + (h2 != T(0) ? 1 : 0) + (h1f ? 1 : 0);
+  const size_t smem = tma_smem_bytes<P, T, STAGES>(nf);
+  auto kern = ax_tma_kernel<P, T, STAGES>;
+  static int configured_smem = 0;
+  static int occ[3] = {0, 0, 0};
+  const int maxsmem = (int)tma_smem_bytes<P, T, STAGES>(9);
+  if (configured_smem < maxsmem) {
+    SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
+    configured_smem = maxsmem;
+  }
+  int& o = occ[nf - 7];
+  if (!o) {
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, P * P, smem));
+    if (o < 1) o = 1;
+  }
+  DMat<P, T> D;
+  for (int a = 0; a < P * P; ++a) D.d[a] = (T)h->Dh[a];
+  const int E = (int)h->E;
+  int grid = std::min<int64_t>(E, (int64_t)o * num_sms());
+  if (grid < 1) grid = 1;
+  kern<<<grid, P * P, smem, s>>>(u, w, op.G.ptr, op.B.ptr, h1f, h1, h2, D, E, st, err,
+                                  timeout_ns, starve);
+  SEM_CHECK_LAUNCH();
+}
+
+template <class T>
+bool tma_ax_supported(const sem_handle* h, const void* u, const void* w, const void* h1f) {
+  const int P = h->P;
+  if (P != 2 && P != 4 && P != 6 && P != 8 && P != 10) return false;
+  auto al = [](const void* p) { return p == nullptr || ((uintptr_t)p % 16) == 0; };
+  return al(u) && al(w) && al(h1f);
+}
+
+template <class T>
+void launch_ax_tma(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
+                   const T* h1f, const CGState* st, int* err, uint64_t timeout_ns,
+                   uint32_t starve, cudaStream_t s) {
+  switch (h->P) {
+    case 2: launch_tma_p<2, T, 3>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    case 4: launch_tma_p<4, T, 3>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    case 6: launch_tma_p<6, T, 2>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    case 8: launch_tma_p<8, T, 2>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    case 10: launch_tma_p<10, T, 2>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    default: throw Error(SEM_ERR_ARG, "launch_ax_tma: unsupported order");
+  }
+}
+
+template bool tma_ax_supported<float>(const sem_handle*, const void*, const void*, const void*);
+template void launch_ax_tma<float>(const sem_handle*, const OpData<float>&, const float*, float*,
+                                   float, float, const float*, const CGState*, int*, uint64_t,
+                                   uint32_t, cudaStream_t);
+
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" sem_status sem_selftest_timeout(sem_handle* h, double timeout_ms, void* stream) {
+  sem_status result = SEM_OK;
+  sem_status st = guarded([&] {
+    SEM_REQUIRE(h, "sem_selftest_timeout: null handle");
+    SEM_REQUIRE(timeout_ms > 0 && timeout_ms <= 2000, "sem_selftest_timeout: timeout in (0, 2000] ms");
+    SEM_REQUIRE(h->f32.G.ptr, "sem_selftest_timeout: needs FP32 geometry");
+    SEM_REQUIRE(tma_ax_supported<float>(h, nullptr, nullptr, nullptr),
+                "sem_selftest_timeout: needs an even number of points per direction");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = h->nL;
+    DevBuf<float> u, w;
+    u.alloc(n);
+    w.alloc(n);
+    SEM_CUDA(cudaMemsetAsync(u.ptr, 0, n * sizeof(float), s));
+    SEM_CUDA(cudaMemsetAsync(h->dev_err.ptr, 0, sizeof(int), s));
+    // 16 bytes more than any copy delivers: the first stage barrier never completes
+    launch_ax_tma<float>(h, h->f32, u.ptr, w.ptr, 1.0f, 0.0f, nullptr, nullptr, h->dev_err.ptr,
+                         (uint64_t)(timeout_ms * 1e6), 16u, s);
+    int herr = 0;
+    SEM_CUDA(cudaMemcpyAsync(&herr, h->dev_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    SEM_CUDA(cudaMemsetAsync(h->dev_err.ptr, 0, sizeof(int), s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    result = (sem_status)herr;
+  });
+  return st != SEM_OK ? st : result;
+}

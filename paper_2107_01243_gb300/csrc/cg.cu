@@ -200,10 +200,20 @@ struct Pinned {
   ~Pinned() { if (p) cudaFreeHost(p); }
 };
 
-static CGState read_state(const CGState* d, cudaStream_t s) {
+// Copies the solver state to the host; raises SEM_ERR_TIMEOUT if a bounded
+// device wait gave up since the last check.
+static CGState read_state(const CGState* d, cudaStream_t s, int* dev_err = nullptr) {
   static thread_local Pinned pin;
   SEM_CUDA(cudaMemcpyAsync(pin.p, d, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+  if (dev_err)
+    SEM_CUDA(cudaMemcpyAsync(&pin.p[1].status, dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   SEM_CUDA(cudaStreamSynchronize(s));
+  if (dev_err && pin.p[1].status) {
+    SEM_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(int), s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    pin.p[1].status = 0;
+    throw Error(SEM_ERR_TIMEOUT, "a bounded device wait timed out during the solve");
+  }
   return *pin.p;
 }
 
@@ -264,7 +274,7 @@ static CGState run_pcg(sem_handle* h, const PcgArgs<T>& a, const sem_solve_opts&
     while (true) {
       if (exec) SEM_CUDA(cudaGraphLaunch(exec, s));
       else pcg_iterations<T>(h, a, batch, s);
-      hs = read_state(a.st, s);
+      hs = read_state(a.st, s, h->dev_err.ptr);
       if (hs.done) break;
     }
   } catch (...) {
@@ -504,6 +514,12 @@ extern "C" sem_status sem_apply_host(sem_handle* h, const void* u_host, void* w_
       launch_dssum<float>(h, out, true, nullptr, s);
     }
     SEM_CUDA(cudaMemcpyAsync(w_host, h->stage_out.ptr, bytes, cudaMemcpyDeviceToHost, s));
+    int herr = 0;
+    SEM_CUDA(cudaMemcpyAsync(&herr, h->dev_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     SEM_CUDA(cudaStreamSynchronize(s));
+    if (herr) {
+      SEM_CUDA(cudaMemsetAsync(h->dev_err.ptr, 0, sizeof(int), s));
+      throw Error(SEM_ERR_TIMEOUT, "sem_apply_host: a bounded device wait timed out");
+    }
   });
 }

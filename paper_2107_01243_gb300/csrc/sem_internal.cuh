@@ -18,6 +18,7 @@ constexpr int kMaxP = kMaxN + 1;
 constexpr int kNumSMs = 152;         // GB300: 2 dies x 76 SMs
 constexpr int kRedBlocks = 4 * kNumSMs;   // blocks of every reduction kernel
 constexpr int kRedThreads = 256;
+constexpr uint64_t kWaitTimeoutNs = 2000000000ull;   // bounded device waits give up after 2 s
 
 // ------------------------------------------------------------------ errors
 struct Error : std::runtime_error {
@@ -126,6 +127,7 @@ struct sem_handle {
   sem::DevBuf<float> imult;                 // 1 / multiplicity (exact)
   sem::DevBuf<uint8_t> mask;                // 0 on Dirichlet points
   sem::DevBuf<int64_t> gid;                 // global numbers
+  sem::DevBuf<int> dev_err;                 // device-side error word (SEM_ERR_TIMEOUT)
 
   // gather-scatter: segments of >= 2 local copies of one global point,
   // unmasked ones first; masked local points listed separately
@@ -155,6 +157,13 @@ void gll_host(int N, std::vector<double>& xi, std::vector<double>& w, std::vecto
 template <class T>
 void launch_ax(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
                const T* h1f, const CGState* state, cudaStream_t s);
+// bulk-copy staged variant (even P, 16-byte aligned vectors)
+template <class T>
+bool tma_ax_supported(const sem_handle* h, const void* u, const void* w, const void* h1f);
+template <class T>
+void launch_ax_tma(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
+                   const T* h1f, const CGState* state, int* err, uint64_t timeout_ns,
+                   uint32_t starve_bytes, cudaStream_t s);
 // diag(H_L) at every local point
 template <class T>
 void launch_local_diag(const sem_handle* h, const OpData<T>& op, T* d, T h1, T h2,

@@ -349,6 +349,8 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
     SEM_CUDA(cudaMemcpyAsync(&hbad, bad.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     SEM_CUDA(cudaStreamSynchronize(s));
     SEM_REQUIRE(!hbad, "sem_setup: element map has detJ <= 0 at some GLL point");
+    h->dev_err.alloc(1);
+    SEM_CUDA(cudaMemsetAsync(h->dev_err.ptr, 0, sizeof(int), s));
     h->state.alloc(3);
     SEM_CUDA(cudaMemsetAsync(h->state.ptr, 0, 3 * sizeof(CGState), s));
     h->partials.alloc(4 * kRedBlocks);
@@ -432,6 +434,21 @@ extern "C" sem_status sem_get_field(sem_handle* h, int which, void* dst, int dty
         break;
       default:
         throw Error(SEM_ERR_ARG, "sem_get_field: unknown field");
+    }
+  });
+}
+
+extern "C" sem_status sem_sync(sem_handle* h, void* stream) {
+  return guarded([&] {
+    SEM_REQUIRE(h, "sem_sync: null handle");
+    cudaStream_t s = (cudaStream_t)stream;
+    int herr = 0;
+    SEM_CUDA(cudaMemcpyAsync(&herr, h->dev_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    if (herr) {
+      SEM_CUDA(cudaMemsetAsync(h->dev_err.ptr, 0, sizeof(int), s));
+      SEM_CUDA(cudaStreamSynchronize(s));
+      throw Error((sem_status)herr, "sem_sync: a device wait timed out in an earlier call");
     }
   });
 }

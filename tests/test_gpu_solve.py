@@ -176,3 +176,18 @@ def test_adjoint_gradient_finite_differences():
     base = to_dev(h1)
     fd = (L(base + eps * d) - L(base - eps * d)) / (2 * eps)
     assert abs(fd - float((g * d).sum())) < 1e-6 * abs(fd)
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A bulk-copy barrier that can never complete: the kernel gives up after
+    the limit, records SEM_ERR_TIMEOUT and returns; the handle keeps working."""
+    h = sem.sem_setup((4, 3, 2), 7, length=(TWO_PI,) * 3, deform=0.1)
+    assert sem.sem_selftest_timeout(h, 20.0) == "SEM_ERR_TIMEOUT"
+    sem.sem_sync(h)                       # the record was cleared
+    o = OracleProblem((4, 3, 2), 7, length=(TWO_PI,) * 3, deform=0.1)
+    u = si.uniform(o.shape, 3)
+    w = torch.empty(h.n_local, dtype=torch.float32, device=DEV)
+    sem.sem_ax(h, torch.from_numpy(u).to(DEV, torch.float32), w)
+    sem.sem_sync(h)
+    ref = o.ax(u.astype(np.float32).astype(np.float64))
+    assert rel_inf(w.double().cpu().numpy().reshape(o.shape), ref) < 2e-5
