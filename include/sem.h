@@ -55,6 +55,12 @@ enum { SEM_PREC_F64 = 1, SEM_PREC_F32 = 2 };
 /* solver precision (sem_solve_opts.precision) */
 enum { SEM_SOLVE_F64 = 0, SEM_SOLVE_MIXED = 1 };
 
+/* FP64 Ax kernel selection (sem_set_f64_kernel) */
+enum { SEM_F64_KERNEL_AUTO = 0,        /* double-float where supported, else native */
+       SEM_F64_KERNEL_NATIVE = 1,      /* IEEE FP64 FMA (bound by the FP64 pipe) */
+       SEM_F64_KERNEL_DOUBLEFLOAT = 2  /* float-pair arithmetic, FP64 in and out */
+};
+
 /* Dirichlet face bits */
 enum { SEM_FACE_XMIN = 1, SEM_FACE_XMAX = 2, SEM_FACE_YMIN = 4,
        SEM_FACE_YMAX = 8, SEM_FACE_ZMIN = 16, SEM_FACE_ZMAX = 32,
@@ -145,6 +151,20 @@ sem_status sem_get_field(sem_handle* h, int which, void* dst, int dtype, void* s
  */
 sem_status sem_ax(sem_handle* h, const void* u_L, void* w_L, double h1, double h2,
                   const void* h1_field, int dtype, void* stream);
+
+/*
+ * sem_set_f64_kernel -- choose how FP64 Ax (sem_ax with SEM_F64, the FP64
+ * matvecs of sem_cg_solve and sem_apply_host) is computed.  GB300's FP64 pipe
+ * runs FMA about 60 times slower than its FP32 pipes, which makes the native
+ * kernel compute bound at roughly a tenth of the HBM rate.  The double-float
+ * kernel (default where supported: N in {5, 7, 9}, constant h1, 16-byte
+ * aligned vectors) keeps FP64 inputs and outputs, stores G and B as float
+ * pairs (8 bytes per value) and evaluates every sum with error-free float
+ * transformations; its error against FP64 is about 1e-14 relative to the
+ * largest |w|.  SEM_F64_KERNEL_NATIVE forces IEEE FP64 arithmetic.  Returns
+ * SEM_ERR_ARG for an unknown kind.
+ */
+sem_status sem_set_f64_kernel(sem_handle* h, int kind);
 
 /*
  * sem_dssum -- in place w_L <- QQ^T w_L: every local copy of a global point

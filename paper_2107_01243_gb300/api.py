@@ -187,6 +187,11 @@ def sem_apply_host(h, u_host, w_host, stream=None):
     return w_host
 
 
+def sem_set_f64_kernel(h, kind):
+    """Select the FP64 Ax kernel: SEM_F64_KERNEL_AUTO / _NATIVE / _DOUBLEFLOAT."""
+    check(_lib.load().sem_set_f64_kernel(h.ptr, int(kind)))
+
+
 def sem_sync(h, stream=None):
     """Synchronise and raise SemError(SEM_ERR_TIMEOUT) if a device wait gave up."""
     check(_lib.load().sem_sync(h.ptr, _stream(stream)))

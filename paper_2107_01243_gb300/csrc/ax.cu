@@ -151,6 +151,14 @@ void launch_ax(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1,
       launch_ax_tma<float>(h, op, u, w, h1, h2, h1f, st, h->dev_err.ptr, kWaitTimeoutNs, 0u, s);
       return;
     }
+  } else {
+    if (h->f64_kernel != SEM_F64_KERNEL_NATIVE && df_ax_supported(h, u, w, h1f)) {
+      launch_ax_df(h, u, w, h1, h2, st, s);
+      return;
+    }
+    if (h->f64_kernel == SEM_F64_KERNEL_DOUBLEFLOAT)
+      throw Error(SEM_ERR_STATE, "double-float Ax needs N in {5, 7, 9}, constant h1 and "
+                                 "16-byte aligned vectors");
   }
   switch (h->P) {
     case 2: launch_ax_p<2, T>(h, op, u, w, h1, h2, h1f, st, s); break;

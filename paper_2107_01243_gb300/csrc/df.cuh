@@ -1,0 +1,113 @@
+// Double-float ("df") arithmetic on the FP32 pipes for FP64-accurate results.
+//
+// A value is an unevaluated pair hi + lo of floats (about 48 significant bits).
+// GB300 runs FP32 FMA 60x faster than FP64 FMA, so FP64-accurate kernels that
+// would be bound by the FP64 pipe run on pairs instead.  Conversions to and
+// from double use integer bit manipulation only (no FP64 instructions).
+//
+// Dot products keep the running sum S of the rounded high-part products and
+// an FP32 error term: each product's rounding error comes from an FMA, each
+// addition's from TwoSum (Knuth), both exact; the low-part cross terms are
+// added to the error term in FP32.  The error of a result is then about
+// 2^-48 of the largest partial sum.  Every rounding below is requested
+// explicitly (the _rn intrinsics are never contracted into FMAs).
+#pragma once
+#include <stdint.h>
+
+namespace sem {
+
+// double -> (hi, lo): hi keeps the top 24 significand bits (truncated), lo the
+// next 23.  |x| below 2^-80 keeps hi only; zero and denormals give (0, 0).
+__device__ __forceinline__ void d2df(double x, float& hi, float& lo) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned int h32 = (unsigned int)(bits >> 32), l32 = (unsigned int)bits;
+  const unsigned int sign = h32 & 0x80000000u;
+  const int ex = (int)((h32 >> 20) & 0x7FF);
+  const int fe = ex - 1023 + 127;
+  if (fe <= 0) {
+    hi = 0.0f;
+    lo = 0.0f;
+    return;
+  }
+  hi = __uint_as_float(sign | ((unsigned)fe << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29));
+  // remaining 29 bits: keep the top 23 as an exact float integer, then scale
+  const unsigned int r = (l32 & 0x1FFFFFFFu) >> 6;
+  const float ri = __fsub_rn(__uint_as_float(0x4B000000u | r), 8388608.0f);
+  const int se = ex - 942;                       // 2^(ex - 1075 + 6) as a float exponent
+  const float scale = se > 0 ? __int_as_float(se << 23) : 0.0f;
+  lo = __uint_as_float(__float_as_uint(__fmul_rn(ri, scale)) | sign);
+}
+
+// (hi, lo) -> double, integer only.  The pair is first renormalised with
+// TwoSum so that |lo| <= ulp(hi)/2; lo's bits are then merged into the 53-bit
+// significand (truncated beyond it).
+__device__ __forceinline__ double df2d(float hi, float lo) {
+  const float s = __fadd_rn(hi, lo);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(lo, bb));
+  const unsigned int bs = __float_as_uint(s);
+  const int es = (int)((bs >> 23) & 0xFF);
+  if (es == 0) return 0.0;
+  unsigned long long m = ((unsigned long long)((bs & 0x7FFFFFu) | 0x800000u)) << 29;
+  int ed = es - 127 + 1023;
+  const unsigned int be = __float_as_uint(e);
+  const int ee = (int)((be >> 23) & 0xFF);
+  if (ee != 0) {
+    const unsigned long long me = (unsigned long long)((be & 0x7FFFFFu) | 0x800000u);
+    const int sh = 29 - (es - ee);               // <= 5 for a normalised pair
+    unsigned long long a = sh >= 0 ? (me << sh) : (sh > -64 ? (me >> (-sh)) : 0ull);
+    if ((be ^ bs) & 0x80000000u) m -= a; else m += a;
+    if (m >= (1ull << 53)) { m >>= 1; ++ed; }
+    else if (m < (1ull << 52)) { m <<= 1; --ed; }
+  }
+  const unsigned long long out = ((unsigned long long)(bs & 0x80000000u) << 32) |
+                                 ((unsigned long long)ed << 52) | (m & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)out);
+}
+
+// First term of a dot product: (S, err) = c z exactly up to the dropped cl zl.
+__device__ __forceinline__ void tmac0(float ch, float cl, float zh, float zl, float& S,
+                                      float& err) {
+  const float p = __fmul_rn(ch, zh);
+  float e = __fmaf_rn(ch, zh, -p);
+  e = __fmaf_rn(ch, zl, e);
+  S = p;
+  err = __fmaf_rn(cl, zh, e);
+}
+
+// Next term: S + RN(c zh) by TwoSum (exact), the product error by FMA (exact);
+// both errors and the low-part cross terms go to err.
+__device__ __forceinline__ void tmac(float ch, float cl, float zh, float zl, float& S,
+                                     float& err) {
+  const float p = __fmul_rn(ch, zh);
+  const float e = __fmaf_rn(ch, zh, -p);
+  const float s = __fadd_rn(S, p);
+  const float bb = __fsub_rn(s, S);
+  const float te = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  err = __fadd_rn(err, __fadd_rn(e, te));
+  err = __fmaf_rn(ch, zl, err);
+  err = __fmaf_rn(cl, zh, err);
+  S = s;
+}
+
+// S += z for a pair z (coefficient one), TwoSum on the high parts
+__device__ __forceinline__ void tadd(float zh, float zl, float& S, float& err) {
+  const float s = __fadd_rn(S, zh);
+  const float bb = __fsub_rn(s, S);
+  const float te = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(zh, bb));
+  err = __fadd_rn(err, __fadd_rn(te, zl));
+  S = s;
+}
+
+// exact product of two floats as a pair, plus low-part cross terms: a * b
+__device__ __forceinline__ void dfmul(float ah, float al, float bh, float bl, float& ph,
+                                      float& pl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  ph = p;
+  pl = e;
+}
+
+}  // namespace sem

@@ -128,6 +128,8 @@ struct sem_handle {
   sem::DevBuf<uint8_t> mask;                // 0 on Dirichlet points
   sem::DevBuf<int64_t> gid;                 // global numbers
   sem::DevBuf<int> dev_err;                 // device-side error word (SEM_ERR_TIMEOUT)
+  sem::DevBuf<float2> gdf, bdf;             // G and B as float pairs (double-float kernel)
+  int f64_kernel = SEM_F64_KERNEL_AUTO;     // which FP64 Ax kernel runs
 
   // gather-scatter: segments of >= 2 local copies of one global point,
   // unmasked ones first; masked local points listed separately
@@ -164,6 +166,10 @@ template <class T>
 void launch_ax_tma(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
                    const T* h1f, const CGState* state, int* err, uint64_t timeout_ns,
                    uint32_t starve_bytes, cudaStream_t s);
+// FP64-accurate double-float variant (even P in {6, 8, 10}, constant h1)
+bool df_ax_supported(const sem_handle* h, const void* u, const void* w, const void* h1f);
+void launch_ax_df(const sem_handle* h, const double* u, double* w, double h1, double h2,
+                  const CGState* state, cudaStream_t s);
 // diag(H_L) at every local point
 template <class T>
 void launch_local_diag(const sem_handle* h, const OpData<T>& op, T* d, T h1, T h2,

@@ -168,6 +168,16 @@ __global__ void convert_kernel(const S* __restrict__ src, D* __restrict__ dst, i
     dst[q] = (D)src[q];
 }
 
+// x -> (hi, lo) with hi = RN(x), lo = RN(x - hi): setup only, FP64 arithmetic
+__global__ void split_kernel(const double* __restrict__ src, float2* __restrict__ dst, int64_t n) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const double x = src[q];
+    const float hi = __double2float_rn(x);
+    dst[q] = make_float2(hi, __double2float_rn(x - (double)hi));
+  }
+}
+
 template <class D>
 __global__ void recip_kernel(const float* __restrict__ src, D* __restrict__ dst, int64_t n) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
@@ -349,6 +359,15 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
     SEM_CUDA(cudaMemcpyAsync(&hbad, bad.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     SEM_CUDA(cudaStreamSynchronize(s));
     SEM_REQUIRE(!hbad, "sem_setup: element map has detJ <= 0 at some GLL point");
+    if (P == 6 || P == 8 || P == 10) {
+      // float-pair copies of G and B for the double-float FP64 kernel
+      h->gdf.alloc(6 * nL);
+      h->bdf.alloc(nL);
+      split_kernel<<<grid_for(6 * nL), 256, 0, s>>>(h->f64.G.ptr, h->gdf.ptr, 6 * nL);
+      SEM_CHECK_LAUNCH();
+      split_kernel<<<grid_for(nL), 256, 0, s>>>(h->f64.B.ptr, h->bdf.ptr, nL);
+      SEM_CHECK_LAUNCH();
+    }
     h->dev_err.alloc(1);
     SEM_CUDA(cudaMemsetAsync(h->dev_err.ptr, 0, sizeof(int), s));
     h->state.alloc(3);
@@ -450,5 +469,17 @@ extern "C" sem_status sem_sync(sem_handle* h, void* stream) {
       SEM_CUDA(cudaStreamSynchronize(s));
       throw Error((sem_status)herr, "sem_sync: a device wait timed out in an earlier call");
     }
+  });
+}
+
+extern "C" sem_status sem_set_f64_kernel(sem_handle* h, int kind) {
+  return guarded([&] {
+    SEM_REQUIRE(h, "sem_set_f64_kernel: null handle");
+    SEM_REQUIRE(kind == SEM_F64_KERNEL_AUTO || kind == SEM_F64_KERNEL_NATIVE ||
+                    kind == SEM_F64_KERNEL_DOUBLEFLOAT,
+                "sem_set_f64_kernel: unknown kind");
+    if (kind == SEM_F64_KERNEL_DOUBLEFLOAT && !h->gdf.ptr)
+      throw Error(SEM_ERR_STATE, "sem_set_f64_kernel: double-float needs N in {5, 7, 9}");
+    h->f64_kernel = kind;
   });
 }

@@ -176,3 +176,26 @@ def test_dot_unique_dof(nel, N):
     first = float(out)
     sem.sem_dot(h, to_dev(ga[o.gid]).view(-1), to_dev(gb[o.gid]).view(-1), out)
     assert float(out) == first
+
+
+@pytest.mark.parametrize("nel,N", [((5, 3, 3), 7), ((4, 3, 2), 5), ((3, 2, 3), 9), ((7, 1, 1), 7)])
+@pytest.mark.parametrize("h1,h2", [(1.0, 0.0), (0.37, 4.25)])
+def test_ax_fp64_native_and_doublefloat(nel, N, h1, h2):
+    """Both FP64 kernels against the oracle at the FP64 tolerance; the
+    double-float one also on smooth input, where cancellation is strongest."""
+    h, o = make(nel, N)
+    inputs = [si.uniform(o.shape, 54), si.eval_fourier(si.fourier_modes(55), o.x, o.y, o.z)]
+    for kind in (sem.SEM_F64_KERNEL_NATIVE, sem.SEM_F64_KERNEL_DOUBLEFLOAT):
+        sem.sem_set_f64_kernel(h, kind)
+        for u in inputs:
+            w = torch.empty(h.n_local, dtype=torch.float64, device=DEV)
+            sem.sem_ax(h, to_dev(u).view(-1), w, h1, h2)
+            sem.sem_sync(h)
+            err = rel_inf(to_np(w).reshape(o.shape), o.ax(u, h1, h2))
+            assert err < TOL64, (kind, err)
+
+
+def test_doublefloat_rejects_unsupported_order():
+    h, _ = make((2, 2, 2), 4)
+    with pytest.raises(sem.SemError):
+        sem.sem_set_f64_kernel(h, sem.SEM_F64_KERNEL_DOUBLEFLOAT)
