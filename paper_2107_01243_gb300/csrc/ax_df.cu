@@ -3,29 +3,33 @@
 // pipes (df.cuh).  FP64 in, FP64 out; the geometric factors are stored as
 // float pairs (8 bytes per value, the same traffic as FP64).
 //
-// A persistent CTA of P x P threads walks its elements; thread 0 keeps
+// A persistent CTA of 3 x P x P threads walks its elements; thread 0 keeps
 // STAGES elements in flight with bulk copies (u_e as doubles, the 6 G pairs,
-// B pairs for Helmholtz).  Every contraction is done by "line tasks": a
-// thread reads one line of P pairs and produces the P outputs of that line,
-// so every D index is a compile-time constant served from the constant bank.
-//   phase 0  thread (i,j): u column -> pairs, kept in registers and stored U
-//   F-r, F-s thread (j,k) / (i,k): lines of U -> UR, US  (D)
-//   G        thread (i,j): F-t on its register column, then per point
-//            (WR, WS, WT) = h1 G (UR, US, UT); WR, WS overwrite UR, US
-//   B-r, B-s thread (j,k) / (i,k): lines of WR, WS -> CR, CS in place (D^T)
-//   B-t      thread (i,j): w = CR + CS + sum_l D_lk WT_l (+ h2 B u) -> double
+// B pairs for Helmholtz).  Contractions are "line tasks": a thread reads one
+// line of P pairs and makes the P outputs of that line, so every D index is a
+// compile-time constant (D lives in constant memory).  The three thread
+// groups take the r-, s- and t-lines side by side and run the same code with
+// different strides, which keeps the kernel small enough for the instruction
+// cache:
+//   phase 0  u -> pairs U
+//   forward  group g: lines of U along direction g -> UR | US | UT   (D)
+//   G        every point: (WR, WS, WT) = h1 G (UR, US, UT), in place
+//   backward group g: lines of W along direction g, in place          (D^T)
+//   final    w = CR + CS + CT (+ h2 B u) -> double
+// Sums use exact float transformations (TwoSum, FMA product errors).
 // Shared arrays use padded rows (P+2 pairs) and planes (stride = 8 mod 16
-// pairs) so the line reads are free of bank conflicts at P = 8.
+// pairs) to spread the shared-memory banks.
 #include "sem_internal.cuh"
 #include "tma.cuh"
 #include "df.cuh"
 
 namespace sem {
 
-template <int P>
-struct DFConst {
-  float dh[P * P];   // D[i][l], high parts
-  float dl[P * P];   // low parts
+// D (high and low parts) for every order, filled once per order on first use
+__constant__ float c_df_dh[kMaxP + 1][kMaxP * kMaxP];
+__constant__ float c_df_dl[kMaxP + 1][kMaxP * kMaxP];
+
+struct DFScal {
   float h1h, h1l, h2h, h2l;
 };
 
@@ -38,43 +42,55 @@ struct DFLayout {
   __device__ static constexpr int at(int i, int j, int k) { return k * PL + j * RS + i; }
 };
 
-// y_i = sum_l M[i][l] x_l (TRANS: M = D^T), all outputs of one line
+// One line task: the P outputs y_i = sum_l M[i][l] x_l of the line starting at
+// base with the given stride (M = D, or D^T when TRANS); in may equal out.
 template <int P, bool TRANS>
-__device__ __forceinline__ void line_df(const DFConst<P>& C, const float (&xh)[P],
-                                        const float (&xl)[P], float (&yh)[P], float (&yl)[P]) {
+__device__ __forceinline__ void line_task(const float2* in, float2* out, int base, int stride) {
+  float xh[P], xl[P];
+#pragma unroll
+  for (int l = 0; l < P; ++l) {
+    const float2 v = in[base + l * stride];
+    xh[l] = v.x;
+    xl[l] = v.y;
+  }
+  float yh[P], yl[P];
 #pragma unroll
   for (int i = 0; i < P; ++i) {
+    const int i0 = TRANS ? i : i * P;
     float S, err;
-    tmac0(C.dh[TRANS ? i : i * P], C.dl[TRANS ? i : i * P], xh[0], xl[0], S, err);
+    tmac0(c_df_dh[P][i0], c_df_dl[P][i0], xh[0], xl[0], S, err);
 #pragma unroll
     for (int l = 1; l < P; ++l) {
       const int idx = TRANS ? l * P + i : i * P + l;
-      tmac(C.dh[idx], C.dl[idx], xh[l], xl[l], S, err);
+      tmac(c_df_dh[P][idx], c_df_dl[P][idx], xh[l], xl[l], S, err);
     }
     yh[i] = S;
     yl[i] = err;
   }
+#pragma unroll
+  for (int i = 0; i < P; ++i) out[base + i * stride] = make_float2(yh[i], yl[i]);
 }
 
 // sum of three products g_a * v_a
-__device__ __forceinline__ void dot3_df(float g0h, float g0l, float g1h, float g1l, float g2h,
-                                        float g2l, float v0h, float v0l, float v1h, float v1l,
-                                        float v2h, float v2l, float& oh, float& ol) {
+__device__ __forceinline__ void dot3_df(float2 g0, float2 g1, float2 g2, float2 v0, float2 v1,
+                                        float2 v2, float& oh, float& ol) {
   float S, err;
-  tmac0(g0h, g0l, v0h, v0l, S, err);
-  tmac(g1h, g1l, v1h, v1l, S, err);
-  tmac(g2h, g2l, v2h, v2l, S, err);
+  tmac0(g0.x, g0.y, v0.x, v0.y, S, err);
+  tmac(g1.x, g1.y, v1.x, v1.y, S, err);
+  tmac(g2.x, g2.y, v2.x, v2.y, S, err);
   oh = S;
   ol = err;
 }
 
+// Three groups of P x P threads, one per direction, run the line tasks of the
+// r-, s- and t-direction side by side.
 template <int P, int STAGES>
-__global__ void __launch_bounds__(P * P)
+__global__ void __launch_bounds__(3 * P * P)
 ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2* __restrict__ G,
-             const float2* __restrict__ B, DFConst<P> C, int E, const CGState* __restrict__ st,
+             const float2* __restrict__ B, DFScal C, int E, const CGState* __restrict__ st,
              int* __restrict__ err, uint64_t timeout_ns) {
   using L = DFLayout<P>;
-  constexpr int P2 = P * P, P3 = P2 * P;
+  constexpr int P2 = P * P, P3 = P2 * P, NT = 3 * P2;
   constexpr uint32_t UB = P3 * sizeof(double), GB = 6 * P3 * sizeof(float2),
                      BB = P3 * sizeof(float2);
   if (st && st->done) return;
@@ -85,10 +101,14 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
   const uint32_t SB = UB + GB + (helm ? BB : 0);          // stage bytes
   unsigned char* stage0 = smem_raw + 128;
   float2* U = reinterpret_cast<float2*>(stage0 + STAGES * SB);
-  float2* UR = U + L::VOL;
-  float2* US = UR + L::VOL;
+  float2* R[3] = {U + L::VOL, U + 2 * L::VOL, U + 3 * L::VOL};   // r, s, t work arrays
   const int tid = threadIdx.x;
-  const int a = tid % P, b = tid / P;     // line / column coordinates
+  const int g = tid / P2, lam = tid % P2;
+  const int c1 = lam % P, c2 = lam / P;
+  // line of direction g: r: (j=c1, k=c2); s: (i=c1, k=c2); t: (i=c1, j=c2)
+  const int base = g == 0 ? L::at(0, c1, c2) : (g == 1 ? L::at(c1, 0, c2) : L::at(c1, c2, 0));
+  const int stride = g == 0 ? 1 : (g == 1 ? L::RS : L::PL);
+  float2* myR = g == 0 ? R[0] : (g == 1 ? R[1] : R[2]);
 
   auto issue = [&](int e, int s) {
     unsigned char* dst = stage0 + s * SB;
@@ -118,12 +138,11 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     const double* su = reinterpret_cast<const double*>(stage0 + s * SB);
     const float2* sg = reinterpret_cast<const float2*>(stage0 + s * SB + UB);
     const float2* sb = reinterpret_cast<const float2*>(stage0 + s * SB + UB + GB);
-    // phase 0: thread (i=a, j=b) converts its column
-    float uch[P], ucl[P];
-#pragma unroll
-    for (int k = 0; k < P; ++k) {
-      d2df(su[k * P2 + tid], uch[k], ucl[k]);
-      U[L::at(a, b, k)] = make_float2(uch[k], ucl[k]);
+    // phase 0: u -> pairs
+    for (int q = tid; q < P3; q += NT) {
+      float hi, lo;
+      d2df(su[q], hi, lo);
+      U[L::at(q % P, (q / P) % P, q / P2)] = make_float2(hi, lo);
     }
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
@@ -135,136 +154,75 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       }
       return;
     }
-    // F-r: line over i at (j=a, k=b);  F-s: line over j at (i=a, k=b)
-    {
-      float xh[P], xl[P], yh[P], yl[P];
-#pragma unroll
-      for (int l = 0; l < P; ++l) {
-        float2 v = U[L::at(l, a, b)];
-        xh[l] = v.x; xl[l] = v.y;
+    // forward derivatives: group g differentiates along direction g
+    line_task<P, false>(U, myR, base, stride);
+    __syncthreads();
+    // geometric factors at every point: (WR, WS, WT) = h1 G (UR, US, UT), in place
+    for (int q = tid; q < P3; q += NT) {
+      const int at = L::at(q % P, (q / P) % P, q / P2);
+      const float2 g11 = sg[q], g22 = sg[P3 + q], g33 = sg[2 * P3 + q];
+      const float2 g12 = sg[3 * P3 + q], g13 = sg[4 * P3 + q], g23 = sg[5 * P3 + q];
+      const float2 ur = R[0][at], us = R[1][at], ut = R[2][at];
+      float rh, rl, sh, sl, th, tl;
+      dot3_df(g11, g12, g13, ur, us, ut, rh, rl);
+      dot3_df(g12, g22, g23, ur, us, ut, sh, sl);
+      dot3_df(g13, g23, g33, ur, us, ut, th, tl);
+      if (scale1) {
+        dfmul(C.h1h, C.h1l, rh, rl, rh, rl);
+        dfmul(C.h1h, C.h1l, sh, sl, sh, sl);
+        dfmul(C.h1h, C.h1l, th, tl, th, tl);
       }
-      line_df<P, false>(C, xh, xl, yh, yl);
-#pragma unroll
-      for (int l = 0; l < P; ++l) UR[L::at(l, a, b)] = make_float2(yh[l], yl[l]);
-#pragma unroll
-      for (int l = 0; l < P; ++l) {
-        float2 v = U[L::at(a, l, b)];
-        xh[l] = v.x; xl[l] = v.y;
-      }
-      line_df<P, false>(C, xh, xl, yh, yl);
-#pragma unroll
-      for (int l = 0; l < P; ++l) US[L::at(a, l, b)] = make_float2(yh[l], yl[l]);
+      R[0][at] = make_float2(rh, rl);
+      R[1][at] = make_float2(sh, sl);
+      R[2][at] = make_float2(th, tl);
     }
     __syncthreads();
-    // G phase: thread (i=a, j=b); F-t on the register column first
-    float wth[P], wtl[P];
-    {
-      float uth[P], utl[P];
-      line_df<P, false>(C, uch, ucl, uth, utl);
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const int q = k * P2 + tid;
-        const float2 g11 = sg[q], g22 = sg[P3 + q], g33 = sg[2 * P3 + q];
-        const float2 g12 = sg[3 * P3 + q], g13 = sg[4 * P3 + q], g23 = sg[5 * P3 + q];
-        const float2 ur = UR[L::at(a, b, k)], us = US[L::at(a, b, k)];
-        float rh, rl, sh, sl, th, tl;
-        dot3_df(g11.x, g11.y, g12.x, g12.y, g13.x, g13.y, ur.x, ur.y, us.x, us.y, uth[k], utl[k],
-                rh, rl);
-        dot3_df(g12.x, g12.y, g22.x, g22.y, g23.x, g23.y, ur.x, ur.y, us.x, us.y, uth[k], utl[k],
-                sh, sl);
-        dot3_df(g13.x, g13.y, g23.x, g23.y, g33.x, g33.y, ur.x, ur.y, us.x, us.y, uth[k], utl[k],
-                th, tl);
-        if (scale1) {
-          dfmul(C.h1h, C.h1l, rh, rl, rh, rl);
-          dfmul(C.h1h, C.h1l, sh, sl, sh, sl);
-          dfmul(C.h1h, C.h1l, th, tl, th, tl);
-        }
-        UR[L::at(a, b, k)] = make_float2(rh, rl);
-        US[L::at(a, b, k)] = make_float2(sh, sl);
-        wth[k] = th;
-        wtl[k] = tl;
-      }
-    }
-    float bh[P], bl[P];
-#pragma unroll
-    for (int k = 0; k < P; ++k) {
-      if (helm) {
-        const float2 bv = sb[k * P2 + tid];
-        dfmul(C.h2h, C.h2l, bv.x, bv.y, bh[k], bl[k]);
-      } else {
-        bh[k] = 0.0f;
-        bl[k] = 0.0f;
-      }
-    }
-    __syncthreads();                          // stage s consumed; WR, WS complete
-    if (tid == 0) {
+    if (!helm && tid == 0) {                   // stage s consumed
       int en = e + STAGES * gridDim.x;
       if (en < E) {
         fence_proxy_async_smem();
         issue(en, s);
       }
     }
-    // B-r: line over i at (j=a, k=b);  B-s: line over j at (i=a, k=b)  (D^T)
-    {
-      float xh[P], xl[P], yh[P], yl[P];
-#pragma unroll
-      for (int l = 0; l < P; ++l) {
-        float2 v = UR[L::at(l, a, b)];
-        xh[l] = v.x; xl[l] = v.y;
-      }
-      line_df<P, true>(C, xh, xl, yh, yl);
-#pragma unroll
-      for (int l = 0; l < P; ++l) UR[L::at(l, a, b)] = make_float2(yh[l], yl[l]);
-#pragma unroll
-      for (int l = 0; l < P; ++l) {
-        float2 v = US[L::at(a, l, b)];
-        xh[l] = v.x; xl[l] = v.y;
-      }
-      line_df<P, true>(C, xh, xl, yh, yl);
-#pragma unroll
-      for (int l = 0; l < P; ++l) US[L::at(a, l, b)] = make_float2(yh[l], yl[l]);
-    }
+    // transposed derivatives, in place: group g along direction g
+    line_task<P, true>(myR, myR, base, stride);
     __syncthreads();
-    // B-t: thread (i=a, j=b): w(i,j,k) = CR + CS + sum_l D_lk WT_l (+ h2 B u)
-    {
-      double* we = w + (size_t)e * P3;
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const float2 cr = UR[L::at(a, b, k)], cs = US[L::at(a, b, k)];
-        float S = cr.x, er = cr.y;
-        tadd(cs.x, cs.y, S, er);
-#pragma unroll
-        for (int l = 0; l < P; ++l) tmac(C.dh[l * P + k], C.dl[l * P + k], wth[l], wtl[l], S, er);
-        if (helm) tmac(bh[k], bl[k], uch[k], ucl[k], S, er);
-        we[k * P2 + tid] = df2d(S, er);
+    // w = CR + CS + CT (+ h2 B u) -> double
+    double* we = w + (size_t)e * P3;
+    for (int q = tid; q < P3; q += NT) {
+      const int at = L::at(q % P, (q / P) % P, q / P2);
+      const float2 cr = R[0][at], cs = R[1][at], ct = R[2][at];
+      float S = cr.x, er = cr.y;
+      tadd(cs.x, cs.y, S, er);
+      tadd(ct.x, ct.y, S, er);
+      if (helm) {
+        const float2 bv = sb[q], uv = U[at];
+        float bh, bl;
+        dfmul(C.h2h, C.h2l, bv.x, bv.y, bh, bl);
+        tmac(bh, bl, uv.x, uv.y, S, er);
+      }
+      we[q] = df2d(S, er);
+    }
+    if (helm) {
+      __syncthreads();                         // U and the stage are free
+      if (tid == 0) {
+        int en = e + STAGES * gridDim.x;
+        if (en < E) {
+          fence_proxy_async_smem();
+          issue(en, s);
+        }
       }
     }
   }
 }
 
 // ---------------------------------------------------------------- launch
-template <int P>
-static DFConst<P> make_consts(const sem_handle* h, double h1, double h2) {
-  DFConst<P> c;
-  for (int q = 0; q < P * P; ++q) {
-    const double d = h->Dh[q];
-    const float dh = (float)d;
-    c.dh[q] = dh;
-    c.dl[q] = (float)(d - (double)dh);
-  }
-  c.h1h = (float)h1;
-  c.h1l = (float)(h1 - (double)c.h1h);
-  c.h2h = (float)h2;
-  c.h2l = (float)(h2 - (double)c.h2h);
-  return c;
-}
-
 template <int P, int STAGES>
 static size_t df_smem_bytes(bool helm) {
   using L = DFLayout<P>;
   const size_t P3 = (size_t)P * P * P;
   const size_t SB = P3 * 8 + 6 * P3 * 8 + (helm ? P3 * 8 : 0);
-  return 128 + STAGES * SB + 3 * (size_t)L::VOL * sizeof(float2);
+  return 128 + STAGES * SB + 4 * (size_t)L::VOL * sizeof(float2);
 }
 
 static int df_num_sms() {
@@ -276,6 +234,23 @@ static int df_num_sms() {
       n = kNumSMs;
   }
   return n;
+}
+
+// copies D of this order into the constant tables (once per order)
+static void df_upload_d(const sem_handle* h) {
+  static bool done[kMaxP + 1] = {};
+  const int P = h->P;
+  if (done[P]) return;
+  float dh[kMaxP * kMaxP] = {}, dl[kMaxP * kMaxP] = {};
+  for (int q = 0; q < P * P; ++q) {
+    const double d = h->Dh[q];
+    dh[q] = (float)d;
+    dl[q] = (float)(d - (double)dh[q]);
+  }
+  const size_t off = (size_t)P * kMaxP * kMaxP * sizeof(float);
+  SEM_CUDA(cudaMemcpyToSymbol(c_df_dh, dh, sizeof(dh), off));
+  SEM_CUDA(cudaMemcpyToSymbol(c_df_dl, dl, sizeof(dl), off));
+  done[P] = true;
 }
 
 template <int P, int STAGES>
@@ -293,14 +268,20 @@ static void launch_df_p(const sem_handle* h, const double* u, double* w, double 
   }
   int& o = occ[helm ? 1 : 0];
   if (!o) {
-    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, P * P, smem));
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 3 * P * P, smem));
     if (o < 1) o = 1;
   }
+  df_upload_d(h);
+  DFScal c;
+  c.h1h = (float)h1;
+  c.h1l = (float)(h1 - (double)c.h1h);
+  c.h2h = (float)h2;
+  c.h2l = (float)(h2 - (double)c.h2h);
   const int E = (int)h->E;
   int grid = (int)std::min<int64_t>(E, (int64_t)o * df_num_sms());
   if (grid < 1) grid = 1;
-  kern<<<grid, P * P, smem, s>>>(u, w, h->gdf.ptr, h->bdf.ptr, make_consts<P>(h, h1, h2), E, st,
-                                 h->dev_err.ptr, kWaitTimeoutNs);
+  kern<<<grid, 3 * P * P, smem, s>>>(u, w, h->gdf.ptr, h->bdf.ptr, c, E, st, h->dev_err.ptr,
+                                     kWaitTimeoutNs);
   SEM_CHECK_LAUNCH();
 }
 
@@ -314,8 +295,8 @@ bool df_ax_supported(const sem_handle* h, const void* u, const void* w, const vo
 void launch_ax_df(const sem_handle* h, const double* u, double* w, double h1, double h2,
                   const CGState* st, cudaStream_t s) {
   switch (h->P) {
-    case 6: launch_df_p<6, 2>(h, u, w, h1, h2, st, s); break;
-    case 8: launch_df_p<8, 2>(h, u, w, h1, h2, st, s); break;
+    case 6: launch_df_p<6, 1>(h, u, w, h1, h2, st, s); break;
+    case 8: launch_df_p<8, 1>(h, u, w, h1, h2, st, s); break;
     case 10: launch_df_p<10, 1>(h, u, w, h1, h2, st, s); break;
     default: throw Error(SEM_ERR_ARG, "launch_ax_df: unsupported order");
   }
