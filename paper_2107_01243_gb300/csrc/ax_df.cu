@@ -28,6 +28,10 @@ namespace sem {
 // D (high and low parts) for every order, filled once per order on first use
 __constant__ float c_df_dh[kMaxP + 1][kMaxP * kMaxP];
 __constant__ float c_df_dl[kMaxP + 1][kMaxP * kMaxP];
+// even-odd halves for even P: [trans][0: A = (M_il - M_i,N-l)/2, 1: S = (M_il + M_i,N-l)/2]
+// [0: high, 1: low][i * (P/2) + l], M = D or D^T
+constexpr int kMaxH = kMaxP / 2 + 1;
+__constant__ float c_df_eo[kMaxP + 1][2][2][2][kMaxH * kMaxH];
 
 struct DFScal {
   float h1h, h1l, h2h, h2l;
@@ -44,8 +48,13 @@ struct DFLayout {
 
 // One line task: the P outputs y_i = sum_l M[i][l] x_l of the line starting at
 // base with the given stride (M = D, or D^T when TRANS); in may equal out.
+// M is centro-antisymmetric (M[N-i][N-l] = -M[i][l] on GLL nodes), so with
+// e_l = x_l + x_{N-l}, o_l = x_l - x_{N-l} (l < P/2) the outputs come in pairs
+// y_i = A o + S e, y_{N-i} = A o - S e with two (P/2)-term dots per pair.
 template <int P, bool TRANS>
 __device__ __forceinline__ void line_task(const float2* in, float2* out, int base, int stride) {
+  static_assert(P % 2 == 0, "even-odd split needs an even number of points");
+  constexpr int H = P / 2, N = P - 1, T = TRANS ? 1 : 0;
   float xh[P], xl[P];
 #pragma unroll
   for (int l = 0; l < P; ++l) {
@@ -53,19 +62,25 @@ __device__ __forceinline__ void line_task(const float2* in, float2* out, int bas
     xh[l] = v.x;
     xl[l] = v.y;
   }
+  float eh[H], el[H], oh[H], ol[H];
+#pragma unroll
+  for (int l = 0; l < H; ++l) {
+    dfadd(xh[l], xl[l], xh[N - l], xl[N - l], eh[l], el[l]);
+    dfadd(xh[l], xl[l], -xh[N - l], -xl[N - l], oh[l], ol[l]);
+  }
   float yh[P], yl[P];
 #pragma unroll
-  for (int i = 0; i < P; ++i) {
-    const int i0 = TRANS ? i : i * P;
-    float S, err;
-    tmac0(c_df_dh[P][i0], c_df_dl[P][i0], xh[0], xl[0], S, err);
+  for (int i = 0; i < H; ++i) {
+    float Ph, Pl, Mh, Ml;
+    tmac0(c_df_eo[P][T][0][0][i * H], c_df_eo[P][T][0][1][i * H], oh[0], ol[0], Ph, Pl);
+    tmac0(c_df_eo[P][T][1][0][i * H], c_df_eo[P][T][1][1][i * H], eh[0], el[0], Mh, Ml);
 #pragma unroll
-    for (int l = 1; l < P; ++l) {
-      const int idx = TRANS ? l * P + i : i * P + l;
-      tmac(c_df_dh[P][idx], c_df_dl[P][idx], xh[l], xl[l], S, err);
+    for (int l = 1; l < H; ++l) {
+      tmac(c_df_eo[P][T][0][0][i * H + l], c_df_eo[P][T][0][1][i * H + l], oh[l], ol[l], Ph, Pl);
+      tmac(c_df_eo[P][T][1][0][i * H + l], c_df_eo[P][T][1][1][i * H + l], eh[l], el[l], Mh, Ml);
     }
-    yh[i] = S;
-    yl[i] = err;
+    dfadd(Ph, Pl, Mh, Ml, yh[i], yl[i]);
+    dfadd(Ph, Pl, -Mh, -Ml, yh[N - i], yl[N - i]);
   }
 #pragma unroll
   for (int i = 0; i < P; ++i) out[base + i * stride] = make_float2(yh[i], yl[i]);
@@ -236,10 +251,10 @@ static int df_num_sms() {
   return n;
 }
 
-// copies D of this order into the constant tables (once per order)
+// copies D and its even-odd halves for this order into constant memory (once)
 static void df_upload_d(const sem_handle* h) {
   static bool done[kMaxP + 1] = {};
-  const int P = h->P;
+  const int P = h->P, N = P - 1, H = P / 2;
   if (done[P]) return;
   float dh[kMaxP * kMaxP] = {}, dl[kMaxP * kMaxP] = {};
   for (int q = 0; q < P * P; ++q) {
@@ -250,6 +265,21 @@ static void df_upload_d(const sem_handle* h) {
   const size_t off = (size_t)P * kMaxP * kMaxP * sizeof(float);
   SEM_CUDA(cudaMemcpyToSymbol(c_df_dh, dh, sizeof(dh), off));
   SEM_CUDA(cudaMemcpyToSymbol(c_df_dl, dl, sizeof(dl), off));
+  float eo[2][2][2][kMaxH * kMaxH] = {};
+  for (int t = 0; t < 2; ++t) {
+    auto M = [&](int i, int l) { return t ? h->Dh[l * P + i] : h->Dh[i * P + l]; };
+    for (int i = 0; i < H; ++i)
+      for (int l = 0; l < H; ++l) {
+        const double a = 0.5 * (M(i, l) - M(i, N - l));
+        const double sm = 0.5 * (M(i, l) + M(i, N - l));
+        const float ah = (float)a, sh = (float)sm;
+        eo[t][0][0][i * H + l] = ah;
+        eo[t][0][1][i * H + l] = (float)(a - (double)ah);
+        eo[t][1][0][i * H + l] = sh;
+        eo[t][1][1][i * H + l] = (float)(sm - (double)sh);
+      }
+  }
+  SEM_CUDA(cudaMemcpyToSymbol(c_df_eo, eo, sizeof(eo), (size_t)P * sizeof(eo)));
   done[P] = true;
 }
 

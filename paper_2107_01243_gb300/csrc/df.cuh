@@ -99,6 +99,16 @@ __device__ __forceinline__ void tadd(float zh, float zl, float& S, float& err) {
   S = s;
 }
 
+// (sh, sl) = a + b for pairs: TwoSum on the high parts, low parts added in FP32
+__device__ __forceinline__ void dfadd(float ah, float al, float bh, float bl, float& sh,
+                                      float& sl) {
+  const float s = __fadd_rn(ah, bh);
+  const float bb = __fsub_rn(s, ah);
+  const float te = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  sh = s;
+  sl = __fadd_rn(te, __fadd_rn(al, bl));
+}
+
 // exact product of two floats as a pair, plus low-part cross terms: a * b
 __device__ __forceinline__ void dfmul(float ah, float al, float bh, float bl, float& ph,
                                       float& pl) {
