@@ -17,23 +17,48 @@
 namespace sem {
 
 // ------------------------------------------------------------------ kernels
+// Per-thread accumulation of a b / mult before the FP64 block and grid sums:
+// FP64 for FP64 vectors; for FP32 vectors an FP32 Kahan-compensated sum
+// (the FP64 pipe of GB300 is 60x slower than FP32, and per-point float to
+// double conversions would dominate these memory-bound kernels).
+template <class T>
+struct Acc;
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b, float im) { s += a * b * (double)im; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Acc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float a, float b, float im) {
+    const float y = __fsub_rn(__fmul_rn(__fmul_rn(a, b), im), c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 template <class T>
 __global__ void __launch_bounds__(kRedThreads)
 k_init(int64_t n, const T* __restrict__ r, const T* __restrict__ dinv,
        const float* __restrict__ imult, T* __restrict__ p, T* __restrict__ xzero,
        CGState* __restrict__ st, double* __restrict__ partials, double tol, int maxit,
        int bb_from_rr) {
-  double v[2] = {0.0, 0.0};
+  Acc<T> a0, a1;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
     T rq = r[q];
     T z = dinv[q] * rq;
     p[q] = z;
     if (xzero) xzero[q] = T(0);
-    double im = (double)imult[q];
-    v[0] += (double)rq * (double)z * im;
-    v[1] += (double)rq * (double)rq * im;
+    const float im = imult[q];
+    a0.add(rq, z, im);
+    a1.add(rq, rq, im);
   }
+  double v[2] = {a0.value(), a1.value()};
   double tot[2];
   if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
     st->rz = tot[0];
@@ -54,10 +79,11 @@ __global__ void __launch_bounds__(kRedThreads)
 k_pw(int64_t n, const T* __restrict__ p, const T* __restrict__ w, const float* __restrict__ imult,
      CGState* __restrict__ st, double* __restrict__ partials) {
   if (st->done) return;
-  double v[1] = {0.0};
+  Acc<T> a0;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x)
-    v[0] += (double)p[q] * (double)w[q] * (double)imult[q];
+    a0.add(p[q], w[q], imult[q]);
+  double v[1] = {a0.value()};
   double tot[1];
   if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
     st->pw = tot[0];
@@ -77,17 +103,18 @@ k_update(int64_t n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ 
          CGState* __restrict__ st, double* __restrict__ partials) {
   if (st->done) return;
   const T alpha = (T)st->alpha;
-  double v[2] = {0.0, 0.0};
+  Acc<T> a0, a1;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
     x[q] += alpha * p[q];
     T rq = r[q] - alpha * w[q];
     r[q] = rq;
     T z = dinv[q] * rq;
-    double im = (double)imult[q];
-    v[0] += (double)rq * (double)z * im;
-    v[1] += (double)rq * (double)rq * im;
+    const float im = imult[q];
+    a0.add(rq, z, im);
+    a1.add(rq, rq, im);
   }
+  double v[2] = {a0.value(), a1.value()};
   double tot[2];
   if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
     st->iter += 1;
