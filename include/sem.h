@@ -61,6 +61,11 @@ enum { SEM_F64_KERNEL_AUTO = 0,        /* double-float where supported, else nat
        SEM_F64_KERNEL_DOUBLEFLOAT = 2  /* float-pair arithmetic, FP64 in and out */
 };
 
+/* gather-scatter kernel selection (sem_set_dssum_kernel) */
+enum { SEM_DSSUM_BOX = 0,       /* copies computed from the box topology (default) */
+       SEM_DSSUM_SEGMENTS = 1   /* precomputed segment lists of shared local points */
+};
+
 /* Dirichlet face bits */
 enum { SEM_FACE_XMIN = 1, SEM_FACE_XMAX = 2, SEM_FACE_YMIN = 4,
        SEM_FACE_YMAX = 8, SEM_FACE_ZMIN = 16, SEM_FACE_ZMAX = 32,
@@ -173,6 +178,15 @@ sem_status sem_set_f64_kernel(sem_handle* h, int kind);
  * set to 0.
  */
 sem_status sem_dssum(sem_handle* h, void* w_L, int apply_mask, int dtype, void* stream);
+
+/*
+ * sem_set_dssum_kernel -- choose how QQ^T runs: SEM_DSSUM_BOX computes the
+ * copies of every shared point from the box topology (no index lists read),
+ * SEM_DSSUM_SEGMENTS walks precomputed segment lists of shared local points
+ * (the gslib-style layout of §3.2).  Both sum the copies of a point in
+ * increasing local index, so their results are bitwise identical.
+ */
+sem_status sem_set_dssum_kernel(sem_handle* h, int kind);
 
 /* b_L = mask o QQ^T (B f_L): the discrete right-hand side of §2, Eq. 6 for a
  * nodal source f (FP64 device L-vectors). */

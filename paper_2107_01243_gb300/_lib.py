@@ -22,6 +22,7 @@ SEM_PREC_F64, SEM_PREC_F32 = 1, 2
 SEM_SOLVE_F64, SEM_SOLVE_MIXED = 0, 1
 SEM_FACE_ALL = 63
 SEM_F64_KERNEL_AUTO, SEM_F64_KERNEL_NATIVE, SEM_F64_KERNEL_DOUBLEFLOAT = 0, 1, 2
+SEM_DSSUM_BOX, SEM_DSSUM_SEGMENTS = 0, 1
 (SEM_FIELD_X, SEM_FIELD_Y, SEM_FIELD_Z, SEM_FIELD_G, SEM_FIELD_B, SEM_FIELD_MULT,
  SEM_FIELD_MASK, SEM_FIELD_GID, SEM_FIELD_DINV) = range(9)
 
@@ -75,6 +76,7 @@ SIGNATURES = {
     "sem_dot": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "sem_sync": (ctypes.c_int, [_P, _P]),
     "sem_set_f64_kernel": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sem_set_dssum_kernel": (ctypes.c_int, [_P, ctypes.c_int]),
     "sem_selftest_timeout": (ctypes.c_int, [_P, ctypes.c_double, _P]),
     "sem_dot_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P]),
 }

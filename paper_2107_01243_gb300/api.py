@@ -192,6 +192,11 @@ def sem_set_f64_kernel(h, kind):
     check(_lib.load().sem_set_f64_kernel(h.ptr, int(kind)))
 
 
+def sem_set_dssum_kernel(h, kind):
+    """Select the gather-scatter kernel: SEM_DSSUM_BOX or SEM_DSSUM_SEGMENTS."""
+    check(_lib.load().sem_set_dssum_kernel(h.ptr, int(kind)))
+
+
 def sem_sync(h, stream=None):
     """Synchronise and raise SemError(SEM_ERR_TIMEOUT) if a device wait gave up."""
     check(_lib.load().sem_sync(h.ptr, _stream(stream)))

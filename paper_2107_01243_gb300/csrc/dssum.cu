@@ -30,6 +30,10 @@ __global__ void dssum_kernel(T* __restrict__ w, const int* __restrict__ seg_ptr,
 
 template <class T>
 void launch_dssum(const sem_handle* h, T* w, bool apply_mask, const CGState* st, cudaStream_t s) {
+  if (h->dssum_kernel == SEM_DSSUM_BOX) {
+    launch_dssum_box<T>(h, w, apply_mask, st, s);
+    return;
+  }
   const int nseg = (int)(apply_mask ? h->nseg_free : h->nseg_all);
   const int nm = apply_mask ? (int)h->nmasked : 0;
   const int total = nseg + nm;
@@ -55,5 +59,14 @@ extern "C" sem_status sem_dssum(sem_handle* h, void* w_L, int apply_mask, int dt
     if (dtype == SEM_F64) launch_dssum<double>(h, (double*)w_L, apply_mask != 0, nullptr, s);
     else if (dtype == SEM_F32) launch_dssum<float>(h, (float*)w_L, apply_mask != 0, nullptr, s);
     else throw Error(SEM_ERR_ARG, "sem_dssum: bad dtype");
+  });
+}
+
+extern "C" sem_status sem_set_dssum_kernel(sem_handle* h, int kind) {
+  return guarded([&] {
+    SEM_REQUIRE(h, "sem_set_dssum_kernel: null handle");
+    SEM_REQUIRE(kind == SEM_DSSUM_BOX || kind == SEM_DSSUM_SEGMENTS,
+                "sem_set_dssum_kernel: unknown kind");
+    h->dssum_kernel = kind;
   });
 }

@@ -137,6 +137,9 @@ struct sem_handle {
   sem::DevBuf<int> seg_ptr;                 // [nseg_all + 1]
   sem::DevBuf<int> seg_idx;                 // local indices
   sem::DevBuf<int> masked_idx;              // local indices with mask 0
+  int64_t nmasked_free = 0;                 // masked points owned by one element
+  sem::DevBuf<int> masked_free_idx;
+  int dssum_kernel = SEM_DSSUM_BOX;         // which gather-scatter kernel runs
 
   // solver scratch (allocated on first use)
   sem::DevBuf<double> r, p, w, x64, tmp64;
@@ -179,6 +182,11 @@ void launch_local_diag(const sem_handle* h, const OpData<T>& op, T* d, T h1, T h
 template <class T>
 void launch_dssum(const sem_handle* h, T* w, bool apply_mask, const CGState* state,
                   cudaStream_t s);
+
+// index-free variant for the structured box (same summation order)
+template <class T>
+void launch_dssum_box(const sem_handle* h, T* w, bool apply_mask, const CGState* state,
+                      cudaStream_t s);
 
 // ---- grad.cu
 void launch_grad(const sem_handle* h, const double* u, const double* lam, double* g,

@@ -322,6 +322,19 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
     h->seg_ptr.alloc(seg_ptr.size()); h->seg_ptr.upload(seg_ptr.data(), seg_ptr.size(), s);
     if (!seg_idx.empty()) { h->seg_idx.alloc(seg_idx.size()); h->seg_idx.upload(seg_idx.data(), seg_idx.size(), s); }
     if (!masked_idx.empty()) { h->masked_idx.alloc(masked_idx.size()); h->masked_idx.upload(masked_idx.data(), masked_idx.size(), s); }
+    {
+      // Dirichlet points with a single copy (the box gather-scatter zeroes the
+      // shared ones itself)
+      std::vector<int> free_idx;
+      for (int q : masked_idx)
+        if (imult[q] == 1.0f) free_idx.push_back(q);
+      h->nmasked_free = (int64_t)free_idx.size();
+      if (!free_idx.empty()) {
+        h->masked_free_idx.alloc(free_idx.size());
+        h->masked_free_idx.upload(free_idx.data(), free_idx.size(), s);
+        SEM_CUDA(cudaStreamSynchronize(s));   // free_idx leaves scope
+      }
+    }
 
     DevBuf<double> dxi, dwq;
     dxi.alloc(P); dxi.upload(h->xi.data(), P, s);

@@ -91,9 +91,11 @@ def test_ax_fp32(nel, N):
 
 @pytest.mark.parametrize("nel,N", CASES)
 @pytest.mark.parametrize("apply_mask", [False, True])
-def test_dssum_fp64_bitexact(nel, N, apply_mask):
+@pytest.mark.parametrize("kind", ["box", "segments"])
+def test_dssum_fp64_bitexact(nel, N, apply_mask, kind):
     from oracle import operator
     h, o = make(nel, N)
+    sem.sem_set_dssum_kernel(h, sem.SEM_DSSUM_BOX if kind == "box" else sem.SEM_DSSUM_SEGMENTS)
     w0 = si.uniform(o.shape, 44)
     w = to_dev(w0).view(-1).clone()
     sem.sem_dssum(h, w, apply_mask=apply_mask)
