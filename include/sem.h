@@ -233,7 +233,27 @@ sem_status sem_cg_solve(sem_handle* h, const double* b_L, double* x_L,
                         const sem_solve_opts* opts, sem_solve_info* info);
 
 /*
- * sem_helmholtz_grad -- g_L = -(D^ lambda)^T G (D^ u) at every local point,
+ * Batched solves.  sem_batch_create groups n (<= 256) handles, each built with
+ * SEM_PREC_F32 and an odd N (even points per direction), into a batch that
+ * advances all their solves together: every stage of an FP32 inner CG
+ * iteration (Ax, gather-scatter, the vector updates with per-problem dot
+ * products) is one kernel launch over all problems, elements of different
+ * orders dispatched inside the same persistent Ax kernel, and batches of
+ * iterations are captured in a CUDA graph.  Each problem refines in FP64 as
+ * in sem_cg_solve with SEM_SOLVE_MIXED (constant h1, h2 per problem).
+ * sem_batch_solve: b_L[p] and x_L[p] are device pointers (host array of n
+ * pointers) as for sem_cg_solve on handle p; h1[p], h2[p] the coefficients;
+ * opts as for sem_cg_solve (precision ignored: always mixed); infos receives
+ * n results.  The call synchronises.  The batch does not own the handles.
+ */
+sem_status sem_batch_create(sem_handle* const* handles, int n, sem_batch** out);
+sem_status sem_batch_solve(sem_batch* b, const double* const* b_L, double* const* x_L,
+                           const double* h1, const double* h2, const sem_solve_opts* opts,
+                           sem_solve_info* infos);
+sem_status sem_batch_destroy(sem_batch* b);
+
+/*
+ * sem_helmholtz_grad --g_L = -(D^ lambda)^T G (D^ u) at every local point,
  * D^ the reference gradient: the derivative of lambda^T H(h1) u with
  * respect to each local h1 value, negated -- the adjoint gradient dL/dh1 when
  * lambda solves H lambda = mask o QQ^T dL/du (structure of §2, Eq. 9).

@@ -74,6 +74,12 @@ SIGNATURES = {
     "sem_helmholtz_grad": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "sem_apply_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "sem_dot": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "sem_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
+    "sem_batch_solve": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]),
+    "sem_batch_destroy": (ctypes.c_int, [_P]),
     "sem_sync": (ctypes.c_int, [_P, _P]),
     "sem_set_f64_kernel": (ctypes.c_int, [_P, ctypes.c_int]),
     "sem_set_dssum_kernel": (ctypes.c_int, [_P, ctypes.c_int]),

@@ -226,3 +226,59 @@ def sem_dot_noalloc(h, a, b, out, stream=None):
                                       h._vec(b, "b", torch.float64),
                                       ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
+
+
+class Batch:
+    """Owns a sem_batch* over a list of Handles (which must outlive it)."""
+
+    def __init__(self, handles):
+        lib = _lib.load()
+        self.handles = list(handles)
+        arr = (ctypes.c_void_p * len(self.handles))(*[h.ptr.value if isinstance(h.ptr, ctypes.c_void_p)
+                                                     else h.ptr for h in self.handles])
+        out = ctypes.c_void_p()
+        check(lib.sem_batch_create(arr, len(self.handles), ctypes.byref(out)))
+        self.ptr = out
+
+    def __del__(self):
+        try:
+            sem_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def sem_batch_create(handles):
+    """Group handles (FP32 geometry, odd N) into a batch for sem_batch_solve."""
+    return Batch(handles)
+
+
+def sem_batch_destroy(batch):
+    if batch is not None and batch.ptr:
+        ptr, batch.ptr = batch.ptr, None
+        check(_lib.load().sem_batch_destroy(ptr))
+
+
+def sem_batch_solve(batch, bs, xs, h1s, h2s, tol=1e-8, maxit=20000, inner_tol=1e-4,
+                    max_outer=30, check_every=16, use_graph=True, stream=None):
+    """Solve every problem of the batch (FP32 inner / FP64 refinement);
+    returns one info dict per problem."""
+    lib = _lib.load()
+    n = len(batch.handles)
+    if not (len(bs) == len(xs) == len(h1s) == len(h2s) == n):
+        raise SemError(1, "sem_batch_solve: one b, x, h1, h2 per problem")
+    pb = (ctypes.c_void_p * n)(*[h._vec(b, "b", torch.float64).value
+                                 for h, b in zip(batch.handles, bs)])
+    px = (ctypes.c_void_p * n)(*[h._vec(x, "x", torch.float64).value
+                                 for h, x in zip(batch.handles, xs)])
+    c1 = (ctypes.c_double * n)(*[float(v) for v in h1s])
+    c2 = (ctypes.c_double * n)(*[float(v) for v in h2s])
+    o = SolveOpts()
+    lib.sem_solve_opts_default(ctypes.byref(o))
+    o.tol, o.maxit, o.inner_tol, o.max_outer = float(tol), int(maxit), float(inner_tol), int(max_outer)
+    o.check_every, o.use_graph = int(check_every), int(bool(use_graph))
+    o.precision = SEM_SOLVE_MIXED
+    o.stream = _stream(stream).value
+    infos = (SolveInfo * n)()
+    check(lib.sem_batch_solve(batch.ptr, pb, px, c1, c2, ctypes.byref(o), infos))
+    return [dict(iters=i.iters, outer_iters=i.outer_iters, rel_res=i.rel_res,
+                 status=STATUS_NAMES.get(i.status, i.status)) for i in infos]

@@ -447,6 +447,35 @@ struct StreamScope {
   }
 };
 
+// ---- pieces of the mixed-precision solve shared with the batched solver
+void mixed_prepare(sem_handle* h, const sem_solve_opts& o, cudaStream_t s) {
+  const int64_t n = h->nL;
+  if (!h->f32.G.ptr) throw Error(SEM_ERR_STATE, "mixed solve needs FP32 geometry (SEM_PREC_F32)");
+  ensure(h->r, n); ensure(h->w, n);
+  ensure(h->r32, n); ensure(h->p32, n); ensure(h->w32, n); ensure(h->x32, n);
+  ensure_dinv(h, o.h1, o.h2, o.h1_field, true, s);
+}
+
+void outer_norm_b(sem_handle* h, const double* b, cudaStream_t s) {
+  k_norm_bb<<<kRedBlocks, kRedThreads, 0, s>>>(h->nL, b, h->imult.ptr, h->state.ptr,
+                                               h->partials.ptr);
+  SEM_CHECK_LAUNCH();
+}
+
+void outer_residual(sem_handle* h, const double* b, const double* x, const sem_solve_opts& o,
+                    cudaStream_t s) {
+  residual64(h, b, x, o.h1, o.h2, o.h1_field, h->r32.ptr, h->state.ptr, s);
+}
+
+void outer_update(sem_handle* h, double* x, cudaStream_t s) {
+  k_addx<<<ew_grid(h->nL), 256, 0, s>>>(h->nL, x, h->x32.ptr);
+  SEM_CHECK_LAUNCH();
+}
+
+CGState state_to_host(const CGState* d, cudaStream_t s, int* dev_err) {
+  return read_state(d, s, dev_err);
+}
+
 }  // namespace sem
 
 using namespace sem;

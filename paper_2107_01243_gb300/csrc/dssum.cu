@@ -67,6 +67,7 @@ extern "C" sem_status sem_set_dssum_kernel(sem_handle* h, int kind) {
     SEM_REQUIRE(h, "sem_set_dssum_kernel: null handle");
     SEM_REQUIRE(kind == SEM_DSSUM_BOX || kind == SEM_DSSUM_SEGMENTS,
                 "sem_set_dssum_kernel: unknown kind");
+    if (kind == SEM_DSSUM_SEGMENTS) sem_build_segments(h, nullptr);
     h->dssum_kernel = kind;
   });
 }

@@ -16,21 +16,6 @@
 
 namespace sem {
 
-// Division of 32-bit unsigned n < 2^31 by a runtime divisor d >= 1 as a
-// multiply and shift (Granlund and Montgomery, 1994): q = (umulhi(n, m) + n) >> s
-struct FastDiv {
-  uint32_t d, m, s;
-  FastDiv() : d(1), m(0), s(0) {}
-  explicit FastDiv(uint32_t dd) : d(dd) {
-    s = 0;
-    while ((1ull << s) < dd) ++s;
-    m = dd == 1 ? 0u : (uint32_t)((((1ull << 32) * ((1ull << s) - dd)) / dd) + 1);
-  }
-  __device__ __forceinline__ uint32_t div(uint32_t n) const {
-    return d == 1 ? n : (__umulhi(n, m) + n) >> s;
-  }
-};
-
 struct BoxDims {
   int nelx, nely, nelz;
   int gx, gy, gz;            // lattice extents N nel + 1
@@ -98,8 +83,9 @@ template <int N>
 __device__ __forceinline__ int free_coord(int m, int nfree, int g) {
   if (m == 0) return 0;
   if (m == nfree - 1) return g - 1;
+  constexpr int M = N > 1 ? N - 1 : 1;      // N = 1 has no interior coordinates
   const int q = m - 1;
-  return q / (N - 1) * N + 1 + q % (N - 1);
+  return q / M * N + 1 + q % M;
 }
 
 template <int N, class T>

@@ -85,6 +85,21 @@ struct DevBuf {
   }
 };
 
+// Division of 32-bit unsigned n < 2^31 by a runtime divisor d >= 1 as a
+// multiply and shift (Granlund and Montgomery, 1994): q = (umulhi(n, m) + n) >> s
+struct FastDiv {
+  uint32_t d, m, s;
+  FastDiv() : d(1), m(0), s(0) {}
+  explicit FastDiv(uint32_t dd) : d(dd) {
+    s = 0;
+    while ((1ull << s) < dd) ++s;
+    m = dd == 1 ? 0u : (uint32_t)((((1ull << 32) * ((1ull << s) - dd)) / dd) + 1);
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    return d == 1 ? n : (__umulhi(n, m) + n) >> s;
+  }
+};
+
 // CG scalars kept on the device so that iterations need no host round trip.
 struct CGState {
   double rz;        // <r, z> of the current residual
@@ -140,6 +155,7 @@ struct sem_handle {
   int64_t nmasked_free = 0;                 // masked points owned by one element
   sem::DevBuf<int> masked_free_idx;
   int dssum_kernel = SEM_DSSUM_BOX;         // which gather-scatter kernel runs
+  int segments_built = 0;                   // segment lists exist (built on first use)
 
   // solver scratch (allocated on first use)
   sem::DevBuf<double> r, p, w, x64, tmp64;
@@ -152,6 +168,9 @@ struct sem_handle {
   const void* dinv_h1f = nullptr;
   int dinv_valid = 0;
 };
+
+// segment lists and the Dirichlet list of the segment-list gather-scatter
+void sem_build_segments(sem_handle* h, cudaStream_t s);
 
 namespace sem {
 
@@ -187,6 +206,14 @@ void launch_dssum(const sem_handle* h, T* w, bool apply_mask, const CGState* sta
 template <class T>
 void launch_dssum_box(const sem_handle* h, T* w, bool apply_mask, const CGState* state,
                       cudaStream_t s);
+
+// ---- cg.cu: pieces of the mixed-precision solve reused by the batched solver
+void mixed_prepare(sem_handle* h, const sem_solve_opts& o, cudaStream_t s);
+void outer_norm_b(sem_handle* h, const double* b, cudaStream_t s);    // <b,b> -> state[0].bb
+void outer_residual(sem_handle* h, const double* b, const double* x, const sem_solve_opts& o,
+                    cudaStream_t s);                                   // r, r32, <r,r> -> state[0]
+void outer_update(sem_handle* h, double* x, cudaStream_t s);          // x += x32
+CGState state_to_host(const CGState* d, cudaStream_t s, int* dev_err);
 
 // ---- grad.cu
 void launch_grad(const sem_handle* h, const double* u, const double* lam, double* g,

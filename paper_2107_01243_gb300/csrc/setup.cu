@@ -161,6 +161,33 @@ __global__ void geom_kernel(int P, int64_t nL, const double* __restrict__ Dm,
   }
 }
 
+// Global number, 1/multiplicity and Dirichlet mask of every local point of
+// the box (the lattice index of (e, i, j, k) is (N ex + i, N ey + j, N ez + k)).
+__global__ void topo_kernel(int N, int nelx, int nely, int nelz, int faces, int64_t nL,
+                            int64_t* __restrict__ gid, float* __restrict__ imult,
+                            uint8_t* __restrict__ mask) {
+  const int P = N + 1, P3 = P * P * P;
+  const int64_t gx = (int64_t)N * nelx + 1, gy = (int64_t)N * nely + 1, gz = (int64_t)N * nelz + 1;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nL;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = q / P3;
+    const int r = (int)(q - e * P3);
+    const int i = r % P, j = (r / P) % P, k = r / (P * P);
+    const int64_t ix = (int64_t)N * (e % nelx) + i;
+    const int64_t iy = (int64_t)N * ((e / nelx) % nely) + j;
+    const int64_t iz = (int64_t)N * (e / ((int64_t)nelx * nely)) + k;
+    gid[q] = ix + gx * (iy + gy * iz);
+    const int m = ((ix % N == 0 && ix > 0 && ix < gx - 1) ? 2 : 1) *
+                  ((iy % N == 0 && iy > 0 && iy < gy - 1) ? 2 : 1) *
+                  ((iz % N == 0 && iz > 0 && iz < gz - 1) ? 2 : 1);
+    imult[q] = 1.0f / (float)m;
+    const bool d = ((faces & SEM_FACE_XMIN) && ix == 0) || ((faces & SEM_FACE_XMAX) && ix == gx - 1) ||
+                   ((faces & SEM_FACE_YMIN) && iy == 0) || ((faces & SEM_FACE_YMAX) && iy == gy - 1) ||
+                   ((faces & SEM_FACE_ZMIN) && iz == 0) || ((faces & SEM_FACE_ZMAX) && iz == gz - 1);
+    mask[q] = d ? 0 : 1;
+  }
+}
+
 template <class S, class D>
 __global__ void convert_kernel(const S* __restrict__ src, D* __restrict__ dst, int64_t n) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
@@ -199,49 +226,76 @@ static int grid_for(int64_t n, int threads = 256) {
 }
 
 // ------------------------------------------------------------------ topology (host)
-static void build_topology(sem_handle* h, std::vector<int64_t>& gid, std::vector<float>& imult,
-                           std::vector<uint8_t>& mask) {
+// Multiplicity factor of one lattice coordinate (2 on an interior interface)
+static inline int mult1(int64_t ind, int N, int nel) {
+  return (ind % N == 0 && ind > 0 && ind < (int64_t)N * nel) ? 2 : 1;
+}
+
+static bool masked_at(const sem_handle* h, int64_t ix, int64_t iy, int64_t iz) {
+  const int64_t gx = (int64_t)h->N * h->nelx + 1, gy = (int64_t)h->N * h->nely + 1;
+  const int64_t gz = (int64_t)h->N * h->nelz + 1;
+  const int f = h->faces;
+  return ((f & SEM_FACE_XMIN) && ix == 0) || ((f & SEM_FACE_XMAX) && ix == gx - 1) ||
+         ((f & SEM_FACE_YMIN) && iy == 0) || ((f & SEM_FACE_YMAX) && iy == gy - 1) ||
+         ((f & SEM_FACE_ZMIN) && iz == 0) || ((f & SEM_FACE_ZMAX) && iz == gz - 1);
+}
+
+// Dirichlet points owned by a single element: only boundary elements can hold one.
+static void build_masked_free(sem_handle* h, cudaStream_t s) {
   const int N = h->N, P = h->P, P3 = h->P3;
-  const int64_t gx = (int64_t)N * h->nelx + 1, gy = (int64_t)N * h->nely + 1;
-  const int64_t gz = (int64_t)N * h->nelz + 1;
-  h->nG = gx * gy * gz;
-  const int64_t nL = h->nL;
-  gid.resize(nL);
-  imult.resize(nL);
-  mask.resize(nL);
-  auto m1 = [N](int64_t ind, int nel) {
-    return (ind % N == 0 && ind > 0 && ind < (int64_t)N * nel) ? 2 : 1;
-  };
-  for (int64_t e = 0; e < h->E; ++e) {
-    int ex = (int)(e % h->nelx), ey = (int)((e / h->nelx) % h->nely);
-    int ez = (int)(e / ((int64_t)h->nelx * h->nely));
-    for (int k = 0; k < P; ++k)
-      for (int j = 0; j < P; ++j)
-        for (int i = 0; i < P; ++i) {
-          int64_t q = e * P3 + (k * P + j) * P + i;
-          int64_t ix = (int64_t)N * ex + i, iy = (int64_t)N * ey + j, iz = (int64_t)N * ez + k;
-          gid[q] = ix + gx * (iy + gy * iz);
-          int m = m1(ix, h->nelx) * m1(iy, h->nely) * m1(iz, h->nelz);
-          imult[q] = 1.0f / (float)m;
-          bool d = ((h->faces & SEM_FACE_XMIN) && ix == 0) ||
-                   ((h->faces & SEM_FACE_XMAX) && ix == gx - 1) ||
-                   ((h->faces & SEM_FACE_YMIN) && iy == 0) ||
-                   ((h->faces & SEM_FACE_YMAX) && iy == gy - 1) ||
-                   ((h->faces & SEM_FACE_ZMIN) && iz == 0) ||
-                   ((h->faces & SEM_FACE_ZMAX) && iz == gz - 1);
-          mask[q] = d ? 0 : 1;
-        }
+  std::vector<int> idx;
+  for (int ez = 0; ez < h->nelz; ++ez)
+    for (int ey = 0; ey < h->nely; ++ey)
+      for (int ex = 0; ex < h->nelx; ++ex) {
+        if (ex > 0 && ex < h->nelx - 1 && ey > 0 && ey < h->nely - 1 && ez > 0 && ez < h->nelz - 1)
+          continue;
+        const int64_t e = ex + (int64_t)h->nelx * (ey + (int64_t)h->nely * ez);
+        for (int k = 0; k < P; ++k)
+          for (int j = 0; j < P; ++j)
+            for (int i = 0; i < P; ++i) {
+              const int64_t ix = (int64_t)N * ex + i, iy = (int64_t)N * ey + j;
+              const int64_t iz = (int64_t)N * ez + k;
+              if (!masked_at(h, ix, iy, iz)) continue;
+              if (mult1(ix, N, h->nelx) * mult1(iy, N, h->nely) * mult1(iz, N, h->nelz) != 1)
+                continue;
+              idx.push_back((int)(e * P3 + (k * P + j) * P + i));
+            }
+      }
+  std::sort(idx.begin(), idx.end());
+  h->nmasked_free = (int64_t)idx.size();
+  if (!idx.empty()) {
+    h->masked_free_idx.alloc(idx.size());
+    h->masked_free_idx.upload(idx.data(), idx.size(), s);
+    SEM_CUDA(cudaStreamSynchronize(s));
   }
 }
 
+}  // namespace sem
+
 // Segments of local points sharing a global number (§3.2: local indices grouped
 // per global id), ordered by global number, local indices ascending inside a
-// segment; unmasked segments first.
-static void build_segments(sem_handle* h, const std::vector<int64_t>& gid,
-                           const std::vector<float>& imult, const std::vector<uint8_t>& mask,
-                           std::vector<int>& seg_ptr, std::vector<int>& seg_idx,
-                           std::vector<int>& masked_idx) {
+// segment, unmasked segments first; plus the list of all Dirichlet points.
+// Built on first use of the segment-list gather-scatter.
+void sem_build_segments(sem_handle* h, cudaStream_t s) {
+  using namespace sem;
+  if (h->segments_built) return;
+  const int N = h->N, P = h->P, P3 = h->P3;
+  const int64_t gx = (int64_t)N * h->nelx + 1, gy = (int64_t)N * h->nely + 1;
   const int64_t nL = h->nL, nG = h->nG;
+  std::vector<int64_t> gid(nL);
+  std::vector<uint8_t> mask(nL);
+  for (int64_t e = 0; e < h->E; ++e) {
+    const int ex = (int)(e % h->nelx), ey = (int)((e / h->nelx) % h->nely);
+    const int ez = (int)(e / ((int64_t)h->nelx * h->nely));
+    for (int k = 0; k < P; ++k)
+      for (int j = 0; j < P; ++j)
+        for (int i = 0; i < P; ++i) {
+          const int64_t q = e * P3 + (k * P + j) * P + i;
+          const int64_t ix = (int64_t)N * ex + i, iy = (int64_t)N * ey + j, iz = (int64_t)N * ez + k;
+          gid[q] = ix + gx * (iy + gy * iz);
+          mask[q] = masked_at(h, ix, iy, iz) ? 0 : 1;
+        }
+  }
   std::vector<int> count(nG, 0);
   std::vector<uint8_t> gmask(nG, 1);
   for (int64_t q = 0; q < nL; ++q) {
@@ -253,29 +307,41 @@ static void build_segments(sem_handle* h, const std::vector<int64_t>& gid,
   for (int pass = 0; pass < 2; ++pass) {
     for (int64_t g = 0; g < nG; ++g) {
       if (count[g] < 2) continue;
-      bool masked = gmask[g] == 0;
+      const bool masked = gmask[g] == 0;
       if ((pass == 0) == masked) continue;
       segid[g] = (int)nseg++;
     }
     if (pass == 0) h->nseg_free = nseg;
   }
   h->nseg_all = nseg;
-  seg_ptr.assign(nseg + 1, 0);
+  std::vector<int> seg_ptr(nseg + 1, 0);
   for (int64_t g = 0; g < nG; ++g)
     if (segid[g] >= 0) seg_ptr[segid[g] + 1] = count[g];
-  for (int64_t s = 0; s < nseg; ++s) seg_ptr[s + 1] += seg_ptr[s];
-  seg_idx.assign(seg_ptr[nseg], 0);
+  for (int64_t q = 0; q < nseg; ++q) seg_ptr[q + 1] += seg_ptr[q];
+  std::vector<int> seg_idx(seg_ptr[nseg], 0);
   std::vector<int> fill(seg_ptr.begin(), seg_ptr.end() - 1);
-  masked_idx.clear();
+  std::vector<int> masked_idx;
   for (int64_t q = 0; q < nL; ++q) {
-    int s = segid[gid[q]];
-    if (s >= 0) seg_idx[fill[s]++] = (int)q;
+    const int sg = segid[gid[q]];
+    if (sg >= 0) seg_idx[fill[sg]++] = (int)q;
     if (!mask[q]) masked_idx.push_back((int)q);
   }
   h->nmasked = (int64_t)masked_idx.size();
-  (void)imult;
+  h->seg_ptr.alloc(seg_ptr.size());
+  h->seg_ptr.upload(seg_ptr.data(), seg_ptr.size(), s);
+  if (!seg_idx.empty()) {
+    h->seg_idx.alloc(seg_idx.size());
+    h->seg_idx.upload(seg_idx.data(), seg_idx.size(), s);
+  }
+  if (!masked_idx.empty()) {
+    h->masked_idx.alloc(masked_idx.size());
+    h->masked_idx.upload(masked_idx.data(), masked_idx.size(), s);
+  }
+  SEM_CUDA(cudaStreamSynchronize(s));
+  h->segments_built = 1;
 }
 
+namespace sem {
 }  // namespace sem
 
 using namespace sem;
@@ -307,34 +373,16 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
     h->faces = mesh->dirichlet_faces & SEM_FACE_ALL;
     gll_host(N, h->xi, h->wq, h->Dh);
 
-    std::vector<int64_t> gid;
-    std::vector<float> imult;
-    std::vector<uint8_t> mask;
-    build_topology(h.get(), gid, imult, mask);
-    std::vector<int> seg_ptr, seg_idx, masked_idx;
-    build_segments(h.get(), gid, imult, mask, seg_ptr, seg_idx, masked_idx);
-
     const int64_t nL = h->nL;
     const int P = h->P;
-    h->gid.alloc(nL);       h->gid.upload(gid.data(), nL, s);
-    h->imult.alloc(nL);     h->imult.upload(imult.data(), nL, s);
-    h->mask.alloc(nL);      h->mask.upload(mask.data(), nL, s);
-    h->seg_ptr.alloc(seg_ptr.size()); h->seg_ptr.upload(seg_ptr.data(), seg_ptr.size(), s);
-    if (!seg_idx.empty()) { h->seg_idx.alloc(seg_idx.size()); h->seg_idx.upload(seg_idx.data(), seg_idx.size(), s); }
-    if (!masked_idx.empty()) { h->masked_idx.alloc(masked_idx.size()); h->masked_idx.upload(masked_idx.data(), masked_idx.size(), s); }
-    {
-      // Dirichlet points with a single copy (the box gather-scatter zeroes the
-      // shared ones itself)
-      std::vector<int> free_idx;
-      for (int q : masked_idx)
-        if (imult[q] == 1.0f) free_idx.push_back(q);
-      h->nmasked_free = (int64_t)free_idx.size();
-      if (!free_idx.empty()) {
-        h->masked_free_idx.alloc(free_idx.size());
-        h->masked_free_idx.upload(free_idx.data(), free_idx.size(), s);
-        SEM_CUDA(cudaStreamSynchronize(s));   // free_idx leaves scope
-      }
-    }
+    h->nG = ((int64_t)N * h->nelx + 1) * ((int64_t)N * h->nely + 1) * ((int64_t)N * h->nelz + 1);
+    h->gid.alloc(nL);
+    h->imult.alloc(nL);
+    h->mask.alloc(nL);
+    topo_kernel<<<grid_for(nL), 256, 0, s>>>(N, h->nelx, h->nely, h->nelz, h->faces, nL,
+                                            h->gid.ptr, h->imult.ptr, h->mask.ptr);
+    SEM_CHECK_LAUNCH();
+    build_masked_free(h.get(), s);
 
     DevBuf<double> dxi, dwq;
     dxi.alloc(P); dxi.upload(h->xi.data(), P, s);

@@ -1,0 +1,56 @@
+"""Batched solves through the C ABI: problems of different element counts,
+orders and Helmholtz coefficients solved together, each judged by the
+oracle's FP64 residual and against its own single solve."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2107_01243_gb300 as sem
+import seeded_inputs as si
+from tests.helpers import OracleProblem, rel_inf, TWO_PI
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+PROBLEMS = [((3, 2, 2), 5, 0.7), ((2, 2, 2), 7, 3.1), ((4, 3, 2), 3, 0.1), ((1, 1, 2), 9, 9.5),
+            ((3, 3, 3), 7, 1.7), ((3, 3, 2), 1, 2.0)]
+
+
+def _setup():
+    hs, oracles, bs = [], [], []
+    for q, (nel, N, lam) in enumerate(PROBLEMS):
+        h = sem.sem_setup(nel, N, length=(TWO_PI,) * 3, deform=0.1)
+        o = OracleProblem(nel, N, length=(TWO_PI,) * 3, deform=0.1)
+        f = si.eval_fourier(si.fourier_modes(2000 + q), o.x, o.y, o.z)
+        b_ref = o.rhs(f)
+        hs.append(h)
+        oracles.append(o)
+        bs.append((b_ref, torch.from_numpy(b_ref).to(DEV).view(-1)))
+    return hs, oracles, bs
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_matches_oracle_and_single_solves(use_graph):
+    hs, oracles, bs = _setup()
+    batch = sem.sem_batch_create(hs)
+    xs = [torch.empty_like(b) for _, b in bs]
+    lams = [lam for _, _, lam in PROBLEMS]
+    infos = sem.sem_batch_solve(batch, [b for _, b in bs], xs, [1.0] * len(hs), lams, tol=1e-8,
+                                check_every=5, use_graph=use_graph)
+    for q, (h, o, (b_ref, b), x, info) in enumerate(zip(hs, oracles, bs, xs, infos)):
+        assert info["status"] == "SEM_OK", (q, info)
+        xg = x.cpu().numpy().reshape(o.shape)
+        res = o.residual(xg, b_ref, h1=1.0, h2=lams[q])
+        assert res <= 1.05e-8, (q, res)
+        assert abs(res - info["rel_res"]) < 1e-12
+        single = torch.empty_like(b)
+        sem.sem_cg_solve(h, b, single, h1=1.0, h2=lams[q], tol=1e-8,
+                         precision=sem.SEM_SOLVE_MIXED)
+        # both solve to 1e-8; the solutions agree to the conditioning of the problem
+        assert rel_inf(xg, single.cpu().numpy().reshape(o.shape)) < 1e-5
+
+
+def test_batch_rejects_even_order():
+    h = sem.sem_setup((2, 2, 2), 4)
+    with pytest.raises(sem.SemError):
+        sem.sem_batch_create([h])
