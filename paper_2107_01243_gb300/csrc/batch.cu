@@ -3,15 +3,18 @@
 // problem (the solver of cg.cu, arXiv 2107.01243 §2 end and §4, applied to a
 // batch).  Every stage of an inner CG iteration is one launch over all
 // problems:
-//   bax     persistent bulk-copy (TMA) Ax over the flat list of all elements,
-//           each element dispatched to the kernel body of its order
+//   bax     persistent bulk-copy (TMA) Ax over all elements of the problems of
+//           one order (one launch per order present, each with the tile and
+//           shared-memory stages of its own order)
 //   bdssum  index-free gather-scatter over all problems' shared points
 //   bpw, bupdate, bpupd  vector updates over fixed-size chunks; the chunk
 //           partial sums of one problem are reduced, in a fixed order, by the
 //           last chunk block to finish (a ticket per problem)
 // Converged problems are skipped by every stage.  A batch of iterations is
-// captured in a CUDA graph; the host reads one counter of finished problems
-// per graph launch.
+// captured in a CUDA graph; after each graph launch the host reads the
+// problems' states and, for every problem whose inner solve finished, applies
+// the correction, computes the FP64 residual and restarts its inner solve,
+// so problems move through their refinement steps independently.
 #include <cmath>
 #include <memory>
 #include <vector>
@@ -23,8 +26,18 @@
 namespace sem {
 
 constexpr int kMaxBatch = 256;
-constexpr int kBaxThreads = 128;       // >= P^2 for every supported order
 constexpr int kChunk = 16384;          // points per vector work item
+
+// batched Ax tile per order: K elements of P^2 threads each per work item
+template <int P>
+struct BaxCfg {
+  static constexpr int K = (64 / (P * P)) > 1 ? (64 / (P * P)) : 1;
+  static constexpr int THREADS = K * P * P;
+  static constexpr int STAGES = 2;
+  static constexpr size_t smem() {
+    return 128 + (size_t)(STAGES * 8 + 3) * K * P * P * P * sizeof(float);
+  }
+};
 
 __constant__ float c_b32_D[kMaxP + 1][kMaxP * kMaxP];   // FP32 D of every order
 
@@ -42,6 +55,7 @@ struct BProb {
   long long nL;
   CGState* st;
   long long e_off;       // first flat element
+  int cls;               // index of the problem's order class
   long long d_off;       // first flat gather-scatter item
   int v_off, v_cnt;      // vector chunk items
   int gx, gy, gz, nix, niy;
@@ -82,24 +96,31 @@ __device__ __forceinline__ void load_row_f(const float* __restrict__ p, float (&
   }
 }
 
-// One element of order P from a filled stage (u, 6 G, [B]); release() is
-// called by all threads once the stage is no longer read.
+// Up to K elements of order P from a filled stage laid out as
+// [u of the K slots][6 G of the K slots][B of the K slots]; slot s uses
+// threads [s P^2, (s+1) P^2).  release() is called by all threads once the
+// stage is no longer read.
 template <int P, class Rel>
-__device__ __forceinline__ void belem(const float* __restrict__ su, float* sT, float* swr,
-                                      float* swsT, float* __restrict__ we, float h1, float h2,
+__device__ __forceinline__ void belem(const float* __restrict__ stage, int K, int count,
+                                      float* work, float* __restrict__ w0, float h1, float h2,
                                       bool helm, int tid, Rel release) {
   constexpr int P2 = P * P, P3 = P2 * P;
-  const bool act = tid < P2;
-  const int i = tid % P, j = tid / P;
-  const float* sg = su + P3;
-  const float* sb = su + 7 * P3;
+  const int slot = tid / P2, lt = tid - slot * P2;
+  const bool act = slot < count;
+  const int i = lt % P, j = lt / P;
+  const float* su = stage + slot * P3;
+  const float* sg = stage + K * P3 + slot * 6 * P3;
+  const float* sb = stage + 7 * K * P3 + slot * P3;
+  float* sT = work + slot * P3;
+  float* swr = work + K * P3 + slot * P3;
+  float* swsT = work + 2 * K * P3 + slot * P3;
   float uc[P], bk[P], wt[P];
   if (act) {
 #pragma unroll
     for (int k = 0; k < P; ++k) {
-      uc[k] = su[k * P2 + tid];
+      uc[k] = su[k * P2 + lt];
       sT[k * P2 + i * P + j] = uc[k];
-      bk[k] = helm ? sb[k * P2 + tid] : 0.0f;
+      bk[k] = helm ? sb[k * P2 + lt] : 0.0f;
     }
   }
   __syncthreads();
@@ -116,7 +137,7 @@ __device__ __forceinline__ void belem(const float* __restrict__ su, float* sT, f
         us = fmaf(c_b32_D[P][j * P + l], col[l], us);
         ut = fmaf(c_b32_D[P][k * P + l], uc[l], ut);
       }
-      const int q = k * P2 + tid;
+      const int q = k * P2 + lt;
       const float g11 = sg[q], g22 = sg[P3 + q], g33 = sg[2 * P3 + q];
       const float g12 = sg[3 * P3 + q], g13 = sg[4 * P3 + q], g23 = sg[5 * P3 + q];
       swr[k * P2 + j * P + i] = h1 * (g11 * ur + g12 * us + g13 * ut);
@@ -127,6 +148,7 @@ __device__ __forceinline__ void belem(const float* __restrict__ su, float* sT, f
   __syncthreads();
   release();
   if (act) {
+    float* we = w0 + (size_t)slot * P3;
 #pragma unroll
     for (int k = 0; k < P; ++k) {
       float row[P], col[P];
@@ -140,27 +162,33 @@ __device__ __forceinline__ void belem(const float* __restrict__ su, float* sT, f
         acc = fmaf(c_b32_D[P][l * P + k], wt[l], acc);
       }
       if (helm) acc = fmaf(h2 * bk[k], uc[k], acc);
-      we[k * P2 + tid] = acc;
+      we[k * P2 + lt] = acc;
     }
   }
 }
 
-template <int STAGES>
-__global__ void __launch_bounds__(kBaxThreads)
-bax_kernel(const BProb* __restrict__ probs, int nprob, long long Etot, int stage_vals,
-           int work_vals, int* __restrict__ err, uint64_t timeout_ns) {
+// Persistent bulk-copy Ax over every element of the problems of one order P;
+// CTAs of K P^2 threads take work items of K consecutive elements of one
+// problem and keep STAGES items in flight.
+template <int P, int STAGES>
+__global__ void __launch_bounds__(BaxCfg<P>::THREADS)
+bax_kernel(const BProb* __restrict__ probs, const int* __restrict__ cls_prob,
+           const long long* __restrict__ cls_ioff, int ncls, long long Itot,
+           int* __restrict__ err, uint64_t timeout_ns) {
+  constexpr int K = BaxCfg<P>::K, P3 = P * P * P;
+  constexpr int SV = 8 * K * P3;                 // values per stage
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ long long s_off[kMaxBatch];
   __shared__ int s_skip[kMaxBatch];
+  __shared__ int s_prob[kMaxBatch];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   float* stage0 = reinterpret_cast<float*>(smem_raw + 128);
-  float* sT = stage0 + STAGES * stage_vals;
-  float* swr = sT + work_vals;
-  float* swsT = swr + work_vals;
+  float* work = stage0 + STAGES * SV;
   const int tid = threadIdx.x;
-  for (int q = tid; q < nprob; q += blockDim.x) {
-    s_off[q] = probs[q].e_off;
-    s_skip[q] = probs[q].st->done;
+  for (int q = tid; q < ncls; q += blockDim.x) {
+    s_off[q] = cls_ioff[q];
+    s_prob[q] = cls_prob[q];
+    s_skip[q] = probs[cls_prob[q]].st->done;
   }
   if (tid == 0) {
 #pragma unroll
@@ -169,33 +197,39 @@ bax_kernel(const BProb* __restrict__ probs, int nprob, long long Etot, int stage
   }
   __syncthreads();
   const long long G = gridDim.x;
-  // next element of this CTA at or after g whose problem is still running
+  // next item of this CTA at or after g whose problem is still running:
+  // a finished problem is stepped over in one jump
   auto next = [&](long long g) {
-    while (g < Etot && s_skip[find_prob(s_off, nprob, g)]) g += G;
+    while (g < Itot) {
+      const int c = find_prob(s_off, ncls, g);
+      if (!s_skip[c]) break;
+      const long long end = c + 1 < ncls ? s_off[c + 1] : Itot;
+      g += (end - g + G - 1) / G * G;
+    }
     return g;
   };
   auto issue = [&](long long g, int s) {
-    const int pi = find_prob(s_off, nprob, g);
-    const BProb& pr = probs[pi];
-    const long long e = g - pr.e_off;
-    const int P3 = pr.P * pr.P * pr.P;
-    const uint32_t FB = (uint32_t)P3 * 4u;
+    const int c = find_prob(s_off, ncls, g);
+    const BProb& pr = probs[s_prob[c]];
+    const long long e0 = (g - s_off[c]) * K;
+    const int cnt = (int)min((long long)K, (long long)pr.E - e0);
+    const uint32_t FB = (uint32_t)(P3 * cnt) * 4u;
     const bool helm = pr.h2 != 0.0f;
-    float* dst = stage0 + s * stage_vals;
+    float* dst = stage0 + s * SV;
     mbar_arrive_expect_tx(&bar[s], (helm ? 8u : 7u) * FB);
-    bulk_g2s(dst, pr.p + e * P3, FB, &bar[s]);
-    bulk_g2s(dst + P3, pr.G + e * 6 * P3, 6 * FB, &bar[s]);
-    if (helm) bulk_g2s(dst + 7 * P3, pr.B + e * P3, FB, &bar[s]);
+    bulk_g2s(dst, pr.p + e0 * P3, FB, &bar[s]);
+    bulk_g2s(dst + K * P3, pr.G + e0 * 6 * P3, 6 * FB, &bar[s]);
+    if (helm) bulk_g2s(dst + 7 * K * P3, pr.B + e0 * P3, FB, &bar[s]);
   };
-  long long ahead = next(blockIdx.x);    // thread 0: next element to prefetch
+  long long ahead = next(blockIdx.x);    // thread 0: next item to prefetch
   if (tid == 0) {
-    for (int s = 0; s < STAGES && ahead < Etot; ++s) {
+    for (int s = 0; s < STAGES && ahead < Itot; ++s) {
       issue(ahead, s);
       ahead = next(ahead + G);
     }
   }
   int n = 0;
-  for (long long g = next(blockIdx.x); g < Etot; g = next(g + G), ++n) {
+  for (long long g = next(blockIdx.x); g < Itot; g = next(g + G), ++n) {
     const int s = n % STAGES;
     const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)(n / STAGES) & 1u, err, timeout_ns);
     if (__syncthreads_or(!ok)) {
@@ -205,28 +239,19 @@ bax_kernel(const BProb* __restrict__ probs, int nprob, long long Etot, int stage
                             timeout_ns);
       return;
     }
-    const int pi = find_prob(s_off, nprob, g);
-    const BProb& pr = probs[pi];
-    const long long e = g - pr.e_off;
-    const float* su = stage0 + s * stage_vals;
-    const bool helm = pr.h2 != 0.0f;
+    const int c = find_prob(s_off, ncls, g);
+    const BProb& pr = probs[s_prob[c]];
+    const long long e0 = (g - s_off[c]) * K;
+    const int cnt = (int)min((long long)K, (long long)pr.E - e0);
     auto release = [&]() {
-      if (tid == 0 && ahead < Etot) {
+      if (tid == 0 && ahead < Itot) {
         fence_proxy_async_smem();
         issue(ahead, s);
         ahead = next(ahead + G);
       }
     };
-    const int P3 = pr.P * pr.P * pr.P;
-    float* we = pr.w + e * P3;
-    switch (pr.P) {
-      case 2: belem<2>(su, sT, swr, swsT, we, pr.h1, pr.h2, helm, tid, release); break;
-      case 4: belem<4>(su, sT, swr, swsT, we, pr.h1, pr.h2, helm, tid, release); break;
-      case 6: belem<6>(su, sT, swr, swsT, we, pr.h1, pr.h2, helm, tid, release); break;
-      case 8: belem<8>(su, sT, swr, swsT, we, pr.h1, pr.h2, helm, tid, release); break;
-      case 10: belem<10>(su, sT, swr, swsT, we, pr.h1, pr.h2, helm, tid, release); break;
-      default: break;
-    }
+    belem<P>(stage0 + s * SV, K, cnt, work, pr.w + e0 * P3, pr.h1, pr.h2, pr.h2 != 0.0f, tid,
+             release);
   }
 }
 
@@ -253,11 +278,19 @@ __device__ __forceinline__ int bfree(int m, int nfree, int g, const BProb& b) {
 __global__ void __launch_bounds__(256)
 bdssum_kernel(const BProb* __restrict__ probs, const long long* __restrict__ d_off, int nprob,
               long long Dtot) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Dtot;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int pi = find_prob(d_off, nprob, t);
+  __shared__ long long s_off[kMaxBatch];
+  for (int q = threadIdx.x; q < nprob; q += blockDim.x) s_off[q] = d_off[q];
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Dtot; t += stride) {
+    const int pi = find_prob(s_off, nprob, t);
     const BProb& b = probs[pi];
-    if (b.st->done) continue;
+    if (b.st->done) {
+      // step over the rest of this problem's items in one jump
+      const long long end = pi + 1 < nprob ? s_off[pi + 1] : Dtot;
+      t += (end - t - 1) / stride * stride;
+      continue;
+    }
     uint32_t r = (uint32_t)(t - b.d_off);
     int ix, iy, iz;
     if (r < b.nSX) {
@@ -358,11 +391,11 @@ __device__ __forceinline__ bool item_sum(double (&v)[NV], double* partials, int 
   return true;
 }
 
+// Starts the inner solve of the problems owning items [item0, item0 + count).
 __global__ void __launch_bounds__(256)
-binit_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob, int nitems,
-             double* partials, unsigned* tickets, const int* __restrict__ active, double tol,
-             int maxit, int* ndone) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+binit_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob, int item0,
+             int count, int nitems, double* partials, unsigned* tickets, double tol, int maxit) {
+  for (int it = item0 + blockIdx.x; it < item0 + count; it += gridDim.x) {
     const int pi = item_prob[it];
     const BProb& b = probs[pi];
     const long long lo = (long long)(it - b.v_off) * kChunk;
@@ -389,8 +422,7 @@ binit_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob,
       st->status = SEM_OK;
       st->maxit = maxit;
       st->alpha = st->beta = 0.0;
-      st->done = (!active[pi] || tot[1] <= st->tol2 || tot[1] == 0.0 || maxit <= 0) ? 1 : 0;
-      if (st->done) atomicAdd(ndone, 1);
+      st->done = (tot[1] <= st->tol2 || tot[1] == 0.0 || maxit <= 0) ? 1 : 0;
     }
     __syncthreads();
   }
@@ -398,16 +430,26 @@ binit_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob,
 
 __global__ void __launch_bounds__(256)
 bpw_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob, int nitems,
-           double* partials, unsigned* tickets, int* ndone) {
+           double* partials, unsigned* tickets) {
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int pi = item_prob[it];
     const BProb& b = probs[pi];
     if (b.st->done) continue;
     const long long lo = (long long)(it - b.v_off) * kChunk;
     const long long hi = min(lo + kChunk, b.nL);
+    const float4* p4 = reinterpret_cast<const float4*>(b.p + lo);
+    const float4* w4 = reinterpret_cast<const float4*>(b.w + lo);
+    const float4* m4 = reinterpret_cast<const float4*>(b.imult + lo);
+    const int n4 = (int)((hi - lo) >> 2);
     KahanF pw;
-    for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x)
-      pw.add(__fmul_rn(__fmul_rn(b.p[q], b.w[q]), b.imult[q]));
+#pragma unroll 4
+    for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+      const float4 p = p4[q], w = w4[q], m = m4[q];
+      pw.add(__fmul_rn(__fmul_rn(p.x, w.x), m.x));
+      pw.add(__fmul_rn(__fmul_rn(p.y, w.y), m.y));
+      pw.add(__fmul_rn(__fmul_rn(p.z, w.z), m.z));
+      pw.add(__fmul_rn(__fmul_rn(p.w, w.w), m.w));
+    }
     double v[1] = {pw.value()}, tot[1];
     if (item_sum<1>(v, partials, it, b.v_off, b.v_cnt, &tickets[pi], tot, nitems) &&
         threadIdx.x == 0) {
@@ -416,7 +458,6 @@ bpw_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob, i
       if (!(tot[0] > 0.0)) {
         st->status = SEM_ERR_BREAKDOWN;
         st->done = 1;
-        atomicAdd(ndone, 1);
       } else {
         st->alpha = st->rz / tot[0];
       }
@@ -425,9 +466,18 @@ bpw_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob, i
   }
 }
 
+__device__ __forceinline__ void upd1(float& x, float& r, float p, float w, float d, float m,
+                                     float alpha, KahanF& rz, KahanF& rr) {
+  x += alpha * p;
+  r -= alpha * w;
+  const float z = d * r;
+  rz.add(__fmul_rn(__fmul_rn(r, z), m));
+  rr.add(__fmul_rn(__fmul_rn(r, r), m));
+}
+
 __global__ void __launch_bounds__(256)
 bupdate_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob, int nitems,
-               double* partials, unsigned* tickets, int* ndone) {
+               double* partials, unsigned* tickets) {
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int pi = item_prob[it];
     const BProb& b = probs[pi];
@@ -435,15 +485,24 @@ bupdate_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_pro
     const float alpha = (float)b.st->alpha;
     const long long lo = (long long)(it - b.v_off) * kChunk;
     const long long hi = min(lo + kChunk, b.nL);
+    float4* x4 = reinterpret_cast<float4*>(b.x + lo);
+    float4* r4 = reinterpret_cast<float4*>(b.r + lo);
+    const float4* p4 = reinterpret_cast<const float4*>(b.p + lo);
+    const float4* w4 = reinterpret_cast<const float4*>(b.w + lo);
+    const float4* d4 = reinterpret_cast<const float4*>(b.dinv + lo);
+    const float4* m4 = reinterpret_cast<const float4*>(b.imult + lo);
+    const int n4 = (int)((hi - lo) >> 2);
     KahanF rz, rr;
-    for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) {
-      b.x[q] += alpha * b.p[q];
-      const float r = b.r[q] - alpha * b.w[q];
-      b.r[q] = r;
-      const float z = b.dinv[q] * r;
-      const float im = b.imult[q];
-      rz.add(__fmul_rn(__fmul_rn(r, z), im));
-      rr.add(__fmul_rn(__fmul_rn(r, r), im));
+#pragma unroll 2
+    for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+      float4 x = x4[q], r = r4[q];
+      const float4 p = p4[q], w = w4[q], d = d4[q], m = m4[q];
+      upd1(x.x, r.x, p.x, w.x, d.x, m.x, alpha, rz, rr);
+      upd1(x.y, r.y, p.y, w.y, d.y, m.y, alpha, rz, rr);
+      upd1(x.z, r.z, p.z, w.z, d.z, m.z, alpha, rz, rr);
+      upd1(x.w, r.w, p.w, w.w, d.w, m.w, alpha, rz, rr);
+      x4[q] = x;
+      r4[q] = r;
     }
     double v[2] = {rz.value(), rr.value()}, tot[2];
     if (item_sum<2>(v, partials, it, b.v_off, b.v_cnt, &tickets[pi], tot, nitems) &&
@@ -463,7 +522,6 @@ bupdate_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_pro
         st->beta = tot[0] / st->rz;
         st->rz = tot[0];
       }
-      if (st->done) atomicAdd(ndone, 1);
     }
     __syncthreads();
   }
@@ -478,8 +536,20 @@ bpupd_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob,
     const float beta = (float)b.st->beta;
     const long long lo = (long long)(it - b.v_off) * kChunk;
     const long long hi = min(lo + kChunk, b.nL);
-    for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x)
-      b.p[q] = b.dinv[q] * b.r[q] + beta * b.p[q];
+    float4* p4 = reinterpret_cast<float4*>(b.p + lo);
+    const float4* r4 = reinterpret_cast<const float4*>(b.r + lo);
+    const float4* d4 = reinterpret_cast<const float4*>(b.dinv + lo);
+    const int n4 = (int)((hi - lo) >> 2);
+#pragma unroll 4
+    for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+      float4 p = p4[q];
+      const float4 r = r4[q], d = d4[q];
+      p.x = d.x * r.x + beta * p.x;
+      p.y = d.y * r.y + beta * p.y;
+      p.z = d.z * r.z + beta * p.z;
+      p.w = d.w * r.w + beta * p.w;
+      p4[q] = p;
+    }
   }
 }
 
@@ -496,12 +566,14 @@ struct sem_batch {
   DevBuf<double> partials;
   DevBuf<unsigned> tickets;
   DevBuf<CGState> states;                // inner solve state per problem
-  DevBuf<int> active;
-  DevBuf<int> ndone;
   long long Etot = 0, Dtot = 0;
-  int nitems = 0, maxP = 0, stage_vals = 0, work_vals = 0;
-  int bax_grid = 0;
-  size_t bax_smem = 0;
+  // per order class (P = 2, 4, 6, 8, 10): problems and work-item offsets
+  int ncls[kMaxP + 1] = {};
+  long long Icls[kMaxP + 1] = {};
+  DevBuf<int> cls_prob[kMaxP + 1];
+  DevBuf<long long> cls_ioff[kMaxP + 1];
+  int bax_grid_cls[kMaxP + 1] = {};
+  int nitems = 0, maxP = 0;
   cudaStream_t stream = nullptr;
 };
 
@@ -516,22 +588,48 @@ static void batch_upload_d(const sem_handle* h) {
   done[h->P] = true;
 }
 
+template <int P>
+static int bax_occupancy() {
+  using C = BaxCfg<P>;
+  auto kern = bax_kernel<P, C::STAGES>;
+  SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)C::smem()));
+  int occ = 0;
+  SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::THREADS, C::smem()));
+  return occ;
+}
+
+template <int P>
+static void launch_bax(sem_batch* bt, cudaStream_t s) {
+  using C = BaxCfg<P>;
+  bax_kernel<P, C::STAGES><<<bt->bax_grid_cls[P], C::THREADS, C::smem(), s>>>(
+      bt->probs.ptr, bt->cls_prob[P].ptr, bt->cls_ioff[P].ptr, bt->ncls[P], bt->Icls[P],
+      bt->hs[0]->dev_err.ptr, kWaitTimeoutNs);
+  SEM_CHECK_LAUNCH();
+}
+
 // one inner iteration over the batch (captured into a graph)
 static void batch_iteration(sem_batch* bt, cudaStream_t s) {
   const int n = (int)bt->hs.size();
-  bax_kernel<2><<<bt->bax_grid, kBaxThreads, bt->bax_smem, s>>>(
-      bt->probs.ptr, n, bt->Etot, bt->stage_vals, bt->work_vals, bt->hs[0]->dev_err.ptr,
-      kWaitTimeoutNs);
-  SEM_CHECK_LAUNCH();
+  for (int P = 2; P <= kMaxP; P += 2) {
+    if (!bt->ncls[P]) continue;
+    switch (P) {
+      case 2: launch_bax<2>(bt, s); break;
+      case 4: launch_bax<4>(bt, s); break;
+      case 6: launch_bax<6>(bt, s); break;
+      case 8: launch_bax<8>(bt, s); break;
+      default: launch_bax<10>(bt, s); break;
+    }
+  }
   const int dblocks = (int)std::min<long long>((bt->Dtot + 255) / 256, 32LL * kNumSMs);
   bdssum_kernel<<<dblocks, 256, 0, s>>>(bt->probs.ptr, bt->d_off.ptr, n, bt->Dtot);
   SEM_CHECK_LAUNCH();
   const int vblocks = std::min(bt->nitems, 8 * kNumSMs);
   bpw_kernel<<<vblocks, 256, 0, s>>>(bt->probs.ptr, bt->item_prob.ptr, bt->nitems,
-                                     bt->partials.ptr, bt->tickets.ptr, bt->ndone.ptr);
+                                     bt->partials.ptr, bt->tickets.ptr);
   SEM_CHECK_LAUNCH();
   bupdate_kernel<<<vblocks, 256, 0, s>>>(bt->probs.ptr, bt->item_prob.ptr, bt->nitems,
-                                         bt->partials.ptr, bt->tickets.ptr, bt->ndone.ptr);
+                                         bt->partials.ptr, bt->tickets.ptr);
   SEM_CHECK_LAUNCH();
   bpupd_kernel<<<vblocks, 256, 0, s>>>(bt->probs.ptr, bt->item_prob.ptr, bt->nitems);
   SEM_CHECK_LAUNCH();
@@ -554,6 +652,7 @@ extern "C" sem_status sem_batch_create(sem_handle* const* handles, int n, sem_ba
       SEM_REQUIRE(h, "sem_batch_create: null handle");
       SEM_REQUIRE(h->f32.G.ptr, "sem_batch_create: every handle needs FP32 geometry");
       SEM_REQUIRE(h->P % 2 == 0, "sem_batch_create: orders must be odd (even points per direction)");
+      SEM_REQUIRE(h->nL % 4 == 0, "sem_batch_create: local point count must be a multiple of 4");
       batch_upload_d(h);
       BProb b{};
       b.G = h->f32.G.ptr;
@@ -597,19 +696,38 @@ extern "C" sem_status sem_batch_create(sem_handle* const* handles, int n, sem_ba
     bt->Etot = eoff;
     bt->Dtot = doff;
     bt->nitems = voff;
-    const int P3 = bt->maxP * bt->maxP * bt->maxP;
-    bt->stage_vals = 8 * P3;
-    bt->work_vals = P3;
-    bt->bax_smem = 128 + (size_t)(2 * bt->stage_vals + 3 * bt->work_vals) * sizeof(float);
-    auto kern = bax_kernel<2>;
-    SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)bt->bax_smem));
-    int occ = 0;
-    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBaxThreads, bt->bax_smem));
     int nsm = 0, dev = 0;
     SEM_CUDA(cudaGetDevice(&dev));
     SEM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    bt->bax_grid = (int)std::min<long long>(bt->Etot, (long long)std::max(1, occ) * nsm);
+    for (int P = 2; P <= kMaxP; P += 2) {
+      std::vector<int> ids;
+      std::vector<long long> ioff;
+      long long items = 0;
+      const int K = P == 2 ? BaxCfg<2>::K : P == 4 ? BaxCfg<4>::K : P == 6 ? BaxCfg<6>::K
+                  : P == 8 ? BaxCfg<8>::K : BaxCfg<10>::K;
+      for (int p = 0; p < n; ++p)
+        if (bt->hp[p].P == P) {
+          ids.push_back(p);
+          ioff.push_back(items);
+          items += (bt->hp[p].E + K - 1) / K;
+        }
+      bt->ncls[P] = (int)ids.size();
+      bt->Icls[P] = items;
+      if (ids.empty()) continue;
+      bt->cls_prob[P].alloc(ids.size());
+      bt->cls_prob[P].upload(ids.data(), ids.size(), nullptr);
+      bt->cls_ioff[P].alloc(ioff.size());
+      bt->cls_ioff[P].upload(ioff.data(), ioff.size(), nullptr);
+      int occ = 0;
+      switch (P) {
+        case 2: occ = bax_occupancy<2>(); break;
+        case 4: occ = bax_occupancy<4>(); break;
+        case 6: occ = bax_occupancy<6>(); break;
+        case 8: occ = bax_occupancy<8>(); break;
+        default: occ = bax_occupancy<10>(); break;
+      }
+      bt->bax_grid_cls[P] = (int)std::min<long long>(items, (long long)std::max(1, occ) * nsm);
+    }
     bt->d_off.alloc(n);
     bt->d_off.upload(d_off.data(), n, nullptr);
     bt->item_prob.alloc(item_prob.size());
@@ -619,8 +737,6 @@ extern "C" sem_status sem_batch_create(sem_handle* const* handles, int n, sem_ba
     SEM_CUDA(cudaMemset(bt->tickets.ptr, 0, n * sizeof(unsigned)));
     bt->states.alloc(n);
     SEM_CUDA(cudaMemset(bt->states.ptr, 0, n * sizeof(CGState)));
-    bt->active.alloc(n);
-    bt->ndone.alloc(1);
     bt->probs.alloc(n);
     SEM_CUDA(cudaDeviceSynchronize());
     *out = bt.release();
@@ -679,7 +795,11 @@ extern "C" sem_status sem_batch_solve(sem_batch* bt, const double* const* b_L,
       outer_norm_b(h, b_L[p], own);
     }
     bt->probs.upload(bt->hp.data(), n, own);
-    std::vector<int> active(n, 1), iters(n, 0), outer(n, 0), status(n, SEM_ERR_NOCONV);
+    // Each problem moves on its own: FP64 residual -> (converged | FP32 inner
+    // solve in the batch) -> correction -> FP64 residual ...  The graph of
+    // batched iterations skips problems whose inner solve is not running.
+    enum { RUNNING = 0, FINISHED = 1 };
+    std::vector<int> phase(n, RUNNING), iters(n, 0), outer(n, 0), status(n, SEM_ERR_NOCONV);
     std::vector<double> rel(n, 0.0);
     const int batch_it = std::max(1, o.check_every);
     cudaGraphExec_t exec = nullptr;
@@ -699,64 +819,63 @@ extern "C" sem_status sem_batch_solve(sem_batch* bt, const double* const* b_L,
       SEM_CUDA(e);
       cleanup.ex = exec;
     }
-    int total_inner = 0;
-    for (int step = 0;; ++step) {
-      // FP64 residual of every running problem
-      int nactive = 0;
-      for (int p = 0; p < n; ++p) {
-        if (!active[p]) continue;
-        sem_handle* h = bt->hs[p];
-        outer_residual(h, b_L[p], x_L[p], po[p], own);
-        const CGState hs0 = state_to_host(h->state.ptr, own, h->dev_err.ptr);
-        rel[p] = hs0.bb > 0 ? std::sqrt(hs0.rr / hs0.bb) : 0.0;
-        if (!(rel[p] == rel[p])) { status[p] = SEM_ERR_BREAKDOWN; active[p] = 0; continue; }
-        if (rel[p] <= o.tol) { status[p] = SEM_OK; active[p] = 0; continue; }
-        if (outer[p] >= o.max_outer || iters[p] >= o.maxit) { active[p] = 0; continue; }
-        ++nactive;
-      }
-      if (nactive == 0) break;
-      // batched FP32 inner PCG of the running problems
-      bt->active.upload(active.data(), n, own);
-      SEM_CUDA(cudaMemsetAsync(bt->ndone.ptr, 0, sizeof(int), own));
-      SEM_CUDA(cudaMemsetAsync(bt->tickets.ptr, 0, n * sizeof(unsigned), own));
-      binit_kernel<<<std::min(bt->nitems, 8 * kNumSMs), 256, 0, own>>>(
-          bt->probs.ptr, bt->item_prob.ptr, bt->nitems, bt->partials.ptr, bt->tickets.ptr,
-          bt->active.ptr, o.inner_tol, o.maxit, bt->ndone.ptr);
-      SEM_CHECK_LAUNCH();
-      int ndone = 0;
-      for (int guard = 0;; ++guard) {
-        SEM_CUDA(cudaMemcpyAsync(&ndone, bt->ndone.ptr, sizeof(int), cudaMemcpyDeviceToHost, own));
+    SEM_CUDA(cudaMemsetAsync(bt->tickets.ptr, 0, n * sizeof(unsigned), own));
+    // FP64 residual of problem p; starts its next inner solve unless it is finished
+    auto refine = [&](int p) {
+      sem_handle* h = bt->hs[p];
+      outer_residual(h, b_L[p], x_L[p], po[p], own);
+      const CGState hs0 = state_to_host(h->state.ptr, own, h->dev_err.ptr);
+      rel[p] = hs0.bb > 0 ? std::sqrt(hs0.rr / hs0.bb) : 0.0;
+      if (!(rel[p] == rel[p])) { status[p] = SEM_ERR_BREAKDOWN; phase[p] = FINISHED; }
+      else if (rel[p] <= o.tol) { status[p] = SEM_OK; phase[p] = FINISHED; }
+      else if (outer[p] >= o.max_outer || iters[p] >= o.maxit) { phase[p] = FINISHED; }
+      if (phase[p] == FINISHED) {
+        CGState fin{};
+        fin.done = 1;
+        SEM_CUDA(cudaMemcpyAsync(bt->states.ptr + p, &fin, sizeof(CGState),
+                                 cudaMemcpyHostToDevice, own));
         SEM_CUDA(cudaStreamSynchronize(own));
-        if (ndone >= n) break;
-        if (exec) SEM_CUDA(cudaGraphLaunch(exec, own));
-        else
-          for (int c = 0; c < batch_it; ++c) batch_iteration(bt, own);
-        if (guard > 1000000) throw Error(SEM_ERR_NOCONV, "sem_batch_solve: inner loop guard");
+        return;
       }
-      std::vector<CGState> st(n);
+      const BProb& b = bt->hp[p];
+      binit_kernel<<<std::min(b.v_cnt, 4 * kNumSMs), 256, 0, own>>>(
+          bt->probs.ptr, bt->item_prob.ptr, b.v_off, b.v_cnt, bt->nitems, bt->partials.ptr,
+          bt->tickets.ptr, o.inner_tol, std::max(1, o.maxit - iters[p]));
+      SEM_CHECK_LAUNCH();
+    };
+    for (int p = 0; p < n; ++p) refine(p);
+    std::vector<CGState> st(n);
+    for (long guard = 0;; ++guard) {
+      bool any = false;
+      for (int p = 0; p < n; ++p) any = any || phase[p] == RUNNING;
+      if (!any) break;
+      if (guard > 10000000L) throw Error(SEM_ERR_NOCONV, "sem_batch_solve: iteration guard");
+      if (exec) SEM_CUDA(cudaGraphLaunch(exec, own));
+      else
+        for (int c = 0; c < batch_it; ++c) batch_iteration(bt, own);
       SEM_CUDA(cudaMemcpyAsync(st.data(), bt->states.ptr, n * sizeof(CGState),
                                cudaMemcpyDeviceToHost, own));
       int herr = 0;
-      SEM_CUDA(cudaMemcpyAsync(&herr, bt->hs[0]->dev_err.ptr, sizeof(int), cudaMemcpyDeviceToHost,
-                               own));
+      SEM_CUDA(cudaMemcpyAsync(&herr, bt->hs[0]->dev_err.ptr, sizeof(int),
+                               cudaMemcpyDeviceToHost, own));
       SEM_CUDA(cudaStreamSynchronize(own));
       if (herr) {
         SEM_CUDA(cudaMemsetAsync(bt->hs[0]->dev_err.ptr, 0, sizeof(int), own));
         throw Error(SEM_ERR_TIMEOUT, "sem_batch_solve: a bounded device wait timed out");
       }
       for (int p = 0; p < n; ++p) {
-        if (!active[p]) continue;
+        if (phase[p] != RUNNING || !st[p].done) continue;
+        // inner solve of p finished: correction, then the next refinement step
         iters[p] += st[p].iter;
-        total_inner += st[p].iter;
         ++outer[p];
         if (st[p].status == SEM_ERR_BREAKDOWN && st[p].iter == 0) {
           status[p] = SEM_ERR_BREAKDOWN;
-          active[p] = 0;
+          phase[p] = FINISHED;
           continue;
         }
         outer_update(bt->hs[p], x_L[p], own);
+        refine(p);
       }
-      (void)step;
     }
     SEM_CUDA(cudaStreamSynchronize(own));
     for (int p = 0; p < n; ++p) {
@@ -767,6 +886,5 @@ extern "C" sem_status sem_batch_solve(sem_batch* bt, const double* const* b_L,
         infos[p].status = status[p];
       }
     }
-    (void)total_inner;
   });
 }
