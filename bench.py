@@ -182,6 +182,7 @@ def main():
 
     cfg = WORKLOAD
     h = sem.sem_setup(cfg["nel"], cfg["N"], length=cfg["length"], deform=cfg["deform"])
+    tiles = sem.sem_autotune(h)
     n = h.n_local
     u_host = torch.from_numpy(si.uniform(n, cfg["seed"])).pin_memory()
     u = u_host.to(dev)
@@ -285,6 +286,7 @@ def main():
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": 2 * K,
+        "autotune": tiles,
         "clocks": clk.summary(),
     }
     del w, w32, u32
@@ -362,6 +364,7 @@ def run_batch(sem, torch, dev, n_problems=64):
 def run_solves(sem, torch, dev):
     cfg = SOLVE
     h = sem.sem_setup(cfg["nel"], cfg["N"], length=cfg["length"], deform=cfg["deform"])
+    sem.sem_autotune(h)
     n = h.n_local
     xs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(3)]
     sem.sem_get_field(h, sem.SEM_FIELD_X, xs[0])

@@ -171,6 +171,33 @@ sem_status sem_ax(sem_handle* h, const void* u_L, void* w_L, double h1, double h
  */
 sem_status sem_set_f64_kernel(sem_handle* h, int kind);
 
+/* Tile chosen by sem_autotune (times in ms per Ax launch, -1 if not timed). */
+typedef struct {
+  int ax32_kernel;          /* FP32 Ax: 0 bulk-copy (TMA) pipeline, 1 global-load kernel */
+  int ax32_stages;          /* bulk-copy stages in flight per CTA (1..3) */
+  int ax32_elems_per_cta;   /* elements per CTA of the bulk-copy kernel (1 or 2) */
+  int f64_stages;           /* double-float FP64 Ax: bulk-copy stages (1 or 2) */
+  double ax32_ms, ax64_ms;  /* best measured times */
+  int from_cache;           /* 1 if taken from the process or file cache */
+} sem_tuning;
+
+/*
+ * sem_autotune -- time every candidate tile of the FP32 Ax (global loads, or
+ * bulk copies with 1-3 stages and 1-2 elements per CTA) and of the
+ * double-float FP64 Ax (1-2 stages) on this handle's geometry and keep the
+ * fastest for all later calls on the handle.  Choices are cached per (order,
+ * element-count bucket) for the process and, if the environment variable
+ * SEM_AUTOTUNE_CACHE names a file, in that file.  Synchronises the stream;
+ * allocates two scratch vectors while timing.  *out (may be NULL) receives
+ * the choice.
+ */
+sem_status sem_autotune(sem_handle* h, void* stream, sem_tuning* out);
+
+/* sem_set_tuning -- apply a tile choice (fields as in sem_tuning; the times
+ * and from_cache are ignored).  SEM_ERR_ARG for a combination that does not
+ * exist (stages 1-3 with 1 element per CTA, or 1-2 with 2; f64_stages 1-2). */
+sem_status sem_set_tuning(sem_handle* h, const sem_tuning* t);
+
 /*
  * sem_dssum -- in place w_L <- QQ^T w_L: every local copy of a global point
  * receives the sum of all its copies, summed in increasing local index

@@ -17,6 +17,7 @@ from ._lib import (SemError, SEM_F64, SEM_F32, SEM_PREC_F64, SEM_PREC_F32, SEM_S
 from .api import (Handle, sem_setup, sem_destroy, sem_get_sizes, sem_get_field, sem_ax,
                   sem_dssum, sem_rhs, sem_cg_solve, sem_helmholtz_grad, sem_apply_host, sem_dot, sem_sync,
                   sem_selftest_timeout, sem_set_f64_kernel, sem_set_dssum_kernel,
+                  sem_autotune, sem_set_tuning,
                   sem_dot_noalloc, Batch, sem_batch_create, sem_batch_solve,
                   sem_batch_destroy)
 from .autograd import HelmholtzSolve, helmholtz_solve

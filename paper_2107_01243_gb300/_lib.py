@@ -49,6 +49,13 @@ class SolveOpts(ctypes.Structure):
                 ("x0_is_zero", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("ax32_kernel", ctypes.c_int), ("ax32_stages", ctypes.c_int),
+                ("ax32_elems_per_cta", ctypes.c_int), ("f64_stages", ctypes.c_int),
+                ("ax32_ms", ctypes.c_double), ("ax64_ms", ctypes.c_double),
+                ("from_cache", ctypes.c_int)]
+
+
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
                 ("rel_res", ctypes.c_double), ("status", ctypes.c_int)]
@@ -81,6 +88,8 @@ SIGNATURES = {
                                        ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]),
     "sem_batch_destroy": (ctypes.c_int, [_P]),
     "sem_sync": (ctypes.c_int, [_P, _P]),
+    "sem_autotune": (ctypes.c_int, [_P, _P, ctypes.c_void_p]),
+    "sem_set_tuning": (ctypes.c_int, [_P, ctypes.c_void_p]),
     "sem_set_f64_kernel": (ctypes.c_int, [_P, ctypes.c_int]),
     "sem_set_dssum_kernel": (ctypes.c_int, [_P, ctypes.c_int]),
     "sem_selftest_timeout": (ctypes.c_int, [_P, ctypes.c_double, _P]),

@@ -197,6 +197,25 @@ def sem_set_dssum_kernel(h, kind):
     check(_lib.load().sem_set_dssum_kernel(h.ptr, int(kind)))
 
 
+def sem_autotune(h, stream=None):
+    """Time the candidate Ax tiles on this handle and keep the fastest; returns the choice."""
+    t = _lib.Tuning()
+    check(_lib.load().sem_autotune(h.ptr, _stream(stream), ctypes.byref(t)))
+    return dict(ax32_kernel="global-load" if t.ax32_kernel else "bulk-copy",
+                ax32_stages=t.ax32_stages, ax32_elems_per_cta=t.ax32_elems_per_cta,
+                f64_stages=t.f64_stages, ax32_ms=t.ax32_ms, ax64_ms=t.ax64_ms,
+                from_cache=bool(t.from_cache))
+
+
+def sem_set_tuning(h, ax32_kernel="bulk-copy", ax32_stages=2, ax32_elems_per_cta=1,
+                   f64_stages=1):
+    """Pin a tile choice (the same fields sem_autotune returns)."""
+    t = _lib.Tuning()
+    t.ax32_kernel = 1 if ax32_kernel == "global-load" else 0
+    t.ax32_stages, t.ax32_elems_per_cta, t.f64_stages = ax32_stages, ax32_elems_per_cta, f64_stages
+    check(_lib.load().sem_set_tuning(h.ptr, ctypes.byref(t)))
+
+
 def sem_sync(h, stream=None):
     """Synchronise and raise SemError(SEM_ERR_TIMEOUT) if a device wait gave up."""
     check(_lib.load().sem_sync(h.ptr, _stream(stream)))

@@ -147,7 +147,7 @@ template <class T>
 void launch_ax(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
                const T* h1f, const CGState* st, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
-    if (tma_ax_supported<float>(h, u, w, h1f)) {
+    if (!h->tune.ax32_ldg && tma_ax_supported<float>(h, u, w, h1f)) {
       launch_ax_tma<float>(h, op, u, w, h1, h2, h1f, st, h->dev_err.ptr, kWaitTimeoutNs, 0u, s);
       return;
     }

@@ -325,9 +325,18 @@ bool df_ax_supported(const sem_handle* h, const void* u, const void* w, const vo
 void launch_ax_df(const sem_handle* h, const double* u, double* w, double h1, double h2,
                   const CGState* st, cudaStream_t s) {
   switch (h->P) {
-    case 6: launch_df_p<6, 1>(h, u, w, h1, h2, st, s); break;
-    case 8: launch_df_p<8, 1>(h, u, w, h1, h2, st, s); break;
-    case 10: launch_df_p<10, 1>(h, u, w, h1, h2, st, s); break;
+    case 6:
+      if (h->tune.df_variant) launch_df_p<6, 2>(h, u, w, h1, h2, st, s);
+      else launch_df_p<6, 1>(h, u, w, h1, h2, st, s);
+      break;
+    case 8:
+      if (h->tune.df_variant) launch_df_p<8, 2>(h, u, w, h1, h2, st, s);
+      else launch_df_p<8, 1>(h, u, w, h1, h2, st, s);
+      break;
+    case 10:
+      if (h->tune.df_variant) launch_df_p<10, 2>(h, u, w, h1, h2, st, s);
+      else launch_df_p<10, 1>(h, u, w, h1, h2, st, s);
+      break;
     default: throw Error(SEM_ERR_ARG, "launch_ax_df: unsupported order");
   }
 }

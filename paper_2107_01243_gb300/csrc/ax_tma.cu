@@ -51,8 +51,8 @@ __device__ __forceinline__ void load_row(const T* __restrict__ p, T (&v)[P]) {
   }
 }
 
-template <int P, class T, int STAGES>
-__global__ void __launch_bounds__(P * P)
+template <int P, class T, int STAGES, int K>
+__global__ void __launch_bounds__(K * P * P)
 ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ G,
               const T* __restrict__ B, const T* __restrict__ h1f, T h1, T h2, DMat<P, T> D,
               int E, const CGState* __restrict__ st, int* __restrict__ err, uint64_t timeout_ns,
@@ -66,11 +66,14 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
   const bool helm = h2 != T(0);
   const bool var = h1f != nullptr;
   const int nf = 7 + (helm ? 1 : 0) + (var ? 1 : 0);
-  const int SE = nf * P3;                              // stage size in values
-  T* sT = stage0 + STAGES * SE;
-  T* swr = sT + P3;
-  T* swsT = swr + P3;
-  const int tid = threadIdx.x, i = tid % P, j = tid / P;
+  const int SE = nf * K * P3;                          // stage size in values
+  const int tid = threadIdx.x;
+  const int slot = tid / P2, lt = tid - slot * P2;     // element slot, thread within it
+  const int i = lt % P, j = lt / P;
+  T* sT = stage0 + STAGES * SE + slot * P3;
+  T* swr = stage0 + STAGES * SE + K * P3 + slot * P3;
+  T* swsT = stage0 + STAGES * SE + 2 * K * P3 + slot * P3;
+  const int nitems = (E + K - 1) / K;
 
   T Di[P], Dj[P], DiT[P], DjT[P];
 #pragma unroll
@@ -81,17 +84,20 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
     DjT[l] = D.d[l * P + j];
   }
 
-  auto issue = [&](int e, int s) {
+  // item it = elements [it K, it K + cnt): one copy per field
+  auto issue = [&](int it, int s) {
+    const int e0 = it * K;
+    const int cnt = min(K, E - e0);
     T* dst = stage0 + s * SE;
-    mbar_arrive_expect_tx(&bar[s], nf * FB + starve_bytes);
-    bulk_g2s(dst, u + (size_t)e * P3, FB, &bar[s]);
-    bulk_g2s(dst + P3, G + (size_t)e * 6 * P3, 6 * FB, &bar[s]);
-    int off = 7 * P3;
+    mbar_arrive_expect_tx(&bar[s], nf * cnt * FB + starve_bytes);
+    bulk_g2s(dst, u + (size_t)e0 * P3, cnt * FB, &bar[s]);
+    bulk_g2s(dst + K * P3, G + (size_t)e0 * 6 * P3, 6 * cnt * FB, &bar[s]);
+    int off = 7 * K * P3;
     if (helm) {
-      bulk_g2s(dst + off, B + (size_t)e * P3, FB, &bar[s]);
-      off += P3;
+      bulk_g2s(dst + off, B + (size_t)e0 * P3, cnt * FB, &bar[s]);
+      off += K * P3;
     }
-    if (var) bulk_g2s(dst + off, h1f + (size_t)e * P3, FB, &bar[s]);
+    if (var) bulk_g2s(dst + off, h1f + (size_t)e0 * P3, cnt * FB, &bar[s]);
   };
 
   if (tid == 0) {
@@ -103,91 +109,99 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
   if (tid == 0) {
 #pragma unroll
     for (int s = 0; s < STAGES; ++s) {
-      int e = blockIdx.x + s * gridDim.x;
-      if (e < E) issue(e, s);
+      int it = blockIdx.x + s * gridDim.x;
+      if (it < nitems) issue(it, s);
     }
   }
 
   int n = 0;
-  for (int e = blockIdx.x; e < E; e += gridDim.x, ++n) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++n) {
     const int s = n % STAGES;
     const uint32_t par = (uint32_t)(n / STAGES) & 1u;
     const bool ok = mbar_wait_bounded(&bar[s], par, err, timeout_ns);
-    const T* su = stage0 + s * SE;
-    const T* sg = su + P3;
-    const T* sb = su + 7 * P3;
-    const T* sh = su + (helm ? 8 : 7) * P3;
+    const int e0 = it * K;
+    const bool act = slot < min(K, E - e0);
+    const T* su = stage0 + s * SE + slot * P3;
+    const T* sg = stage0 + s * SE + K * P3 + slot * 6 * P3;
+    const T* sb = stage0 + s * SE + 7 * K * P3 + slot * P3;
+    const T* sh = stage0 + s * SE + (helm ? 8 : 7) * K * P3 + slot * P3;
     T uc[P], bk[P], ck[P];
+    if (act) {
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      uc[k] = su[k * P2 + tid];
-      sT[k * P2 + i * P + j] = uc[k];
-      bk[k] = helm ? sb[k * P2 + tid] : T(0);
-      ck[k] = var ? sh[k * P2 + tid] : h1;
+      for (int k = 0; k < P; ++k) {
+        uc[k] = su[k * P2 + lt];
+        sT[k * P2 + i * P + j] = uc[k];
+        bk[k] = helm ? sb[k * P2 + lt] : T(0);
+        ck[k] = var ? sh[k * P2 + lt] : h1;
+      }
     }
     if (__syncthreads_or(!ok)) {
       // a copy never completed: wait (bounded) for what is in flight, then leave
       if (tid == 0) {
         for (int m = 0; m < STAGES; ++m) {
           int nn = n + m;
-          if (blockIdx.x + nn * gridDim.x < E)
+          if (blockIdx.x + nn * gridDim.x < nitems)
             mbar_wait_bounded(&bar[nn % STAGES], (uint32_t)(nn / STAGES) & 1u, err, timeout_ns);
         }
       }
       return;
     }
     T wt[P];
+    if (act) {
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      T row[P], col[P];
-      load_row<P, T>(su + k * P2 + j * P, row);
-      load_row<P, T>(sT + k * P2 + i * P, col);
-      T ur = T(0), us = T(0), ut = T(0);
+      for (int k = 0; k < P; ++k) {
+        T row[P], col[P];
+        load_row<P, T>(su + k * P2 + j * P, row);
+        load_row<P, T>(sT + k * P2 + i * P, col);
+        T ur = T(0), us = T(0), ut = T(0);
 #pragma unroll
-      for (int l = 0; l < P; ++l) {
-        ur = fma(Di[l], row[l], ur);
-        us = fma(Dj[l], col[l], us);
-        ut = fma(D.d[k * P + l], uc[l], ut);
+        for (int l = 0; l < P; ++l) {
+          ur = fma(Di[l], row[l], ur);
+          us = fma(Dj[l], col[l], us);
+          ut = fma(D.d[k * P + l], uc[l], ut);
+        }
+        const int q = k * P2 + lt;
+        T g11 = sg[q], g22 = sg[P3 + q], g33 = sg[2 * P3 + q];
+        T g12 = sg[3 * P3 + q], g13 = sg[4 * P3 + q], g23 = sg[5 * P3 + q];
+        T c = ck[k];
+        swr[k * P2 + j * P + i] = c * (g11 * ur + g12 * us + g13 * ut);
+        swsT[k * P2 + i * P + j] = c * (g12 * ur + g22 * us + g23 * ut);
+        wt[k] = c * (g13 * ur + g23 * us + g33 * ut);
       }
-      const int q = k * P2 + tid;
-      T g11 = sg[q], g22 = sg[P3 + q], g33 = sg[2 * P3 + q];
-      T g12 = sg[3 * P3 + q], g13 = sg[4 * P3 + q], g23 = sg[5 * P3 + q];
-      T c = ck[k];
-      swr[k * P2 + j * P + i] = c * (g11 * ur + g12 * us + g13 * ut);
-      swsT[k * P2 + i * P + j] = c * (g12 * ur + g22 * us + g23 * ut);
-      wt[k] = c * (g13 * ur + g23 * us + g33 * ut);
     }
     __syncthreads();
     if (tid == 0) {
-      int en = e + STAGES * gridDim.x;
-      if (en < E) {
+      int in = it + STAGES * gridDim.x;
+      if (in < nitems) {
         fence_proxy_async_smem();
-        issue(en, s);
+        issue(in, s);
       }
     }
-    T* we = w + (size_t)e * P3;
+    if (act) {
+      T* we = w + (size_t)(e0 + slot) * P3;
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      T row[P], col[P];
-      load_row<P, T>(swr + k * P2 + j * P, row);
-      load_row<P, T>(swsT + k * P2 + i * P, col);
-      T acc = T(0);
+      for (int k = 0; k < P; ++k) {
+        T row[P], col[P];
+        load_row<P, T>(swr + k * P2 + j * P, row);
+        load_row<P, T>(swsT + k * P2 + i * P, col);
+        T acc = T(0);
 #pragma unroll
-      for (int l = 0; l < P; ++l) {
-        acc = fma(DiT[l], row[l], acc);
-        acc = fma(DjT[l], col[l], acc);
-        acc = fma(D.d[l * P + k], wt[l], acc);
+        for (int l = 0; l < P; ++l) {
+          acc = fma(DiT[l], row[l], acc);
+          acc = fma(DjT[l], col[l], acc);
+          acc = fma(D.d[l * P + k], wt[l], acc);
+        }
+        if (helm) acc = fma(h2 * bk[k], uc[k], acc);
+        we[k * P2 + lt] = acc;
       }
-      if (helm) acc = fma(h2 * bk[k], uc[k], acc);
-      we[k * P2 + tid] = acc;
     }
   }
 }
 
 // ---------------------------------------------------------------- launch
-template <int P, class T, int STAGES>
+template <int P, class T, int STAGES, int K>
 static size_t tma_smem_bytes(int nf) {
-  return 128 + (size_t)(STAGES * nf + 3) * P * P * P * sizeof(T);
+  return 128 + (size_t)(STAGES * nf + 3) * K * P * P * P * sizeof(T);
 }
 
 static int num_sms() {
@@ -201,32 +215,33 @@ static int num_sms() {
   return n;
 }
 
-template <int P, class T, int STAGES>
+template <int P, class T, int STAGES, int K>
 static void launch_tma_p(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
                          const T* h1f, const CGState* st, int* err, uint64_t timeout_ns,
                          uint32_t starve, cudaStream_t s) {
   const int nf = 7 + (h2 != T(0) ? 1 : 0) + (h1f ? 1 : 0);
-  const size_t smem = tma_smem_bytes<P, T, STAGES>(nf);
-  auto kern = ax_tma_kernel<P, T, STAGES>;
+  const size_t smem = tma_smem_bytes<P, T, STAGES, K>(nf);
+  auto kern = ax_tma_kernel<P, T, STAGES, K>;
   static int configured_smem = 0;
   static int occ[3] = {0, 0, 0};
-  const int maxsmem = (int)tma_smem_bytes<P, T, STAGES>(9);
+  const int maxsmem = (int)tma_smem_bytes<P, T, STAGES, K>(9);
   if (configured_smem < maxsmem) {
     SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsmem));
     configured_smem = maxsmem;
   }
   int& o = occ[nf - 7];
   if (!o) {
-    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, P * P, smem));
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, K * P * P, smem));
     if (o < 1) o = 1;
   }
   DMat<P, T> D;
   for (int a = 0; a < P * P; ++a) D.d[a] = (T)h->Dh[a];
   const int E = (int)h->E;
-  int grid = std::min<int64_t>(E, (int64_t)o * num_sms());
+  const int nitems = (E + K - 1) / K;
+  int grid = std::min<int64_t>(nitems, (int64_t)o * num_sms());
   if (grid < 1) grid = 1;
-  kern<<<grid, P * P, smem, s>>>(u, w, op.G.ptr, op.B.ptr, h1f, h1, h2, D, E, st, err,
-                                  timeout_ns, starve);
+  kern<<<grid, K * P * P, smem, s>>>(u, w, op.G.ptr, op.B.ptr, h1f, h1, h2, D, E, st, err,
+                                     timeout_ns, starve);
   SEM_CHECK_LAUNCH();
 }
 
@@ -238,16 +253,31 @@ bool tma_ax_supported(const sem_handle* h, const void* u, const void* w, const v
   return al(u) && al(w) && al(h1f);
 }
 
+// (stages, elements per CTA) variants the autotuner chooses from
+template <int P, class T>
+static void launch_tma_variant(int variant, const sem_handle* h, const OpData<T>& op, const T* u,
+                               T* w, T h1, T h2, const T* h1f, const CGState* st, int* err,
+                               uint64_t timeout_ns, uint32_t starve, cudaStream_t s) {
+  switch (variant) {
+    case 0: launch_tma_p<P, T, 1, 1>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    case 1: launch_tma_p<P, T, 2, 1>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    case 2: launch_tma_p<P, T, 3, 1>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    case 3: launch_tma_p<P, T, 1, 2>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    default: launch_tma_p<P, T, 2, 2>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+  }
+}
+
 template <class T>
 void launch_ax_tma(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
                    const T* h1f, const CGState* st, int* err, uint64_t timeout_ns,
                    uint32_t starve, cudaStream_t s) {
+  const int v = h->tune.ax32_variant;
   switch (h->P) {
-    case 2: launch_tma_p<2, T, 3>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
-    case 4: launch_tma_p<4, T, 3>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
-    case 6: launch_tma_p<6, T, 2>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
-    case 8: launch_tma_p<8, T, 2>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
-    case 10: launch_tma_p<10, T, 2>(h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    case 2: launch_tma_variant<2, T>(v, h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    case 4: launch_tma_variant<4, T>(v, h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    case 6: launch_tma_variant<6, T>(v, h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    case 8: launch_tma_variant<8, T>(v, h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
+    case 10: launch_tma_variant<10, T>(v, h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
     default: throw Error(SEM_ERR_ARG, "launch_ax_tma: unsupported order");
   }
 }

@@ -145,6 +145,12 @@ struct sem_handle {
   sem::DevBuf<int> dev_err;                 // device-side error word (SEM_ERR_TIMEOUT)
   sem::DevBuf<float2> gdf, bdf;             // G and B as float pairs (double-float kernel)
   int f64_kernel = SEM_F64_KERNEL_AUTO;     // which FP64 Ax kernel runs
+  struct Tune {
+    int ax32_ldg = 0;          // 1: FP32 Ax by the global-load kernel instead of bulk copies
+    int ax32_variant = 1;      // bulk-copy variant: (stages, elements per CTA), see ax_tma.cu
+    int df_variant = 0;        // double-float Ax: 0 = one stage, 1 = two stages
+    int tuned = 0;
+  } tune;
 
   // gather-scatter: segments of >= 2 local copies of one global point,
   // unmasked ones first; masked local points listed separately
