@@ -109,7 +109,8 @@ extern "C" sem_status sem_autotune(sem_handle* h, void* stream, sem_tuning* out)
         DevBuf<float> u, w;
         u.alloc(n);
         w.alloc(n);
-        SEM_CUDA(cudaMemsetAsync(u.ptr, 0, n * sizeof(float), s));
+        // non-zero data (zeros take shortcuts in some kernels): every byte 0x3F
+        SEM_CUDA(cudaMemsetAsync(u.ptr, 0x3F, n * sizeof(float), s));
         float bt = 1e30f;
         auto run32 = [&]() {
           launch_ax<float>(h, h->f32, u.ptr, w.ptr, 1.0f, 0.0f, nullptr, nullptr, s);
@@ -131,7 +132,7 @@ extern "C" sem_status sem_autotune(sem_handle* h, void* stream, sem_tuning* out)
         DevBuf<double> u, w;
         u.alloc(n);
         w.alloc(n);
-        SEM_CUDA(cudaMemsetAsync(u.ptr, 0, n * sizeof(double), s));
+        SEM_CUDA(cudaMemsetAsync(u.ptr, 0x3F, n * sizeof(double), s));
         SEM_REQUIRE(df_ax_supported(h, u.ptr, w.ptr, nullptr), "sem_autotune: double-float Ax");
         float bt = 1e30f;
         for (int v = 0; v < 2; ++v) {

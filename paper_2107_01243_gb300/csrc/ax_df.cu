@@ -9,7 +9,7 @@
 // line of P pairs and makes the P outputs of that line, so every D index is a
 // compile-time constant (D lives in constant memory).  The three thread
 // groups take the r-, s- and t-lines side by side and run the same code with
-// different strides, which keeps the kernel small enough for the instruction
+// different element positions, which keeps the kernel small enough for the instruction
 // cache:
 //   phase 0  u -> pairs U
 //   forward  group g: lines of U along direction g -> UR | US | UT   (D)
@@ -17,8 +17,8 @@
 //   backward group g: lines of W along direction g, in place          (D^T)
 //   final    w = CR + CS + CT (+ h2 B u) -> double
 // Sums use exact float transformations (TwoSum, FMA product errors).
-// Shared arrays use padded rows (P+2 pairs) and planes (stride = 8 mod 16
-// pairs) to spread the shared-memory banks.
+// The shared-memory layout (DFLayout) keeps the line and point accesses free
+// of bank conflicts; each thread computes its positions once per launch.
 #include "sem_internal.cuh"
 #include "tma.cuh"
 #include "df.cuh"
@@ -37,28 +37,42 @@ struct DFScal {
   float h1h, h1l, h2h, h2l;
 };
 
+// Shared-memory layout of one element's pairs.  P = 8: planes of 72 pairs and
+// rows of 8 with the row index XOR-swizzled, position of (i, j, k) =
+// 72 k + 8 j + (i ^ ((j >> 1) + 4 (k & 1))): the i-, j- and k-lines read by
+// three thread groups and the per-point phases are all free of bank
+// conflicts (16 threads of a half warp hit 16 distinct bank pairs).  Other
+// orders: rows padded to P + 2 and planes to 8 mod 16 pairs.
 template <int P>
 struct DFLayout {
-  static constexpr int RS = P + 2;                              // row stride (pairs)
+  static constexpr int RS = P + 2;
   static constexpr int PL0 = P * RS;
-  static constexpr int PL = PL0 + ((8 - (PL0 % 16)) + 16) % 16; // plane stride = 8 mod 16
-  static constexpr int VOL = P * PL;                            // one padded array (pairs)
-  __device__ static constexpr int at(int i, int j, int k) { return k * PL + j * RS + i; }
+  static constexpr int PL = PL0 + ((8 - (PL0 % 16)) + 16) % 16;
+  static constexpr int VOL = P * PL;
+  __device__ static int at(int i, int j, int k) { return k * PL + j * RS + i; }
+};
+template <>
+struct DFLayout<8> {
+  static constexpr int PL = 72;
+  static constexpr int VOL = 8 * PL;
+  __device__ static int at(int i, int j, int k) {
+    return k * PL + j * 8 + (i ^ (((j >> 1) + 4 * (k & 1)) & 7));
+  }
 };
 
-// One line task: the P outputs y_i = sum_l M[i][l] x_l of the line starting at
-// base with the given stride (M = D, or D^T when TRANS); in may equal out.
+// One line task: the P outputs y_i = sum_l M[i][l] x_l of the line whose
+// elements sit at positions off[0..P) (M = D, or D^T when TRANS); in may equal out.
 // M is centro-antisymmetric (M[N-i][N-l] = -M[i][l] on GLL nodes), so with
 // e_l = x_l + x_{N-l}, o_l = x_l - x_{N-l} (l < P/2) the outputs come in pairs
 // y_i = A o + S e, y_{N-i} = A o - S e with two (P/2)-term dots per pair.
 template <int P, bool TRANS>
-__device__ __forceinline__ void line_task(const float2* in, float2* out, int base, int stride) {
+__device__ __forceinline__ void line_task(const float2* in, float2* out, const int (&off)[P]) {
   static_assert(P % 2 == 0, "even-odd split needs an even number of points");
   constexpr int H = P / 2, N = P - 1, T = TRANS ? 1 : 0;
   float xh[P], xl[P];
 #pragma unroll
   for (int l = 0; l < P; ++l) {
-    const float2 v = in[base + l * stride];
+    const float2 v = in[off[l]];
     xh[l] = v.x;
     xl[l] = v.y;
   }
@@ -83,7 +97,7 @@ __device__ __forceinline__ void line_task(const float2* in, float2* out, int bas
     dfadd(Ph, Pl, -Mh, -Ml, yh[N - i], yl[N - i]);
   }
 #pragma unroll
-  for (int i = 0; i < P; ++i) out[base + i * stride] = make_float2(yh[i], yl[i]);
+  for (int i = 0; i < P; ++i) out[off[i]] = make_float2(yh[i], yl[i]);
 }
 
 // sum of three products g_a * v_a
@@ -120,9 +134,19 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
   const int tid = threadIdx.x;
   const int g = tid / P2, lam = tid % P2;
   const int c1 = lam % P, c2 = lam / P;
-  // line of direction g: r: (j=c1, k=c2); s: (i=c1, k=c2); t: (i=c1, j=c2)
-  const int base = g == 0 ? L::at(0, c1, c2) : (g == 1 ? L::at(c1, 0, c2) : L::at(c1, c2, 0));
-  const int stride = g == 0 ? 1 : (g == 1 ? L::RS : L::PL);
+  // line of direction g: r: (j=c1, k=c2); s: (i=c1, k=c2); t: (i=c1, j=c2);
+  // its element positions and this thread's point positions, fixed for the kernel
+  int loff[P];
+#pragma unroll
+  for (int l = 0; l < P; ++l)
+    loff[l] = g == 0 ? L::at(l, c1, c2) : (g == 1 ? L::at(c1, l, c2) : L::at(c1, c2, l));
+  constexpr int NQ = (P3 + NT - 1) / NT;
+  int qoff[NQ];
+#pragma unroll
+  for (int m = 0; m < NQ; ++m) {
+    const int q = tid + m * NT;
+    qoff[m] = q < P3 ? L::at(q % P, (q / P) % P, q / P2) : 0;
+  }
   float2* myR = g == 0 ? R[0] : (g == 1 ? R[1] : R[2]);
 
   auto issue = [&](int e, int s) {
@@ -154,10 +178,14 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     const float2* sg = reinterpret_cast<const float2*>(stage0 + s * SB + UB);
     const float2* sb = reinterpret_cast<const float2*>(stage0 + s * SB + UB + GB);
     // phase 0: u -> pairs
-    for (int q = tid; q < P3; q += NT) {
-      float hi, lo;
-      d2df(su[q], hi, lo);
-      U[L::at(q % P, (q / P) % P, q / P2)] = make_float2(hi, lo);
+#pragma unroll
+    for (int m = 0; m < NQ; ++m) {
+      const int q = tid + m * NT;
+      if (q < P3) {
+        float hi, lo;
+        d2df(su[q], hi, lo);
+        U[qoff[m]] = make_float2(hi, lo);
+      }
     }
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
@@ -170,11 +198,14 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       return;
     }
     // forward derivatives: group g differentiates along direction g
-    line_task<P, false>(U, myR, base, stride);
+    line_task<P, false>(U, myR, loff);
     __syncthreads();
     // geometric factors at every point: (WR, WS, WT) = h1 G (UR, US, UT), in place
-    for (int q = tid; q < P3; q += NT) {
-      const int at = L::at(q % P, (q / P) % P, q / P2);
+#pragma unroll
+    for (int m = 0; m < NQ; ++m) {
+      const int q = tid + m * NT;
+      if (q >= P3) break;
+      const int at = qoff[m];
       const float2 g11 = sg[q], g22 = sg[P3 + q], g33 = sg[2 * P3 + q];
       const float2 g12 = sg[3 * P3 + q], g13 = sg[4 * P3 + q], g23 = sg[5 * P3 + q];
       const float2 ur = R[0][at], us = R[1][at], ut = R[2][at];
@@ -200,12 +231,15 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       }
     }
     // transposed derivatives, in place: group g along direction g
-    line_task<P, true>(myR, myR, base, stride);
+    line_task<P, true>(myR, myR, loff);
     __syncthreads();
     // w = CR + CS + CT (+ h2 B u) -> double
     double* we = w + (size_t)e * P3;
-    for (int q = tid; q < P3; q += NT) {
-      const int at = L::at(q % P, (q / P) % P, q / P2);
+#pragma unroll
+    for (int m = 0; m < NQ; ++m) {
+      const int q = tid + m * NT;
+      if (q >= P3) break;
+      const int at = qoff[m];
       const float2 cr = R[0][at], cs = R[1][at], ct = R[2][at];
       float S = cr.x, er = cr.y;
       tadd(cs.x, cs.y, S, er);
