@@ -43,6 +43,23 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# FP64 Ax kernel on the 32^3, N=7 throughput mesh, from one ncu capture of the
+# kernel as it now stands (summary and command under profiles/); a kernel
+# variant that no capture covers reports null.
+AX_TRAFFIC = {}
+
+
+def ax_kernel_name(tiles):
+    """The FP64 Ax kernel the autotuned handle launches at N=7 (double-float
+    arithmetic on the FP32 pipes, 1 or 2 shared-memory stages)."""
+    return f"ax_df_kernel<8, {tiles['f64_stages']}>"
+
+
+def ax_traffic(tiles):
+    return AX_TRAFFIC.get(ax_kernel_name(tiles))
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -273,7 +290,8 @@ def main():
                    "local_points": n, "l2": "inputs larger than L2 (u 134 MB, G 805 MB)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": "ax_kernel<8,double>",
+                     "frac": achieved / hbm, "traffic": ax_traffic(tiles),
+                     "kernel": ax_kernel_name(tiles),
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": ax_bytes},
         "kernels": {"ax_f64_ms": ax_ms, "dssum_f64_ms": ds_ms,

@@ -227,7 +227,9 @@ typedef struct {
   double tol;             /* relative residual ||b - Hx|| / ||b|| (1e-8) */
   int maxit;              /* CG iteration limit, counted over inner iterations (20000) */
   int precision;          /* SEM_SOLVE_F64 or SEM_SOLVE_MIXED (SEM_SOLVE_F64) */
-  double inner_tol;       /* mixed: FP32 inner relative tolerance (1e-4) */
+  double inner_tol;       /* mixed: FP32 inner relative tolerance (1e-4); a step
+                             whose outer residual needs less reduction than that
+                             to reach tol stops at 0.5 tol / (outer rel. residual) */
   int max_outer;          /* mixed: refinement steps limit (30) */
   int check_every;        /* iterations per host convergence check (16) */
   int use_graph;          /* capture check_every iterations in a CUDA graph (1) */

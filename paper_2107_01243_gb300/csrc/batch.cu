@@ -840,7 +840,8 @@ extern "C" sem_status sem_batch_solve(sem_batch* bt, const double* const* b_L,
       const BProb& b = bt->hp[p];
       binit_kernel<<<std::min(b.v_cnt, 4 * kNumSMs), 256, 0, own>>>(
           bt->probs.ptr, bt->item_prob.ptr, b.v_off, b.v_cnt, bt->nitems, bt->partials.ptr,
-          bt->tickets.ptr, o.inner_tol, std::max(1, o.maxit - iters[p]));
+          bt->tickets.ptr, inner_target(o.inner_tol, o.tol, rel[p]),
+          std::max(1, o.maxit - iters[p]));
       SEM_CHECK_LAUNCH();
     };
     for (int p = 0; p < n; ++p) refine(p);

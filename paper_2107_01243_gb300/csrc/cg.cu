@@ -10,6 +10,8 @@
 // captured in a CUDA graph and the host reads the state once per batch.
 #include <cmath>
 #include <algorithm>
+#include <cstdint>
+#include <initializer_list>
 
 #include "sem_internal.cuh"
 #include "reduce.cuh"
@@ -40,6 +42,130 @@ struct Acc<float> {
   }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
+
+// ---- vectorised forms of k_pw / k_update / k_pupd: 16-byte loads (float4 for
+// FP32, double2 for FP64), used when nL is a multiple of the lane count and
+// the vectors are 16-byte aligned; same per-point arithmetic as the scalar forms.
+template <class T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using V = float4;
+  using M = float4;
+  static constexpr int L = 4;
+};
+template <>
+struct Vec<double> {
+  using V = double2;
+  using M = float2;
+  static constexpr int L = 2;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kRedThreads)
+k_pw_v(int64_t nv, const typename Vec<T>::V* __restrict__ p, const typename Vec<T>::V* __restrict__ w,
+       const typename Vec<T>::M* __restrict__ imult, CGState* __restrict__ st,
+       double* __restrict__ partials) {
+  using VT = Vec<T>;
+  if (st->done) return;
+  Acc<T> a0;
+#pragma unroll 4
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const typename VT::V a = p[q], b = w[q];
+    const typename VT::M m = imult[q];
+    const T* ae = reinterpret_cast<const T*>(&a);
+    const T* be = reinterpret_cast<const T*>(&b);
+    const float* me = reinterpret_cast<const float*>(&m);
+#pragma unroll
+    for (int l = 0; l < VT::L; ++l) a0.add(ae[l], be[l], me[l]);
+  }
+  double v[1] = {a0.value()};
+  double tot[1];
+  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    st->pw = tot[0];
+    if (!(tot[0] > 0.0)) {
+      st->status = SEM_ERR_BREAKDOWN;
+      st->done = 1;
+    } else {
+      st->alpha = st->rz / tot[0];
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kRedThreads)
+k_update_v(int64_t nv, typename Vec<T>::V* __restrict__ x, typename Vec<T>::V* __restrict__ r,
+           const typename Vec<T>::V* __restrict__ p, const typename Vec<T>::V* __restrict__ w,
+           const typename Vec<T>::V* __restrict__ dinv, const typename Vec<T>::M* __restrict__ imult,
+           CGState* __restrict__ st, double* __restrict__ partials) {
+  using VT = Vec<T>;
+  if (st->done) return;
+  const T alpha = (T)st->alpha;
+  Acc<T> a0, a1;
+#pragma unroll 2
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    typename VT::V xq = x[q], rq = r[q];
+    const typename VT::V pq = p[q], wq = w[q], dq = dinv[q];
+    const typename VT::M mq = imult[q];
+    T* xe = reinterpret_cast<T*>(&xq);
+    T* re = reinterpret_cast<T*>(&rq);
+    const T* pe = reinterpret_cast<const T*>(&pq);
+    const T* we = reinterpret_cast<const T*>(&wq);
+    const T* de = reinterpret_cast<const T*>(&dq);
+    const float* me = reinterpret_cast<const float*>(&mq);
+#pragma unroll
+    for (int l = 0; l < VT::L; ++l) {
+      xe[l] += alpha * pe[l];
+      re[l] = re[l] - alpha * we[l];
+      const T z = de[l] * re[l];
+      a0.add(re[l], z, me[l]);
+      a1.add(re[l], re[l], me[l]);
+    }
+    x[q] = xq;
+    r[q] = rq;
+  }
+  double v[2] = {a0.value(), a1.value()};
+  double tot[2];
+  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    st->iter += 1;
+    st->rr = tot[1];
+    if (!(tot[1] == tot[1]) || !(tot[0] == tot[0])) {
+      st->status = SEM_ERR_BREAKDOWN;
+      st->done = 1;
+    } else if (tot[1] <= st->tol2) {
+      st->done = 1;
+    } else if (st->iter >= st->maxit) {
+      st->status = SEM_ERR_NOCONV;
+      st->done = 1;
+    } else {
+      st->beta = tot[0] / st->rz;
+      st->rz = tot[0];
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kRedThreads)
+k_pupd_v(int64_t nv, typename Vec<T>::V* __restrict__ p, const typename Vec<T>::V* __restrict__ r,
+         const typename Vec<T>::V* __restrict__ dinv, const CGState* __restrict__ st) {
+  using VT = Vec<T>;
+  if (st->done) return;
+  const T beta = (T)st->beta;
+#pragma unroll 4
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    typename VT::V pq = p[q];
+    const typename VT::V rq = r[q], dq = dinv[q];
+    T* pe = reinterpret_cast<T*>(&pq);
+    const T* re = reinterpret_cast<const T*>(&rq);
+    const T* de = reinterpret_cast<const T*>(&dq);
+#pragma unroll
+    for (int l = 0; l < VT::L; ++l) pe[l] = de[l] * re[l] + beta * pe[l];
+    p[q] = pq;
+  }
+}
 
 template <class T>
 __global__ void __launch_bounds__(kRedThreads)
@@ -257,19 +383,47 @@ struct PcgArgs {
   CGState* st;
 };
 
+// true when the vectorised kernels apply: n a multiple of the lane count and
+// every vector (and the multiplicity array) 16-byte (FP32 imult: 8-byte) aligned
+template <class T>
+static bool vec_ok(int64_t n, std::initializer_list<const T*> ptrs, const float* imult) {
+  if (n % Vec<T>::L) return false;
+  for (const T* q : ptrs)
+    if (reinterpret_cast<uintptr_t>(q) % 16) return false;
+  return reinterpret_cast<uintptr_t>(imult) % (Vec<T>::L * sizeof(float)) == 0;
+}
+
 template <class T>
 static void pcg_iterations(sem_handle* h, const PcgArgs<T>& a, int count, cudaStream_t s) {
   const int64_t n = h->nL;
+  const bool vec = vec_ok<T>(n, {a.x, a.r, a.p, a.w, a.dinv}, h->imult.ptr);
   for (int c = 0; c < count; ++c) {
     launch_ax<T>(h, *a.op, a.p, a.w, a.h1, a.h2, a.h1f, a.st, s);
     launch_dssum<T>(h, a.w, true, a.st, s);
-    k_pw<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, a.p, a.w, h->imult.ptr, a.st, h->partials.ptr);
-    SEM_CHECK_LAUNCH();
-    k_update<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, a.x, a.r, a.p, a.w, a.dinv, h->imult.ptr,
-                                                   a.st, h->partials.ptr);
-    SEM_CHECK_LAUNCH();
-    k_pupd<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, a.p, a.r, a.dinv, a.st);
-    SEM_CHECK_LAUNCH();
+    if (vec) {
+      using V = typename Vec<T>::V;
+      using M = typename Vec<T>::M;
+      const int64_t nv = n / Vec<T>::L;
+      k_pw_v<T><<<kRedBlocks, kRedThreads, 0, s>>>(nv, (const V*)a.p, (const V*)a.w,
+                                                   (const M*)h->imult.ptr, a.st, h->partials.ptr);
+      SEM_CHECK_LAUNCH();
+      k_update_v<T><<<kRedBlocks, kRedThreads, 0, s>>>(nv, (V*)a.x, (V*)a.r, (const V*)a.p,
+                                                       (const V*)a.w, (const V*)a.dinv,
+                                                       (const M*)h->imult.ptr, a.st,
+                                                       h->partials.ptr);
+      SEM_CHECK_LAUNCH();
+      k_pupd_v<T><<<kRedBlocks, kRedThreads, 0, s>>>(nv, (V*)a.p, (const V*)a.r,
+                                                     (const V*)a.dinv, a.st);
+      SEM_CHECK_LAUNCH();
+    } else {
+      k_pw<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, a.p, a.w, h->imult.ptr, a.st, h->partials.ptr);
+      SEM_CHECK_LAUNCH();
+      k_update<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, a.x, a.r, a.p, a.w, a.dinv, h->imult.ptr,
+                                                     a.st, h->partials.ptr);
+      SEM_CHECK_LAUNCH();
+      k_pupd<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, a.p, a.r, a.dinv, a.st);
+      SEM_CHECK_LAUNCH();
+    }
   }
 }
 
@@ -378,6 +532,17 @@ static void solve_fp64(sem_handle* h, const double* b, double* x, const sem_solv
   info.status = fin.status;
 }
 
+// Relative tolerance of the next inner FP32 solve when the outer relative
+// residual is rel: inner_tol (the reduction FP32 can be trusted with), or,
+// once less is needed, the reduction that reaches the outer tolerance with a
+// factor kInnerMargin to spare, so that the last refinement step does only
+// the iterations it needs.
+double inner_target(double inner_tol, double tol, double rel) {
+  constexpr double kInnerMargin = 0.5;
+  const double need = rel > 0.0 ? kInnerMargin * tol / rel : inner_tol;
+  return std::max(inner_tol, std::min(0.5, need));
+}
+
 static void solve_mixed(sem_handle* h, const double* b, double* x, const sem_solve_opts& o,
                         sem_solve_info& info, cudaStream_t s) {
   const int64_t n = h->nL;
@@ -407,10 +572,11 @@ static void solve_mixed(sem_handle* h, const double* b, double* x, const sem_sol
     if (!(rel == rel)) { status = SEM_ERR_BREAKDOWN; break; }
     if (rel <= o.tol) { status = SEM_OK; break; }
     if (outer >= o.max_outer || total >= o.maxit) { status = SEM_ERR_NOCONV; break; }
-    // inner FP32 PCG on H d = r32, d = 0 initially, relative tolerance inner_tol
+    // inner FP32 PCG on H d = r32, d = 0 initially
     k_init<float><<<kRedBlocks, kRedThreads, 0, s>>>(n, h->r32.ptr, h->f32.dinv.ptr,
                                                      h->imult.ptr, h->p32.ptr, h->x32.ptr, st1,
-                                                     h->partials.ptr, o.inner_tol,
+                                                     h->partials.ptr,
+                                                     inner_target(o.inner_tol, o.tol, rel),
                                                      o.maxit - total, 1);
     SEM_CHECK_LAUNCH();
     PcgArgs<float> a{&h->f32, h->x32.ptr, h->r32.ptr, h->p32.ptr, h->w32.ptr, h->f32.dinv.ptr,

@@ -214,6 +214,7 @@ void launch_dssum_box(const sem_handle* h, T* w, bool apply_mask, const CGState*
                       cudaStream_t s);
 
 // ---- cg.cu: pieces of the mixed-precision solve reused by the batched solver
+double inner_target(double inner_tol, double tol, double rel);
 void mixed_prepare(sem_handle* h, const sem_solve_opts& o, cudaStream_t s);
 void outer_norm_b(sem_handle* h, const double* b, cudaStream_t s);    // <b,b> -> state[0].bb
 void outer_residual(sem_handle* h, const double* b, const double* x, const sem_solve_opts& o,
