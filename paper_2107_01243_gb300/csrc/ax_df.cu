@@ -37,12 +37,13 @@ struct DFScal {
   float h1h, h1l, h2h, h2l;
 };
 
-// Shared-memory layout of one element's pairs.  P = 8: planes of 72 pairs and
-// rows of 8 with the row index XOR-swizzled, position of (i, j, k) =
-// 72 k + 8 j + (i ^ ((j >> 1) + 4 (k & 1))): the i-, j- and k-lines read by
-// three thread groups and the per-point phases are all free of bank
-// conflicts (16 threads of a half warp hit 16 distinct bank pairs).  Other
-// orders: rows padded to P + 2 and planes to 8 mod 16 pairs.
+// Shared-memory layout of one element's pairs.  P = 8: unpadded planes of 64
+// pairs with rows and columns XOR-swizzled by the plane parity, position of
+// (i, j, k) = 64 k + 8 (j ^ (k & 1)) + (i ^ ((j >> 1) + 4 (k & 1))): the i-, j-
+// and k-lines read by the three thread groups and the per-point phases are
+// all free of bank conflicts (16 threads of a half warp hit 16 distinct bank
+// pairs), and an element takes 4 KB per array.  Other orders: rows padded to
+// P + 2 and planes to 8 mod 16 pairs.
 template <int P>
 struct DFLayout {
   static constexpr int RS = P + 2;
@@ -53,10 +54,10 @@ struct DFLayout {
 };
 template <>
 struct DFLayout<8> {
-  static constexpr int PL = 72;
+  static constexpr int PL = 64;
   static constexpr int VOL = 8 * PL;
   __device__ static int at(int i, int j, int k) {
-    return k * PL + j * 8 + (i ^ (((j >> 1) + 4 * (k & 1)) & 7));
+    return k * PL + 8 * (j ^ (k & 1)) + (i ^ (((j >> 1) + 4 * (k & 1)) & 7));
   }
 };
 
@@ -250,7 +251,7 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
         dfmul(C.h2h, C.h2l, bv.x, bv.y, bh, bl);
         tmac(bh, bl, uv.x, uv.y, S, er);
       }
-      we[q] = df2d(S, er);
+      we[q] = (double)S + (double)er;          // exact widenings, one rounding
     }
     if (helm) {
       __syncthreads();                         // U and the stage are free
@@ -328,6 +329,8 @@ static void launch_df_p(const sem_handle* h, const double* u, double* w, double 
   if (!configured) {
     SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)df_smem_bytes<P, STAGES>(true)));
+    SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared));
     configured = true;
   }
   int& o = occ[helm ? 1 : 0];
