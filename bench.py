@@ -47,7 +47,12 @@ def peaks():
 # FP64 Ax kernel on the 32^3, N=7 throughput mesh, from one ncu capture of the
 # kernel as it now stands (summary and command under profiles/); a kernel
 # variant that no capture covers reports null.
-AX_TRAFFIC = {}
+AX_TRAFFIC = {"ax_df_kernel<8, 1>": 939_595_776 + 124_905_984}
+# smsp__inst_executed.sum per launch from the same capture: the double-float
+# kernel is bound by instruction issue on the FP32 pipe, so its second roof is
+# the issue rate, 152 SMs x 4 schedulers x the maximum SM clock.
+AX_WARP_INSTR = {"ax_df_kernel<8, 1>": 279_412_696}
+ISSUE_PEAK = 152 * 4 * 2.07e9         # warp instructions per second
 
 
 def ax_kernel_name(tiles):
@@ -58,6 +63,19 @@ def ax_kernel_name(tiles):
 
 def ax_traffic(tiles):
     return AX_TRAFFIC.get(ax_kernel_name(tiles))
+
+
+def alu_roof(tiles, ax_ms):
+    """Issue roof of the FP64 Ax kernel: warp instructions per launch (ncu)
+    over its CUDA-event duration, against the SMs' issue rate at max clock."""
+    k = ax_kernel_name(tiles)
+    instr = AX_WARP_INSTR.get(k)
+    if instr is None:
+        return None
+    achieved = instr / (ax_ms / 1e3)
+    return {"bound": "alu", "kernel": k, "unit": "warp instr/s", "achieved": achieved,
+            "peak": ISSUE_PEAK, "frac": achieved / ISSUE_PEAK,
+            "warp_instructions_per_launch": instr}
 
 
 # ---------------------------------------------------------------- clocks
@@ -179,6 +197,9 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--tiles", default=None,
+                    help="pin the Ax tiles instead of autotuning: "
+                         "<bulk-copy|global-load>:<fp32 stages>:<fp32 elements per CTA>:<fp64 stages>")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -199,7 +220,14 @@ def main():
 
     cfg = WORKLOAD
     h = sem.sem_setup(cfg["nel"], cfg["N"], length=cfg["length"], deform=cfg["deform"])
-    tiles = sem.sem_autotune(h)
+    if args.tiles:
+        k32, st32, el32, st64 = args.tiles.split(":")
+        sem.sem_set_tuning(h, ax32_kernel=k32, ax32_stages=int(st32),
+                           ax32_elems_per_cta=int(el32), f64_stages=int(st64))
+        tiles = dict(ax32_kernel=k32, ax32_stages=int(st32), ax32_elems_per_cta=int(el32),
+                     f64_stages=int(st64), pinned=True)
+    else:
+        tiles = sem.sem_autotune(h)
     n = h.n_local
     u_host = torch.from_numpy(si.uniform(n, cfg["seed"])).pin_memory()
     u = u_host.to(dev)
@@ -294,6 +322,7 @@ def main():
                      "kernel": ax_kernel_name(tiles),
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": ax_bytes},
+        "alu": alu_roof(tiles, ax_ms),
         "kernels": {"ax_f64_ms": ax_ms, "dssum_f64_ms": ds_ms,
                     "dssum_f64_gbs": ds_bytes / (ds_ms / 1e3) / 1e9,
                     "ax_f32_ms": ax32, "ax_f32_gbs": 32 * n / (ax32 / 1e3) / 1e9,
@@ -314,6 +343,9 @@ def main():
         line["solve"] = run_solves(sem, torch, dev)
     if not args.no_batch:
         line["batch"] = run_batch(sem, torch, dev)
+    if not args.no_solve:
+        line["manufactured"] = run_manufactured(sem, torch, dev)
+        line["adjoint"] = run_adjoint(sem, torch, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         gd, meta = time_oracle(8, 10.0)
@@ -407,6 +439,100 @@ def run_solves(sem, torch, dev):
     out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
     sem.sem_destroy(h)
     return out
+
+
+def _coords(sem, torch, h, dev):
+    xs = [torch.empty(h.n_local, dtype=torch.float64, device=dev) for _ in range(3)]
+    for t, f in zip(xs, (sem.SEM_FIELD_X, sem.SEM_FIELD_Y, sem.SEM_FIELD_Z)):
+        sem.sem_get_field(h, f, t)
+    return [t.cpu().numpy() for t in xs]
+
+
+def run_manufactured(sem, torch, dev):
+    """Unit cube, 4^3 undeformed elements, u = sin(pi x) sin(pi y) sin(pi z):
+    FP64 PCG to 1e-10 at N = 7 (iterations, time, time per iteration, max
+    nodal error against the exact solution) and the spectral-convergence sweep
+    N = 2..10 (max nodal error per order)."""
+    cfg = si.MANUFACTURED
+
+    def solve(N, reps=1):
+        h = sem.sem_setup(cfg["nel"], N, length=cfg["length"], deform=cfg["deform"])
+        X, Y, Z = _coords(sem, torch, h, dev)
+        f = torch.from_numpy(si.manufactured_f(X, Y, Z)).to(dev)
+        b = torch.empty_like(f)
+        sem.sem_rhs(h, f, b)
+        x = torch.empty_like(b)
+        info = sem.sem_cg_solve(h, b, x, tol=cfg["tol"])          # warm-up (graph, dinv)
+        times = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = sem.sem_cg_solve(h, b, x, tol=cfg["tol"])
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        err = float(np.abs(x.cpu().numpy() - si.manufactured_u(X, Y, Z)).max())
+        sem.sem_destroy(h)
+        return info, statistics.median(times), err
+
+    info, sec, err = solve(cfg["N"], reps=5)
+    sweep = {}
+    for N in range(2, 11):
+        i2, _, e2 = solve(N)
+        sweep[str(N)] = {"max_nodal_error": e2, "iters": i2["iters"]}
+    return {"workload": "Poisson on the unit cube, 4^3 undeformed elements, N=7, "
+                        "u = sin(pi x) sin(pi y) sin(pi z), FP64 PCG to 1e-10",
+            "iters": info["iters"], "seconds": sec, "ms_per_iter": 1e3 * sec / max(1, info["iters"]),
+            "rel_res": info["rel_res"], "status": info["status"], "max_nodal_error": err,
+            "spectral_sweep_E4cubed": sweep}
+
+
+def run_adjoint(sem, torch, dev):
+    """16^3 deformed elements, N = 7, h1 = 1 + 0.5 tanh(smooth field), h2 = 1:
+    forward solve + adjoint solve + dL/dh1 kernel through autograd (time), and
+    the gradient along a smooth direction against central differences."""
+    cfg = si.ADJOINT
+    h = sem.sem_setup(cfg["nel"], cfg["N"], length=cfg["length"], deform=cfg["deform"])
+    X, Y, Z = _coords(sem, torch, h, dev)
+    h1 = torch.from_numpy(si.smooth_coefficient(X, Y, Z, cfg["h1_seed"])).to(dev)
+    ut = torch.from_numpy(0.01 * si.eval_fourier(si.fourier_modes(cfg["target_seed"]),
+                                                 X, Y, Z)).to(dev)
+    f = torch.from_numpy(si.eval_fourier(si.fourier_modes(cfg["rhs_seed"]), X, Y, Z)).to(dev)
+    d = torch.from_numpy(si.eval_fourier(si.fourier_modes(80), X, Y, Z)).to(dev)
+    b = torch.empty_like(f)
+    sem.sem_rhs(h, f, b)
+    mult = torch.empty_like(b)
+    sem.sem_get_field(h, sem.SEM_FIELD_MULT, mult)
+    tol = 1e-13
+
+    def fwd_bwd():
+        h1_t = h1.clone().requires_grad_(True)
+        x = sem.helmholtz_solve(h1_t, b, h, h2=1.0, tol=tol)
+        loss = (((x - ut) ** 2) / mult).sum()
+        loss.backward()
+        return h1_t.grad
+
+    fwd_bwd()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = fwd_bwd()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+
+    def L(h1v):
+        x = torch.empty_like(b)
+        sem.sem_cg_solve(h, b, x, h1_field=h1v, h2=1.0, tol=tol)
+        return float((((x - ut) ** 2) / mult).sum())
+
+    eps = 1e-5 * float(h1.abs().max())
+    fd = (L(h1 + eps * d) - L(h1 - eps * d)) / (2 * eps)
+    gd = float((g * d).sum())
+    n = h.n_local
+    sem.sem_destroy(h)
+    return {"workload": "variable-coefficient Helmholtz, 16^3 deformed elements, N=7, "
+                        "loss ||u - u_target||^2, dL/dh1 by adjoint PCG, FP64, tol 1e-13",
+            "local_points": n,
+            "forward_backward_seconds": sec, "fd": fd, "grad_dot_dir": gd,
+            "fd_rel_diff": abs(fd - gd) / abs(fd)}
 
 
 if __name__ == "__main__":

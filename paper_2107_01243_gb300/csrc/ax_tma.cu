@@ -14,42 +14,9 @@
 // Needs P^3 * sizeof(T) % 16 == 0 (even P) and 16-byte aligned vectors.
 #include "sem_internal.cuh"
 #include "tma.cuh"
+#include "ax_tile.cuh"
 
 namespace sem {
-
-template <int P, class T>
-struct DMat {
-  T d[P * P];
-};
-
-template <int P, class T>
-__device__ __forceinline__ void load_row(const T* __restrict__ p, T (&v)[P]) {
-  constexpr int bytes = P * (int)sizeof(T);
-  if constexpr (bytes % 16 == 0) {
-    constexpr int nv = bytes / 16;
-    const float4* q = reinterpret_cast<const float4*>(p);
-#pragma unroll
-    for (int a = 0; a < nv; ++a) {
-      float4 f = q[a];
-      const T* t = reinterpret_cast<const T*>(&f);
-#pragma unroll
-      for (int b = 0; b < 16 / (int)sizeof(T); ++b) v[a * (16 / (int)sizeof(T)) + b] = t[b];
-    }
-  } else if constexpr (bytes % 8 == 0) {
-    constexpr int nv = bytes / 8;
-    const float2* q = reinterpret_cast<const float2*>(p);
-#pragma unroll
-    for (int a = 0; a < nv; ++a) {
-      float2 f = q[a];
-      const T* t = reinterpret_cast<const T*>(&f);
-#pragma unroll
-      for (int b = 0; b < 8 / (int)sizeof(T); ++b) v[a * (8 / (int)sizeof(T)) + b] = t[b];
-    }
-  } else {
-#pragma unroll
-    for (int a = 0; a < P; ++a) v[a] = p[a];
-  }
-}
 
 template <int P, class T, int STAGES, int K>
 __global__ void __launch_bounds__(K * P * P)
@@ -68,21 +35,14 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
   const int nf = 7 + (helm ? 1 : 0) + (var ? 1 : 0);
   const int SE = nf * K * P3;                          // stage size in values
   const int tid = threadIdx.x;
-  const int slot = tid / P2, lt = tid - slot * P2;     // element slot, thread within it
-  const int i = lt % P, j = lt / P;
+  const int slot = tid / P2;                           // element slot of this thread
   T* sT = stage0 + STAGES * SE + slot * P3;
   T* swr = stage0 + STAGES * SE + K * P3 + slot * P3;
   T* swsT = stage0 + STAGES * SE + 2 * K * P3 + slot * P3;
   const int nitems = (E + K - 1) / K;
-
-  T Di[P], Dj[P], DiT[P], DjT[P];
-#pragma unroll
-  for (int l = 0; l < P; ++l) {
-    Di[l] = D.d[i * P + l];
-    Dj[l] = D.d[j * P + l];
-    DiT[l] = D.d[l * P + i];
-    DjT[l] = D.d[l * P + j];
-  }
+  auto Dm = [&](int r, int c) { return D.d[r * P + c]; };
+  TileThread<P, T> t;
+  t.init(tid - slot * P2, Dm);
 
   // item it = elements [it K, it K + cnt): one copy per field
   auto issue = [&](int it, int s) {
@@ -123,18 +83,10 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
     const bool act = slot < min(K, E - e0);
     const T* su = stage0 + s * SE + slot * P3;
     const T* sg = stage0 + s * SE + K * P3 + slot * 6 * P3;
-    const T* sb = stage0 + s * SE + 7 * K * P3 + slot * P3;
-    const T* sh = stage0 + s * SE + (helm ? 8 : 7) * K * P3 + slot * P3;
-    T uc[P], bk[P], ck[P];
-    if (act) {
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        uc[k] = su[k * P2 + lt];
-        sT[k * P2 + i * P + j] = uc[k];
-        bk[k] = helm ? sb[k * P2 + lt] : T(0);
-        ck[k] = var ? sh[k * P2 + lt] : h1;
-      }
-    }
+    const T* sb = helm ? stage0 + s * SE + 7 * K * P3 + slot * P3 : nullptr;
+    const T* sh = var ? stage0 + s * SE + (helm ? 8 : 7) * K * P3 + slot * P3 : nullptr;
+    T uc[P], bk[P], ck[P], wt[P];
+    if (act) tile_load<P, T>(t, su, sb, sh, h1, sT, uc, bk, ck);
     if (__syncthreads_or(!ok)) {
       // a copy never completed: wait (bounded) for what is in flight, then leave
       if (tid == 0) {
@@ -146,29 +98,7 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
       }
       return;
     }
-    T wt[P];
-    if (act) {
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        T row[P], col[P];
-        load_row<P, T>(su + k * P2 + j * P, row);
-        load_row<P, T>(sT + k * P2 + i * P, col);
-        T ur = T(0), us = T(0), ut = T(0);
-#pragma unroll
-        for (int l = 0; l < P; ++l) {
-          ur = fma(Di[l], row[l], ur);
-          us = fma(Dj[l], col[l], us);
-          ut = fma(D.d[k * P + l], uc[l], ut);
-        }
-        const int q = k * P2 + lt;
-        T g11 = sg[q], g22 = sg[P3 + q], g33 = sg[2 * P3 + q];
-        T g12 = sg[3 * P3 + q], g13 = sg[4 * P3 + q], g23 = sg[5 * P3 + q];
-        T c = ck[k];
-        swr[k * P2 + j * P + i] = c * (g11 * ur + g12 * us + g13 * ut);
-        swsT[k * P2 + i * P + j] = c * (g12 * ur + g22 * us + g23 * ut);
-        wt[k] = c * (g13 * ur + g23 * us + g33 * ut);
-      }
-    }
+    if (act) tile_forward<P, T>(t, su, sT, sg, uc, ck, swr, swsT, wt, Dm);
     __syncthreads();
     if (tid == 0) {
       int in = it + STAGES * gridDim.x;
@@ -177,24 +107,7 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
         issue(in, s);
       }
     }
-    if (act) {
-      T* we = w + (size_t)(e0 + slot) * P3;
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        T row[P], col[P];
-        load_row<P, T>(swr + k * P2 + j * P, row);
-        load_row<P, T>(swsT + k * P2 + i * P, col);
-        T acc = T(0);
-#pragma unroll
-        for (int l = 0; l < P; ++l) {
-          acc = fma(DiT[l], row[l], acc);
-          acc = fma(DjT[l], col[l], acc);
-          acc = fma(D.d[l * P + k], wt[l], acc);
-        }
-        if (helm) acc = fma(h2 * bk[k], uc[k], acc);
-        we[k * P2 + lt] = acc;
-      }
-    }
+    if (act) tile_backward<P, T>(t, swr, swsT, wt, uc, bk, h2, helm, w + (size_t)(e0 + slot) * P3, Dm);
   }
 }
 

@@ -22,6 +22,7 @@
 #include "sem_internal.cuh"
 #include "tma.cuh"
 #include "reduce.cuh"
+#include "ax_tile.cuh"
 
 namespace sem {
 
@@ -33,7 +34,7 @@ template <int P>
 struct BaxCfg {
   static constexpr int K = (64 / (P * P)) > 1 ? (64 / (P * P)) : 1;
   static constexpr int THREADS = K * P * P;
-  static constexpr int STAGES = 2;
+  static constexpr int STAGES = P >= 10 ? 1 : 2;     // P = 10: more CTAs per SM
   static constexpr size_t smem() {
     return 128 + (size_t)(STAGES * 8 + 3) * K * P * P * P * sizeof(float);
   }
@@ -74,99 +75,6 @@ __device__ __forceinline__ int find_prob(const long long* off, int n, long long 
 }
 
 // ---------------------------------------------------------------- batched Ax
-template <int P>
-__device__ __forceinline__ void load_row_f(const float* __restrict__ p, float (&v)[P]) {
-  if constexpr ((P * 4) % 16 == 0) {
-    const float4* q = reinterpret_cast<const float4*>(p);
-#pragma unroll
-    for (int a = 0; a < P / 4; ++a) {
-      const float4 f = q[a];
-      v[4 * a] = f.x; v[4 * a + 1] = f.y; v[4 * a + 2] = f.z; v[4 * a + 3] = f.w;
-    }
-  } else if constexpr ((P * 4) % 8 == 0) {
-    const float2* q = reinterpret_cast<const float2*>(p);
-#pragma unroll
-    for (int a = 0; a < P / 2; ++a) {
-      const float2 f = q[a];
-      v[2 * a] = f.x; v[2 * a + 1] = f.y;
-    }
-  } else {
-#pragma unroll
-    for (int a = 0; a < P; ++a) v[a] = p[a];
-  }
-}
-
-// Up to K elements of order P from a filled stage laid out as
-// [u of the K slots][6 G of the K slots][B of the K slots]; slot s uses
-// threads [s P^2, (s+1) P^2).  release() is called by all threads once the
-// stage is no longer read.
-template <int P, class Rel>
-__device__ __forceinline__ void belem(const float* __restrict__ stage, int K, int count,
-                                      float* work, float* __restrict__ w0, float h1, float h2,
-                                      bool helm, int tid, Rel release) {
-  constexpr int P2 = P * P, P3 = P2 * P;
-  const int slot = tid / P2, lt = tid - slot * P2;
-  const bool act = slot < count;
-  const int i = lt % P, j = lt / P;
-  const float* su = stage + slot * P3;
-  const float* sg = stage + K * P3 + slot * 6 * P3;
-  const float* sb = stage + 7 * K * P3 + slot * P3;
-  float* sT = work + slot * P3;
-  float* swr = work + K * P3 + slot * P3;
-  float* swsT = work + 2 * K * P3 + slot * P3;
-  float uc[P], bk[P], wt[P];
-  if (act) {
-#pragma unroll
-    for (int k = 0; k < P; ++k) {
-      uc[k] = su[k * P2 + lt];
-      sT[k * P2 + i * P + j] = uc[k];
-      bk[k] = helm ? sb[k * P2 + lt] : 0.0f;
-    }
-  }
-  __syncthreads();
-  if (act) {
-#pragma unroll
-    for (int k = 0; k < P; ++k) {
-      float row[P], col[P];
-      load_row_f<P>(su + k * P2 + j * P, row);
-      load_row_f<P>(sT + k * P2 + i * P, col);
-      float ur = 0.0f, us = 0.0f, ut = 0.0f;
-#pragma unroll
-      for (int l = 0; l < P; ++l) {
-        ur = fmaf(c_b32_D[P][i * P + l], row[l], ur);
-        us = fmaf(c_b32_D[P][j * P + l], col[l], us);
-        ut = fmaf(c_b32_D[P][k * P + l], uc[l], ut);
-      }
-      const int q = k * P2 + lt;
-      const float g11 = sg[q], g22 = sg[P3 + q], g33 = sg[2 * P3 + q];
-      const float g12 = sg[3 * P3 + q], g13 = sg[4 * P3 + q], g23 = sg[5 * P3 + q];
-      swr[k * P2 + j * P + i] = h1 * (g11 * ur + g12 * us + g13 * ut);
-      swsT[k * P2 + i * P + j] = h1 * (g12 * ur + g22 * us + g23 * ut);
-      wt[k] = h1 * (g13 * ur + g23 * us + g33 * ut);
-    }
-  }
-  __syncthreads();
-  release();
-  if (act) {
-    float* we = w0 + (size_t)slot * P3;
-#pragma unroll
-    for (int k = 0; k < P; ++k) {
-      float row[P], col[P];
-      load_row_f<P>(swr + k * P2 + j * P, row);
-      load_row_f<P>(swsT + k * P2 + i * P, col);
-      float acc = 0.0f;
-#pragma unroll
-      for (int l = 0; l < P; ++l) {
-        acc = fmaf(c_b32_D[P][l * P + i], row[l], acc);
-        acc = fmaf(c_b32_D[P][l * P + j], col[l], acc);
-        acc = fmaf(c_b32_D[P][l * P + k], wt[l], acc);
-      }
-      if (helm) acc = fmaf(h2 * bk[k], uc[k], acc);
-      we[k * P2 + lt] = acc;
-    }
-  }
-}
-
 // Persistent bulk-copy Ax over every element of the problems of one order P;
 // CTAs of K P^2 threads take work items of K consecutive elements of one
 // problem and keep STAGES items in flight.
@@ -228,10 +136,30 @@ bax_kernel(const BProb* __restrict__ probs, const int* __restrict__ cls_prob,
       ahead = next(ahead + G);
     }
   }
+  constexpr int P2 = P * P;
+  const int slot = tid / P2;
+  auto Dm = [](int r, int c) { return c_b32_D[P][r * P + c]; };
+  TileThread<P, float> t;
+  t.init(tid - slot * P2, Dm);
+  float* sT = work + slot * P3;
+  float* swr = work + K * P3 + slot * P3;
+  float* swsT = work + 2 * K * P3 + slot * P3;
   int n = 0;
   for (long long g = next(blockIdx.x); g < Itot; g = next(g + G), ++n) {
     const int s = n % STAGES;
     const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)(n / STAGES) & 1u, err, timeout_ns);
+    const int c = find_prob(s_off, ncls, g);
+    const BProb& pr = probs[s_prob[c]];
+    const long long e0 = (g - s_off[c]) * K;
+    const int cnt = (int)min((long long)K, (long long)pr.E - e0);
+    const bool act = slot < cnt;
+    const bool helm = pr.h2 != 0.0f;
+    const float* stage = stage0 + s * SV;
+    const float* su = stage + slot * P3;
+    const float* sg = stage + K * P3 + slot * 6 * P3;
+    const float* sb = helm ? stage + 7 * K * P3 + slot * P3 : nullptr;
+    float uc[P], bk[P], ck[P], wt[P];
+    if (act) tile_load<P, float>(t, su, sb, nullptr, pr.h1, sT, uc, bk, ck);
     if (__syncthreads_or(!ok)) {
       if (tid == 0)
         for (int m = 1; m < STAGES; ++m)
@@ -239,19 +167,15 @@ bax_kernel(const BProb* __restrict__ probs, const int* __restrict__ cls_prob,
                             timeout_ns);
       return;
     }
-    const int c = find_prob(s_off, ncls, g);
-    const BProb& pr = probs[s_prob[c]];
-    const long long e0 = (g - s_off[c]) * K;
-    const int cnt = (int)min((long long)K, (long long)pr.E - e0);
-    auto release = [&]() {
-      if (tid == 0 && ahead < Itot) {
-        fence_proxy_async_smem();
-        issue(ahead, s);
-        ahead = next(ahead + G);
-      }
-    };
-    belem<P>(stage0 + s * SV, K, cnt, work, pr.w + e0 * P3, pr.h1, pr.h2, pr.h2 != 0.0f, tid,
-             release);
+    if (act) tile_forward<P, float>(t, su, sT, sg, uc, ck, swr, swsT, wt, Dm);
+    __syncthreads();
+    if (tid == 0 && ahead < Itot) {            // stage s consumed
+      fence_proxy_async_smem();
+      issue(ahead, s);
+      ahead = next(ahead + G);
+    }
+    if (act)
+      tile_backward<P, float>(t, swr, swsT, wt, uc, bk, pr.h2, helm, pr.w + (e0 + slot) * P3, Dm);
   }
 }
 
