@@ -47,18 +47,18 @@ def peaks():
 # FP64 Ax kernel on the 32^3, N=7 throughput mesh, from one ncu capture of the
 # kernel as it now stands (summary and command under profiles/); a kernel
 # variant that no capture covers reports null.
-AX_TRAFFIC = {"ax_df_kernel<8, 1>": 939_595_776 + 124_905_984}
+AX_TRAFFIC = {"ax_df_kernel<8, 1, 1>": 939_649_792 + 124_298_240}
 # smsp__inst_executed.sum per launch from the same capture: the double-float
 # kernel is bound by instruction issue on the FP32 pipe, so its second roof is
 # the issue rate, 152 SMs x 4 schedulers x the maximum SM clock.
-AX_WARP_INSTR = {"ax_df_kernel<8, 1>": 279_412_696}
+AX_WARP_INSTR = {"ax_df_kernel<8, 1, 1>": 306_102_072}
 ISSUE_PEAK = 152 * 4 * 2.07e9         # warp instructions per second
 
 
 def ax_kernel_name(tiles):
-    """The FP64 Ax kernel the autotuned handle launches at N=7 (double-float
-    arithmetic on the FP32 pipes, 1 or 2 shared-memory stages)."""
-    return f"ax_df_kernel<8, {tiles['f64_stages']}>"
+    """The FP64 element kernel of the operator step at N=7 (double-float
+    arithmetic on the FP32 pipes, 1 or 2 shared-memory stages, fused output)."""
+    return f"ax_df_kernel<8, {tiles['f64_stages']}, 1>"
 
 
 def ax_traffic(tiles):
@@ -197,6 +197,9 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--model-sweep", action="store_true",
+                    help="print the Eq. 12-13 cost model against measured kernel times for "
+                         "N = 2..9 instead of the benchmark line")
     ap.add_argument("--tiles", default=None,
                     help="pin the Ax tiles instead of autotuning: "
                          "<bulk-copy|global-load>:<fp32 stages>:<fp32 elements per CTA>:<fp64 stages>")
@@ -217,6 +220,10 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    if args.model_sweep:
+        if rank == 0:
+            print(json.dumps(run_model_sweep(sem, torch, dev)))
+        return 0
 
     cfg = WORKLOAD
     h = sem.sem_setup(cfg["nel"], cfg["N"], length=cfg["length"], deform=cfg["deform"])
@@ -236,20 +243,24 @@ def main():
     w32 = torch.empty_like(u32)
 
     def step64():
-        sem.sem_ax(h, u, w)
-        sem.sem_dssum(h, w, apply_mask=True)
+        sem.sem_apply(h, u, w)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
+    def ev3():
+        return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+                 torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+
     for _ in range(args.warmup):
         step64()
     barrier()
     K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    # a step is the assembled operator, split into its element phase (Ax with
+    # the x-face sums) and its finishing gather-scatter passes by events
+    ev = ev3()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -257,9 +268,9 @@ def main():
         t0.record(stream)
         for s in range(K):
             ev[s][0].record(stream)
-            sem.sem_ax(h, u, w)
+            sem.sem_apply(h, u, w, phase=sem.SEM_APPLY_LOCAL)
             ev[s][1].record(stream)
-            sem.sem_dssum(h, w, apply_mask=True)
+            sem.sem_apply(h, u, w, phase=sem.SEM_APPLY_FINISH)
             ev[s][2].record(stream)
         t1.record(stream)
         barrier()
@@ -272,22 +283,27 @@ def main():
     ms = float(ms_t)
     value = world * n * K / (ms / 1e3) / 1e9
 
-    # FP32 operator
-    for _ in range(3):
-        sem.sem_ax(h, u32, w32)
-        sem.sem_dssum(h, w32, apply_mask=True)
-    torch.cuda.synchronize()
-    e32 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-            torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    for s in range(K):
-        e32[s][0].record(stream)
-        sem.sem_ax(h, u32, w32)
-        e32[s][1].record(stream)
-        sem.sem_dssum(h, w32, apply_mask=True)
-        e32[s][2].record(stream)
-    torch.cuda.synchronize()
-    ax32 = statistics.mean(a.elapsed_time(b) for a, b, _ in e32)
-    ds32 = statistics.mean(b.elapsed_time(c) for _, b, c in e32)
+    def split_times(local, finish, warm=3):
+        for _ in range(warm):
+            local()
+            finish()
+        torch.cuda.synchronize()
+        e = ev3()
+        for s in range(K):
+            e[s][0].record(stream)
+            local()
+            e[s][1].record(stream)
+            finish()
+            e[s][2].record(stream)
+        torch.cuda.synchronize()
+        return (statistics.mean(a.elapsed_time(b) for a, b, _ in e),
+                statistics.mean(b.elapsed_time(c) for _, b, c in e))
+
+    # FP32 operator, and both precisions as element kernel + separate gather-scatter
+    ax32, ds32 = split_times(lambda: sem.sem_apply(h, u32, w32, phase=sem.SEM_APPLY_LOCAL),
+                             lambda: sem.sem_apply(h, u32, w32, phase=sem.SEM_APPLY_FINISH))
+    sep64 = split_times(lambda: sem.sem_ax(h, u, w), lambda: sem.sem_dssum(h, w))
+    sep32 = split_times(lambda: sem.sem_ax(h, u32, w32), lambda: sem.sem_dssum(h, w32))
 
     # end to end through the host-buffer call
     w_host = torch.empty_like(u_host).pin_memory()
@@ -323,16 +339,21 @@ def main():
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": ax_bytes},
         "alu": alu_roof(tiles, ax_ms),
-        "kernels": {"ax_f64_ms": ax_ms, "dssum_f64_ms": ds_ms,
-                    "dssum_f64_gbs": ds_bytes / (ds_ms / 1e3) / 1e9,
+        "kernels": {"ax_f64_ms": ax_ms, "gs_finish_f64_ms": ds_ms,
                     "ax_f32_ms": ax32, "ax_f32_gbs": 32 * n / (ax32 / 1e3) / 1e9,
                     "ax_f32_frac": 32 * n / (ax32 / 1e3) / 1e9 / hbm,
-                    "dssum_f32_ms": ds32,
+                    "gs_finish_f32_ms": ds32,
                     "ax_f64_gdofs": n / (ax_ms / 1e3) / 1e9,
-                    "axdssum_f32_gdofs": n / ((ax32 + ds32) / 1e3) / 1e9},
+                    "operator_f32_gdofs": n / ((ax32 + ds32) / 1e3) / 1e9,
+                    "separate": {"note": "sem_ax then sem_dssum (increasing-index gather-scatter)",
+                                 "ax_f64_ms": sep64[0], "dssum_f64_ms": sep64[1],
+                                 "dssum_f64_gbs": ds_bytes / (sep64[1] / 1e3) / 1e9,
+                                 "ax_f32_ms": sep32[0], "dssum_f32_ms": sep32[1],
+                                 "operator_f64_gdofs": n / (sum(sep64) / 1e3) / 1e9,
+                                 "operator_f32_gdofs": n / (sum(sep32) / 1e3) / 1e9}},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
-        "gpu_launches": 2 * K,
+        "gpu_launches": 4 * K,              # element kernel + 3 gather-scatter passes
         "autotune": tiles,
         "clocks": clk.summary(),
     }
@@ -533,6 +554,75 @@ def run_adjoint(sem, torch, dev):
             "local_points": n,
             "forward_backward_seconds": sec, "fd": fd, "grad_dot_dir": gd,
             "fd_rel_diff": abs(fd - gd) / abs(fd)}
+
+
+# ---------------------------------------------------------------- cost model
+FP64_PEAK = 1.20e12        # FLOP/s, FMA probe on this GB300 (independent FMA chains)
+FP32_PEAK = 71.4e12
+
+
+def model_costs(N, fp64):
+    """Eq. 12 per local point: W (adds + mults) and Q (bytes loaded and stored,
+    cold cache) of the element operator and of the gather-scatter."""
+    P = N + 1
+    wsz = 8 if fp64 else 4
+    W_ax = 3 * (2 * P - 1) + 15 + 3 * (2 * P - 1) + 2      # D, G (9 mult 6 add), D^T, sum
+    Q_ax = (1 + 1 + 6) * wsz                              # u, w, G
+    shared = 1.0 - ((P - 2) / P) ** 3 if P > 2 else 1.0   # interior elements
+    W_gs = 0.5 * shared                                   # one add per extra copy
+    Q_gs = 2 * wsz * shared                               # read + write of shared copies
+    return W_ax, Q_ax, W_gs, Q_gs
+
+
+def run_model_sweep(sem, torch, dev, target_points=16_777_216, reps=20):
+    """Eq. 13 (T = max(W / pi, Q / beta)) against the measured kernel times for
+    N = 2..9 on deformed boxes of about target_points local points."""
+    beta = peaks()[0] * 1e9
+    rows = []
+    for N in range(2, 10):
+        P = N + 1
+        nel = si.near_cubic_box(target_points / P ** 3, max_side=128)
+        h = sem.sem_setup(nel, N, length=(si.TWO_PI,) * 3, deform=0.1)
+        sem.sem_autotune(h)
+        n = h.n_local
+        row = {"N": N, "nel": list(nel), "local_points": n}
+        for fp64 in (True, False):
+            dt = torch.float64 if fp64 else torch.float32
+            u = torch.rand(n, dtype=dt, device=dev) - 0.5
+            w = torch.empty_like(u)
+            W_ax, Q_ax, W_gs, Q_gs = model_costs(N, fp64)
+            pi = FP64_PEAK if fp64 else FP32_PEAK
+            kinds = [("ax", lambda: sem.sem_ax(h, u, w), W_ax, Q_ax),
+                     ("dssum", lambda: sem.sem_dssum(h, w), W_gs, Q_gs),
+                     ("apply", lambda: sem.sem_apply(h, u, w), W_ax + W_gs, Q_ax + Q_gs)]
+            if fp64:
+                def native():
+                    sem.sem_set_f64_kernel(h, sem.SEM_F64_KERNEL_NATIVE)
+                    sem.sem_ax(h, u, w)
+                    sem.sem_set_f64_kernel(h, sem.SEM_F64_KERNEL_AUTO)
+                kinds.append(("ax_native", native, W_ax, Q_ax))
+            tag = "f64" if fp64 else "f32"
+            for name, fn, W, Q in kinds:
+                for _ in range(3):
+                    fn()
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(reps):
+                    fn()
+                b.record()
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b) / reps
+                t_model = max(W * n / pi, Q * n / beta) * 1e3
+                row[f"{name}_{tag}"] = {"ms": ms, "model_ms": t_model,
+                                        "bound": "flops" if W * n / pi > Q * n / beta else "bytes",
+                                        "measured_over_model": ms / t_model}
+            del u, w
+        sem.sem_destroy(h)
+        rows.append(row)
+    return {"model": "Eq. 13: T = max(W / pi, Q / beta), cold cache, per kernel",
+            "pi_fp64": FP64_PEAK, "pi_fp32": FP32_PEAK, "beta": beta, "rows": rows}
 
 
 if __name__ == "__main__":

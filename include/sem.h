@@ -66,6 +66,12 @@ enum { SEM_DSSUM_BOX = 0,       /* copies computed from the box topology (defaul
        SEM_DSSUM_SEGMENTS = 1   /* precomputed segment lists of shared local points */
 };
 
+/* phases of sem_apply */
+enum { SEM_APPLY_LOCAL = 1,     /* element operator, x-neighbour sums inside CTAs, mask */
+       SEM_APPLY_FINISH = 2,    /* remaining gather-scatter passes */
+       SEM_APPLY_FULL = 3       /* both */
+};
+
 /* Dirichlet face bits */
 enum { SEM_FACE_XMIN = 1, SEM_FACE_XMAX = 2, SEM_FACE_YMIN = 4,
        SEM_FACE_YMAX = 8, SEM_FACE_ZMIN = 16, SEM_FACE_ZMAX = 32,
@@ -199,6 +205,28 @@ sem_status sem_autotune(sem_handle* h, void* stream, sem_tuning* out);
 sem_status sem_set_tuning(sem_handle* h, const sem_tuning* t);
 
 /*
+ * sem_apply -- the assembled operator w_L = mask o QQ^T (h1 A_L + h2 B_L) u_L
+ * (§2, Eq. 9-10; one CG matvec), the same result as sem_ax followed by
+ * sem_dssum with the mask, computed with the gather-scatter split by
+ * direction.  The element kernel walks segments of four consecutive
+ * elements per CTA and sums the copies of x-interface points inside a
+ * segment itself; short passes then add the x-pairs between segments and
+ * the y- and z-pairs.  The copies of a point on several interfaces are summed
+ * pair by pair, (w0 + w1) + (w2 + w3) ..., so FP64 results can differ from
+ * sem_dssum's increasing-index order in the last bits.
+ * phase: SEM_APPLY_FULL, or SEM_APPLY_LOCAL then SEM_APPLY_FINISH (the
+ * finish phase must follow a local phase on the same handle, dtype and
+ * vectors; splitting lets a caller time or overlap the two).  Orders,
+ * dtypes or alignments the fused kernels do not cover (odd N, the native
+ * FP64 kernel, a per-point h1 in FP64) run sem_ax and sem_dssum's kernels
+ * instead, the local phase being the element operator and the finish phase
+ * the whole gather-scatter.  u_L and w_L are distinct L-vectors of the
+ * dtype (SEM_F64 or SEM_F32); SEM_ERR_ARG otherwise.
+ */
+sem_status sem_apply(sem_handle* h, const void* u_L, void* w_L, double h1, double h2,
+                     const void* h1_field, int dtype, int phase, void* stream);
+
+/*
  * sem_dssum -- in place w_L <- QQ^T w_L: every local copy of a global point
  * receives the sum of all its copies, summed in increasing local index
  * (§2, Eq. 10; §3.2).  With apply_mask != 0 the Dirichlet points are then
@@ -319,9 +347,9 @@ sem_status sem_dot_noalloc(sem_handle* h, const double* a, const double* b, doub
 
 /*
  * sem_apply_host -- w = mask o QQ^T A_L u with HOST buffers: copies u_host
- * (n_L values of dtype) to the device, applies Ax and dssum with the mask,
- * copies the result to w_host and synchronises the stream.  Pinned host
- * memory gives full copy bandwidth.
+ * (n_L values of dtype) to the device, applies the assembled operator as
+ * sem_apply does, copies the result to w_host and synchronises the stream.
+ * Pinned host memory gives full copy bandwidth.
  */
 sem_status sem_apply_host(sem_handle* h, const void* u_host, void* w_host, int dtype,
                           void* stream);

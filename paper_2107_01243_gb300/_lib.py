@@ -23,6 +23,7 @@ SEM_SOLVE_F64, SEM_SOLVE_MIXED = 0, 1
 SEM_FACE_ALL = 63
 SEM_F64_KERNEL_AUTO, SEM_F64_KERNEL_NATIVE, SEM_F64_KERNEL_DOUBLEFLOAT = 0, 1, 2
 SEM_DSSUM_BOX, SEM_DSSUM_SEGMENTS = 0, 1
+SEM_APPLY_LOCAL, SEM_APPLY_FINISH, SEM_APPLY_FULL = 1, 2, 3
 (SEM_FIELD_X, SEM_FIELD_Y, SEM_FIELD_Z, SEM_FIELD_G, SEM_FIELD_B, SEM_FIELD_MULT,
  SEM_FIELD_MASK, SEM_FIELD_GID, SEM_FIELD_DINV) = range(9)
 
@@ -74,6 +75,8 @@ SIGNATURES = {
     "sem_ax": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P, ctypes.c_int,
                               _P]),
     "sem_dssum": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P]),
+    "sem_apply": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P,
+                                 ctypes.c_int, ctypes.c_int, _P]),
     "sem_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
     "sem_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "sem_cg_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(SolveOpts),

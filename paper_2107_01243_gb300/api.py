@@ -122,6 +122,16 @@ def sem_ax(h, u, w, h1=1.0, h2=0.0, h1_field=None, stream=None):
     return w
 
 
+def sem_apply(h, u, w, h1=1.0, h2=0.0, h1_field=None, phase=_lib.SEM_APPLY_FULL, stream=None):
+    """w = mask o QQ^T (h1 A_L + h2 B_L) u: the assembled operator (one CG matvec)."""
+    pu = h._vec(u, "u")
+    pw = h._vec(w, "w", u.dtype)
+    pf = h._vec(h1_field, "h1_field", u.dtype) if h1_field is not None else None
+    check(_lib.load().sem_apply(h.ptr, pu, pw, float(h1), float(h2), pf, _dtype_code(u),
+                                int(phase), _stream(stream)))
+    return w
+
+
 def sem_dssum(h, w, apply_mask=True, stream=None):
     """In place w <- QQ^T w (then the Dirichlet mask if apply_mask)."""
     pw = h._vec(w, "w")

@@ -1,0 +1,225 @@
+// The assembled operator w = mask o QQ^T (h1 A_L + h2 B_L) u (arXiv 2107.01243
+// §2, Eq. 9-10) with the gather-scatter split by direction.  On the box,
+// QQ^T is the product of three commuting pair sums, one per direction: the
+// copies of a point on an x-interface are the i = N value of element e and
+// the i = 0 value of element e + 1, and so on for y (e + nelx) and z
+// (e + nelx nely).  Summing the x-pairs, then the y-pairs, then the z-pairs
+// gives every copy the sum of all its copies (2, 4 or 8).
+//
+//   local   the element kernel walks segments of kFuseSeg consecutive elements
+//           per CTA and sums the x-pairs inside a segment itself (the upper
+//           element reads back the copy the lower one stored just before);
+//           masked points are written as zero
+//   finish  k_sx_cut: x-pairs between segments;
+//           k_sy, k_sz: the y- and z-pairs, each a coalesced sweep over the
+//           j = N / k = N planes of the elements and their neighbours' j = 0 /
+//           k = 0 planes
+//
+// The x-face copies are 8-byte values 64 bytes apart (P = 8), so a separate
+// gather-scatter spends a 32-byte sector on each; here they never leave the
+// element kernel.  Summation order: ((x-pairs) + (x-pairs)) + ..., i.e. the
+// copies of an edge point are added as (w0 + w1) + (w2 + w3); sem_dssum keeps
+// the increasing-index order instead.
+#include "sem_internal.cuh"
+#include <type_traits>
+
+#include "ax_tile.cuh"
+
+namespace sem {
+
+int launch_ax_tma_fused(const sem_handle* h, const float* u, float* w, float h1, float h2,
+                        const float* h1f, const CGState* st, cudaStream_t s);
+int launch_ax_df_fused(const sem_handle* h, const double* u, double* w, double h1, double h2,
+                       const CGState* st, cudaStream_t s);
+bool df_ax_supported(const sem_handle* h, const void* u, const void* w, const void* h1f);
+
+namespace {
+
+// x-pairs at the segment starts of the element kernel: the first element
+// e_b = g kFuseSeg of segment g >= 1 pairs its i = 0 face with the i = N face
+// of the element before it, unless it starts an x-row.  One block per segment
+// start.
+template <int P, class T>
+__global__ void __launch_bounds__(P * P)
+k_sx_cut(T* __restrict__ w, int nelx, const CGState* __restrict__ st) {
+  if (st && st->done) return;
+  constexpr int P2 = P * P;
+  constexpr long long P3 = (long long)P2 * P;
+  const long long eb = (long long)(blockIdx.x + 1) * kFuseSeg;
+  if (eb % nelx == 0) return;
+  const int j = threadIdx.x % P, k = threadIdx.x / P;
+  const long long hi = eb * P3 + (long long)k * P2 + j * P;    // (eb, 0, j, k)
+  const long long lo = hi - P3 + (P - 1);                       // (eb - 1, N, j, k)
+  const T sum = w[lo] + w[hi];
+  w[lo] = sum;
+  w[hi] = sum;
+}
+
+template <class T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using V = float2;
+};
+template <>
+struct Vec2<double> {
+  using V = double2;
+};
+
+// y-pairs: (e, i, N, k) + (e + nelx, i, 0, k) for every element with
+// ey < nely - 1; a thread takes two neighbouring i (P is even), threads run
+// over (i pair, k, element) with the i pair fastest
+template <int P, class T>
+__global__ void __launch_bounds__(256)
+k_sy(T* __restrict__ w, int nelx, int nely, uint32_t total, FastDiv dnx, FastDiv dny1,
+     const CGState* __restrict__ st) {
+  if (st && st->done) return;
+  using V = typename Vec2<T>::V;
+  constexpr int H = P / 2, P2 = P * P, P3 = P2 * P;
+  V* wv = reinterpret_cast<V*>(w);
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += gridDim.x * blockDim.x) {
+    const uint32_t ip = t % H, r = t / H;
+    const uint32_t k = r % P, m = r / P;            // element among those with ey < nely - 1
+    const uint32_t r2 = dnx.div(m);
+    const uint32_t ex = m - r2 * (uint32_t)nelx;
+    const uint32_t ez = dny1.div(r2);
+    const uint32_t ey = r2 - ez * (uint32_t)(nely - 1);
+    const uint32_t e = ex + (uint32_t)nelx * (ey + (uint32_t)nely * ez);
+    const uint32_t lo = (e * P3 + k * P2 + (P - 1) * P) / 2 + ip;
+    const uint32_t hi = ((e + nelx) * P3 + k * P2) / 2 + ip;
+    const V a = wv[lo], b = wv[hi];
+    const V sum = {a.x + b.x, a.y + b.y};
+    wv[lo] = sum;
+    wv[hi] = sum;
+  }
+}
+
+// z-pairs: (e, i, j, N) + (e + nelx nely, i, j, 0) for every element with
+// ez < nelz - 1 (the first nelx nely (nelz - 1) elements); 16 bytes per thread
+template <int P, class T>
+__global__ void __launch_bounds__(256)
+k_sz(T* __restrict__ w, uint32_t layer, uint32_t total, const CGState* __restrict__ st) {
+  if (st && st->done) return;
+  constexpr int VW = 16 / (int)sizeof(T), P2 = P * P, P3 = P2 * P, Q = P2 / VW;
+  static_assert(P2 % VW == 0, "plane not a whole number of 16-byte vectors");
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  V* wv = reinterpret_cast<V*>(w);
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += gridDim.x * blockDim.x) {
+    const uint32_t q = t % Q, e = t / Q;
+    const uint32_t lo = (e * P3 + (P - 1) * P2) / VW + q;
+    const uint32_t hi = ((e + layer) * P3) / VW + q;
+    V a = wv[lo];
+    const V b = wv[hi];
+    T* ap = reinterpret_cast<T*>(&a);
+    const T* bp = reinterpret_cast<const T*>(&b);
+#pragma unroll
+    for (int c = 0; c < VW; ++c) ap[c] = ap[c] + bp[c];
+    wv[lo] = a;
+    wv[hi] = a;
+  }
+}
+
+int sweep_blocks(long long total) {
+  return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 16LL * kNumSMs));
+}
+
+template <int P, class T>
+void finish_p(const sem_handle* h, T* w, const CGState* st, cudaStream_t s) {
+  const long long nseg = (h->E + kFuseSeg - 1) / kFuseSeg;
+  if (nseg > 1 && h->nelx > 1) {
+    k_sx_cut<P, T><<<(unsigned)(nseg - 1), P * P, 0, s>>>(w, h->nelx, st);
+    SEM_CHECK_LAUNCH();
+  }
+  if (h->nely > 1) {
+    const long long total = (long long)h->nelx * (h->nely - 1) * h->nelz * P * (P / 2);
+    k_sy<P, T><<<sweep_blocks(total), 256, 0, s>>>(
+        w, h->nelx, h->nely, (uint32_t)total, FastDiv((uint32_t)h->nelx),
+        FastDiv((uint32_t)(h->nely - 1)), st);
+    SEM_CHECK_LAUNCH();
+  }
+  if (h->nelz > 1) {
+    const long long layer = (long long)h->nelx * h->nely;
+    const long long total = layer * (h->nelz - 1) * P * P / (16 / (int)sizeof(T));
+    k_sz<P, T><<<sweep_blocks(total), 256, 0, s>>>(w, (uint32_t)layer, (uint32_t)total, st);
+    SEM_CHECK_LAUNCH();
+  }
+}
+
+template <class T>
+void finish(const sem_handle* h, T* w, const CGState* st, cudaStream_t s) {
+  switch (h->P) {
+    case 2: finish_p<2, T>(h, w, st, s); break;
+    case 4: finish_p<4, T>(h, w, st, s); break;
+    case 6: finish_p<6, T>(h, w, st, s); break;
+    case 8: finish_p<8, T>(h, w, st, s); break;
+    case 10: finish_p<10, T>(h, w, st, s); break;
+    default: throw Error(SEM_ERR_ARG, "apply: unsupported order");
+  }
+}
+
+}  // namespace
+
+template <>
+bool apply_fused_supported<float>(const sem_handle* h, const void* u, const void* w,
+                                  const void* h1f) {
+  return h->f32.G.ptr && tma_ax_supported<float>(h, u, w, h1f) && h->nL < (1LL << 31);
+}
+
+template <>
+bool apply_fused_supported<double>(const sem_handle* h, const void* u, const void* w,
+                                   const void* h1f) {
+  return h->f64_kernel != SEM_F64_KERNEL_NATIVE && df_ax_supported(h, u, w, h1f) &&
+         h->nL < (1LL << 31);
+}
+
+template <class T>
+void launch_apply(sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2, const T* h1f,
+                  const CGState* st, int phase, cudaStream_t s) {
+  if (!apply_fused_supported<T>(h, u, w, h1f)) {
+    // element kernel and the gather-scatter kernel, in the full phase
+    if (phase & SEM_APPLY_LOCAL) launch_ax<T>(h, op, u, w, h1, h2, h1f, st, s);
+    if (phase & SEM_APPLY_FINISH) launch_dssum<T>(h, w, true, st, s);
+    return;
+  }
+  if (phase & SEM_APPLY_LOCAL) {
+    if constexpr (std::is_same<T, float>::value)
+      launch_ax_tma_fused(h, u, w, h1, h2, h1f, st, s);
+    else
+      launch_ax_df_fused(h, u, w, h1, h2, st, s);
+  }
+  if (phase & SEM_APPLY_FINISH) finish<T>(h, w, st, s);
+}
+
+template void launch_apply<float>(sem_handle*, const OpData<float>&, const float*, float*, float,
+                                  float, const float*, const CGState*, int, cudaStream_t);
+template void launch_apply<double>(sem_handle*, const OpData<double>&, const double*, double*,
+                                   double, double, const double*, const CGState*, int,
+                                   cudaStream_t);
+
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" sem_status sem_apply(sem_handle* h, const void* u_L, void* w_L, double h1, double h2,
+                                const void* h1_field, int dtype, int phase, void* stream) {
+  return guarded([&] {
+    SEM_REQUIRE(h && u_L && w_L, "sem_apply: null argument");
+    SEM_REQUIRE(phase == SEM_APPLY_FULL || phase == SEM_APPLY_LOCAL || phase == SEM_APPLY_FINISH,
+                "sem_apply: phase must be SEM_APPLY_FULL, _LOCAL or _FINISH");
+    SEM_REQUIRE(u_L != w_L, "sem_apply: u and w must not alias");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == SEM_F64) {
+      SEM_REQUIRE(h->f64.G.ptr, "sem_apply: handle has no FP64 geometry");
+      launch_apply<double>(h, h->f64, (const double*)u_L, (double*)w_L, h1, h2,
+                           (const double*)h1_field, nullptr, phase, s);
+    } else if (dtype == SEM_F32) {
+      SEM_REQUIRE(h->f32.G.ptr, "sem_apply: handle has no FP32 geometry");
+      launch_apply<float>(h, h->f32, (const float*)u_L, (float*)w_L, (float)h1, (float)h2,
+                          (const float*)h1_field, nullptr, phase, s);
+    } else {
+      throw Error(SEM_ERR_ARG, "sem_apply: dtype must be SEM_F64 or SEM_F32");
+    }
+  });
+}

@@ -22,6 +22,7 @@
 #include "sem_internal.cuh"
 #include "tma.cuh"
 #include "df.cuh"
+#include "ax_tile.cuh"
 
 namespace sem {
 
@@ -114,11 +115,15 @@ __device__ __forceinline__ void dot3_df(float2 g0, float2 g1, float2 g2, float2 
 
 // Three groups of P x P threads, one per direction, run the line tasks of the
 // r-, s- and t-direction side by side.
-template <int P, int STAGES>
-__global__ void __launch_bounds__(3 * P * P)
+//
+// FUSE: the CTA walks segments of kFuseSeg consecutive elements and writes
+// the fused output (FusedStore: mask, x-neighbour pairs of the segment summed
+// in the CTA) for the assembled operator of apply.cu.
+template <int P, int STAGES, bool FUSE>
+__global__ void __launch_bounds__(3 * P * P, P == 8 ? 5 : 1)     // P = 8: five CTAs per SM
 ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2* __restrict__ G,
              const float2* __restrict__ B, DFScal C, int E, const CGState* __restrict__ st,
-             int* __restrict__ err, uint64_t timeout_ns) {
+             int* __restrict__ err, uint64_t timeout_ns, FuseBox fb) {
   using L = DFLayout<P>;
   constexpr int P2 = P * P, P3 = P2 * P, NT = 3 * P2;
   constexpr uint32_t UB = P3 * sizeof(double), GB = 6 * P3 * sizeof(float2),
@@ -149,6 +154,7 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     qoff[m] = q < P3 ? L::at(q % P, (q / P) % P, q / P2) : 0;
   }
   float2* myR = g == 0 ? R[0] : (g == 1 ? R[1] : R[2]);
+  const ItemSeq<FUSE> seq{E};          // this CTA's elements in order
 
   auto issue = [&](int e, int s) {
     unsigned char* dst = stage0 + s * SB;
@@ -163,16 +169,22 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     mbar_fence_init();
   }
   __syncthreads();
+  int ahead = seq.first(), issued = 0;     // thread 0: next element to prefetch, copies issued
   if (tid == 0) {
 #pragma unroll
     for (int s = 0; s < STAGES; ++s) {
-      int e = blockIdx.x + s * gridDim.x;
-      if (e < E) issue(e, s);
+      if (ahead < E) {
+        issue(ahead, s);
+        ahead = seq.next(ahead);
+        ++issued;
+      }
     }
   }
 
+  BoxWalk bw;                          // thread 0 (FUSE)
+  __shared__ unsigned s_fl;            // FusedStore flags of the current element
   int n = 0;
-  for (int e = blockIdx.x; e < E; e += gridDim.x, ++n) {
+  for (int e = seq.first(); e < E; e = seq.next(e), ++n) {
     const int s = n % STAGES;
     const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)(n / STAGES) & 1u, err, timeout_ns);
     const double* su = reinterpret_cast<const double*>(stage0 + s * SB);
@@ -190,13 +202,14 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     }
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
-        for (int m = 0; m < STAGES; ++m) {
-          int nn = n + m;
-          if (blockIdx.x + nn * gridDim.x < E)
-            mbar_wait_bounded(&bar[nn % STAGES], (uint32_t)(nn / STAGES) & 1u, err, timeout_ns);
-        }
+        for (int nn = n; nn < issued; ++nn)
+          mbar_wait_bounded(&bar[nn % STAGES], (uint32_t)(nn / STAGES) & 1u, err, timeout_ns);
       }
       return;
+    }
+    if (FUSE && tid == 0) {            // box position of e, read back in the output phase
+      if (e % kFuseSeg == 0) bw.start(e, fb); else bw.step(fb);
+      s_fl = fused_flags(e, bw, fb);
     }
     // forward derivatives: group g differentiates along direction g
     line_task<P, false>(U, myR, loff);
@@ -225,10 +238,11 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     }
     __syncthreads();
     if (!helm && tid == 0) {                   // stage s consumed
-      int en = e + STAGES * gridDim.x;
-      if (en < E) {
+      if (ahead < E) {
         fence_proxy_async_smem();
-        issue(en, s);
+        issue(ahead, s);
+        ahead = seq.next(ahead);
+        ++issued;
       }
     }
     // transposed derivatives, in place: group g along direction g
@@ -236,6 +250,11 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     __syncthreads();
     // w = CR + CS + CT (+ h2 B u) -> double
     double* we = w + (size_t)e * P3;
+    FusedStore<P, double> fs;
+    if constexpr (FUSE) {
+      fs.we = we;
+      fs.fl = s_fl;
+    }
 #pragma unroll
     for (int m = 0; m < NQ; ++m) {
       const int q = tid + m * NT;
@@ -251,15 +270,20 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
         dfmul(C.h2h, C.h2l, bv.x, bv.y, bh, bl);
         tmac(bh, bl, uv.x, uv.y, S, er);
       }
-      we[q] = (double)S + (double)er;          // exact widenings, one rounding
+      const double val = (double)S + (double)er;   // exact widenings, one rounding
+      if constexpr (FUSE)
+        fs.store(q % P, (q / P) % P, q / P2, val);
+      else
+        we[q] = val;
     }
     if (helm) {
       __syncthreads();                         // U and the stage are free
       if (tid == 0) {
-        int en = e + STAGES * gridDim.x;
-        if (en < E) {
+        if (ahead < E) {
           fence_proxy_async_smem();
-          issue(en, s);
+          issue(ahead, s);
+          ahead = seq.next(ahead);
+          ++issued;
         }
       }
     }
@@ -318,12 +342,13 @@ static void df_upload_d(const sem_handle* h) {
   done[P] = true;
 }
 
-template <int P, int STAGES>
-static void launch_df_p(const sem_handle* h, const double* u, double* w, double h1, double h2,
-                        const CGState* st, cudaStream_t s) {
+// returns the grid it launched (the fused operator's later passes need it)
+template <int P, int STAGES, bool FUSE = false>
+static int launch_df_p(const sem_handle* h, const double* u, double* w, double h1, double h2,
+                       const CGState* st, cudaStream_t s) {
   const bool helm = (float)h2 != 0.0f;
   const size_t smem = df_smem_bytes<P, STAGES>(helm);
-  auto kern = ax_df_kernel<P, STAGES>;
+  auto kern = ax_df_kernel<P, STAGES, FUSE>;
   static bool configured = false;
   static int occ[2] = {0, 0};
   if (!configured) {
@@ -347,9 +372,11 @@ static void launch_df_p(const sem_handle* h, const double* u, double* w, double 
   const int E = (int)h->E;
   int grid = (int)std::min<int64_t>(E, (int64_t)o * df_num_sms());
   if (grid < 1) grid = 1;
+  const FuseBox fb{h->nelx, h->nely, h->nelz, h->faces};
   kern<<<grid, 3 * P * P, smem, s>>>(u, w, h->gdf.ptr, h->bdf.ptr, c, E, st, h->dev_err.ptr,
-                                     kWaitTimeoutNs);
+                                     kWaitTimeoutNs, fb);
   SEM_CHECK_LAUNCH();
+  return grid;
 }
 
 bool df_ax_supported(const sem_handle* h, const void* u, const void* w, const void* h1f) {
@@ -375,6 +402,20 @@ void launch_ax_df(const sem_handle* h, const double* u, double* w, double h1, do
       else launch_df_p<10, 1>(h, u, w, h1, h2, st, s);
       break;
     default: throw Error(SEM_ERR_ARG, "launch_ax_df: unsupported order");
+  }
+}
+
+int launch_ax_df_fused(const sem_handle* h, const double* u, double* w, double h1, double h2,
+                       const CGState* st, cudaStream_t s) {
+  const bool two = h->tune.df_variant != 0;
+  switch (h->P) {
+    case 6: return two ? launch_df_p<6, 2, true>(h, u, w, h1, h2, st, s)
+                       : launch_df_p<6, 1, true>(h, u, w, h1, h2, st, s);
+    case 8: return two ? launch_df_p<8, 2, true>(h, u, w, h1, h2, st, s)
+                       : launch_df_p<8, 1, true>(h, u, w, h1, h2, st, s);
+    case 10: return two ? launch_df_p<10, 2, true>(h, u, w, h1, h2, st, s)
+                        : launch_df_p<10, 1, true>(h, u, w, h1, h2, st, s);
+    default: throw Error(SEM_ERR_ARG, "launch_ax_df_fused: unsupported order");
   }
 }
 

@@ -132,11 +132,13 @@ __device__ __forceinline__ void tile_forward(const TileThread<P, T>& t, const T*
   }
 }
 
-// transposed contractions (+ h2 B u) into the element's output we
-template <int P, class T, class DF>
+// transposed contractions (+ h2 B u); store(k, value) receives the output of
+// point (i, j, k)
+template <int P, class T, class DF, class ST>
 __device__ __forceinline__ void tile_backward(const TileThread<P, T>& t, const T* swr,
                                               const T* swsT, const T (&wt)[P], const T (&uc)[P],
-                                              const T (&bk)[P], T h2, bool helm, T* we, DF D) {
+                                              const T (&bk)[P], T h2, bool helm, DF D,
+                                              ST store) {
   constexpr int P2 = P * P;
 #pragma unroll
   for (int k = 0; k < P; ++k) {
@@ -151,8 +153,100 @@ __device__ __forceinline__ void tile_backward(const TileThread<P, T>& t, const T
       acc = fma(D(l, k), wt[l], acc);
     }
     if (helm) acc = fma(h2 * bk[k], uc[k], acc);
-    we[k * P2 + t.lt] = acc;
+    store(k, acc);
   }
 }
+
+// Box position of element e and the Dirichlet faces, for the operator kernels
+// that apply the mask and sum x-neighbour pairs themselves (apply.cu).
+struct FuseBox {
+  int nelx, nely, nelz, faces;
+};
+
+// Elements per segment of the fused operator: a CTA takes segments of
+// kFuseSeg consecutive elements, segment g = blockIdx.x + m gridDim.x, so
+// that the x-neighbour pairs inside a segment are summed in the CTA while all
+// CTAs together stream one contiguous window of memory (whole per-CTA ranges
+// spread the streams over the address space and ran 25-45% slower).
+constexpr int kFuseSeg = 4;
+
+// The items a persistent CTA walks: blockIdx.x + m gridDim.x, or (SEG) the
+// items of its segments in order
+template <bool SEG>
+struct ItemSeq {
+  int n;   // number of items
+  __device__ __forceinline__ int first() const {
+    return SEG ? (int)blockIdx.x * kFuseSeg : (int)blockIdx.x;
+  }
+  __device__ __forceinline__ int next(int it) const {
+    if (!SEG) return it + (int)gridDim.x;
+    const int nx = it + 1;
+    if (nx % kFuseSeg != 0 && nx < n) return nx;
+    return (it / kFuseSeg + (int)gridDim.x) * kFuseSeg;
+  }
+};
+
+// box position of the elements a CTA walks in order: set at the start of a
+// segment, then stepped (no divisions per element)
+struct BoxWalk {
+  int ex, ey, ez;
+  __device__ __forceinline__ void start(int e, const FuseBox& b) {
+    ex = e % b.nelx;
+    const int r = e / b.nelx;
+    ey = r % b.nely;
+    ez = r / b.nely;
+  }
+  __device__ __forceinline__ void step(const FuseBox& b) {
+    if (++ex == b.nelx) {
+      ex = 0;
+      if (++ey == b.nely) {
+        ey = 0;
+        ++ez;
+      }
+    }
+  }
+};
+
+// The fused output of one element e: masked points are zeroed, and when the
+// element before it (e - 1, the -x neighbour) came just before in the same
+// segment of the same CTA, each point of the i = 0 face is summed with e - 1's
+// copy at i = N (lower element first), read back from w where e - 1's threads
+// stored it before the CTA's last barrier, and the sum goes to both copies.
+// FusedStore flags of element e at the walk's box position: bit 0 pairs it
+// with e - 1 (same segment, not the first of an x-row), bits 2-7 its faces on
+// Dirichlet boundaries (XMIN, XMAX, YMIN, YMAX, ZMIN, ZMAX)
+__device__ __forceinline__ unsigned fused_flags(int e, const BoxWalk& bw, const FuseBox& b) {
+  unsigned fl = (bw.ex > 0 && e % kFuseSeg != 0) ? 1u : 0u;
+  if (b.faces) {
+    fl |= ((b.faces & SEM_FACE_XMIN) && bw.ex == 0 ? 4u : 0u) |
+          ((b.faces & SEM_FACE_XMAX) && bw.ex == b.nelx - 1 ? 8u : 0u) |
+          ((b.faces & SEM_FACE_YMIN) && bw.ey == 0 ? 16u : 0u) |
+          ((b.faces & SEM_FACE_YMAX) && bw.ey == b.nely - 1 ? 32u : 0u) |
+          ((b.faces & SEM_FACE_ZMIN) && bw.ez == 0 ? 64u : 0u) |
+          ((b.faces & SEM_FACE_ZMAX) && bw.ez == b.nelz - 1 ? 128u : 0u);
+  }
+  return fl;
+}
+
+template <int P, class T>
+struct FusedStore {
+  T* we;             // this element's output
+  unsigned fl;       // fused_flags of the element
+  __device__ __forceinline__ void store(int i, int j, int k, T v) const {
+    constexpr int P2 = P * P, P3 = P2 * P, N = P - 1;
+    if (fl & 0xFCu) {                 // element on a Dirichlet face (uniform branch)
+      const unsigned pf = (i == 0 ? 4u : 0u) | (i == N ? 8u : 0u) | (j == 0 ? 16u : 0u) |
+                          (j == N ? 32u : 0u) | (k == 0 ? 64u : 0u) | (k == N ? 128u : 0u);
+      if (pf & fl) v = T(0);
+    }
+    const int idx = k * P2 + j * P + i;
+    if ((fl & 1u) && i == 0) {
+      const T sum = we[idx - P3 + N] + v;
+      we[idx - P3 + N] = sum;
+      v = sum;
+    }
+    we[idx] = v;
+  }
+};
 
 }  // namespace sem

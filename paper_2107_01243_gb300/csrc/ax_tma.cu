@@ -18,12 +18,16 @@
 
 namespace sem {
 
-template <int P, class T, int STAGES, int K>
+// FUSE (K = 1 only): the CTA walks segments of kFuseSeg consecutive elements
+// and writes the fused output of each (FusedStore: mask, x-neighbour pairs of
+// the segment summed in the CTA), for the assembled operator of apply.cu.
+template <int P, class T, int STAGES, int K, bool FUSE>
 __global__ void __launch_bounds__(K * P * P)
 ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ G,
               const T* __restrict__ B, const T* __restrict__ h1f, T h1, T h2, DMat<P, T> D,
               int E, const CGState* __restrict__ st, int* __restrict__ err, uint64_t timeout_ns,
-              uint32_t starve_bytes) {
+              uint32_t starve_bytes, FuseBox fb) {
+  static_assert(!FUSE || K == 1, "the fused output needs one element per CTA");
   constexpr int P2 = P * P, P3 = P2 * P;
   constexpr uint32_t FB = P3 * sizeof(T);          // bytes of one field of one element
   if (st && st->done) return;
@@ -40,6 +44,9 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
   T* swr = stage0 + STAGES * SE + K * P3 + slot * P3;
   T* swsT = stage0 + STAGES * SE + 2 * K * P3 + slot * P3;
   const int nitems = (E + K - 1) / K;
+  const ItemSeq<FUSE> seq{nitems};     // this CTA's items in order
+  BoxWalk bw;                          // thread 0 (FUSE)
+  __shared__ unsigned s_fl;            // FusedStore flags of the current element
   auto Dm = [&](int r, int c) { return D.d[r * P + c]; };
   TileThread<P, T> t;
   t.init(tid - slot * P2, Dm);
@@ -66,16 +73,20 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
     mbar_fence_init();
   }
   __syncthreads();
+  int ahead = seq.first(), issued = 0;     // thread 0: next item to prefetch, copies issued
   if (tid == 0) {
 #pragma unroll
     for (int s = 0; s < STAGES; ++s) {
-      int it = blockIdx.x + s * gridDim.x;
-      if (it < nitems) issue(it, s);
+      if (ahead < nitems) {
+        issue(ahead, s);
+        ahead = seq.next(ahead);
+        ++issued;
+      }
     }
   }
 
   int n = 0;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++n) {
+  for (int it = seq.first(); it < nitems; it = seq.next(it), ++n) {
     const int s = n % STAGES;
     const uint32_t par = (uint32_t)(n / STAGES) & 1u;
     const bool ok = mbar_wait_bounded(&bar[s], par, err, timeout_ns);
@@ -90,24 +101,35 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
     if (__syncthreads_or(!ok)) {
       // a copy never completed: wait (bounded) for what is in flight, then leave
       if (tid == 0) {
-        for (int m = 0; m < STAGES; ++m) {
-          int nn = n + m;
-          if (blockIdx.x + nn * gridDim.x < nitems)
-            mbar_wait_bounded(&bar[nn % STAGES], (uint32_t)(nn / STAGES) & 1u, err, timeout_ns);
-        }
+        for (int nn = n; nn < issued; ++nn)
+          mbar_wait_bounded(&bar[nn % STAGES], (uint32_t)(nn / STAGES) & 1u, err, timeout_ns);
       }
       return;
     }
+    if (FUSE && tid == 0) {            // box position of e0, read back in the output phase
+      if (e0 % kFuseSeg == 0) bw.start(e0, fb); else bw.step(fb);
+      s_fl = fused_flags(e0, bw, fb);
+    }
     if (act) tile_forward<P, T>(t, su, sT, sg, uc, ck, swr, swsT, wt, Dm);
     __syncthreads();
-    if (tid == 0) {
-      int in = it + STAGES * gridDim.x;
-      if (in < nitems) {
-        fence_proxy_async_smem();
-        issue(in, s);
-      }
+    if (tid == 0 && ahead < nitems) {           // stage s consumed
+      fence_proxy_async_smem();
+      issue(ahead, s);
+      ahead = seq.next(ahead);
+      ++issued;
     }
-    if (act) tile_backward<P, T>(t, swr, swsT, wt, uc, bk, h2, helm, w + (size_t)(e0 + slot) * P3, Dm);
+    if (!act) continue;
+    if constexpr (FUSE) {
+      FusedStore<P, T> fs;
+      fs.we = w + (size_t)e0 * P3;
+      fs.fl = s_fl;
+      tile_backward<P, T>(t, swr, swsT, wt, uc, bk, h2, helm, Dm,
+                          [&](int k, T v) { fs.store(t.i, t.j, k, v); });
+    } else {
+      T* we = w + (size_t)(e0 + slot) * P3;
+      tile_backward<P, T>(t, swr, swsT, wt, uc, bk, h2, helm, Dm,
+                          [&](int k, T v) { we[k * P2 + t.lt] = v; });
+    }
   }
 }
 
@@ -128,13 +150,14 @@ static int num_sms() {
   return n;
 }
 
-template <int P, class T, int STAGES, int K>
-static void launch_tma_p(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
-                         const T* h1f, const CGState* st, int* err, uint64_t timeout_ns,
-                         uint32_t starve, cudaStream_t s) {
+// returns the grid it launched (the fused operator's later passes need it)
+template <int P, class T, int STAGES, int K, bool FUSE = false>
+static int launch_tma_p(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
+                        const T* h1f, const CGState* st, int* err, uint64_t timeout_ns,
+                        uint32_t starve, cudaStream_t s) {
   const int nf = 7 + (h2 != T(0) ? 1 : 0) + (h1f ? 1 : 0);
   const size_t smem = tma_smem_bytes<P, T, STAGES, K>(nf);
-  auto kern = ax_tma_kernel<P, T, STAGES, K>;
+  auto kern = ax_tma_kernel<P, T, STAGES, K, FUSE>;
   static int configured_smem = 0;
   static int occ[3] = {0, 0, 0};
   const int maxsmem = (int)tma_smem_bytes<P, T, STAGES, K>(9);
@@ -153,9 +176,11 @@ static void launch_tma_p(const sem_handle* h, const OpData<T>& op, const T* u, T
   const int nitems = (E + K - 1) / K;
   int grid = std::min<int64_t>(nitems, (int64_t)o * num_sms());
   if (grid < 1) grid = 1;
+  const FuseBox fb{h->nelx, h->nely, h->nelz, h->faces};
   kern<<<grid, K * P * P, smem, s>>>(u, w, op.G.ptr, op.B.ptr, h1f, h1, h2, D, E, st, err,
-                                     timeout_ns, starve);
+                                     timeout_ns, starve, fb);
   SEM_CHECK_LAUNCH();
+  return grid;
 }
 
 template <class T>
@@ -167,6 +192,7 @@ bool tma_ax_supported(const sem_handle* h, const void* u, const void* w, const v
 }
 
 // (stages, elements per CTA) variants the autotuner chooses from
+constexpr int kTmaVariantStages[5] = {1, 2, 3, 1, 2};
 template <int P, class T>
 static void launch_tma_variant(int variant, const sem_handle* h, const OpData<T>& op, const T* u,
                                T* w, T h1, T h2, const T* h1f, const CGState* st, int* err,
@@ -192,6 +218,34 @@ void launch_ax_tma(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T
     case 8: launch_tma_variant<8, T>(v, h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
     case 10: launch_tma_variant<10, T>(v, h, op, u, w, h1, h2, h1f, st, err, timeout_ns, starve, s); break;
     default: throw Error(SEM_ERR_ARG, "launch_ax_tma: unsupported order");
+  }
+}
+
+// The fused-output FP32 kernel (one element per CTA, the tuned stage count);
+// faces = the Dirichlet faces to zero (0: none).  Returns the grid.
+template <int P>
+static int launch_tma_fused_p(const sem_handle* h, const float* u, float* w, float h1, float h2,
+                              const float* h1f, const CGState* st, cudaStream_t s) {
+  const int stages = kTmaVariantStages[h->tune.ax32_variant];
+  if (stages == 1)
+    return launch_tma_p<P, float, 1, 1, true>(h, h->f32, u, w, h1, h2, h1f, st,
+                                              h->dev_err.ptr, kWaitTimeoutNs, 0, s);
+  if (stages == 2)
+    return launch_tma_p<P, float, 2, 1, true>(h, h->f32, u, w, h1, h2, h1f, st,
+                                              h->dev_err.ptr, kWaitTimeoutNs, 0, s);
+  return launch_tma_p<P, float, 3, 1, true>(h, h->f32, u, w, h1, h2, h1f, st, h->dev_err.ptr,
+                                            kWaitTimeoutNs, 0, s);
+}
+
+int launch_ax_tma_fused(const sem_handle* h, const float* u, float* w, float h1, float h2,
+                        const float* h1f, const CGState* st, cudaStream_t s) {
+  switch (h->P) {
+    case 2: return launch_tma_fused_p<2>(h, u, w, h1, h2, h1f, st, s);
+    case 4: return launch_tma_fused_p<4>(h, u, w, h1, h2, h1f, st, s);
+    case 6: return launch_tma_fused_p<6>(h, u, w, h1, h2, h1f, st, s);
+    case 8: return launch_tma_fused_p<8>(h, u, w, h1, h2, h1f, st, s);
+    case 10: return launch_tma_fused_p<10>(h, u, w, h1, h2, h1f, st, s);
+    default: throw Error(SEM_ERR_ARG, "launch_ax_tma_fused: unsupported order");
   }
 }
 

@@ -27,7 +27,7 @@
 namespace sem {
 
 constexpr int kMaxBatch = 256;
-constexpr int kChunk = 16384;          // points per vector work item
+constexpr int kChunk = 65536;          // points per vector work item
 
 // batched Ax tile per order: K elements of P^2 threads each per work item
 template <int P>
@@ -35,10 +35,24 @@ struct BaxCfg {
   static constexpr int K = (64 / (P * P)) > 1 ? (64 / (P * P)) : 1;
   static constexpr int THREADS = K * P * P;
   static constexpr int STAGES = P >= 10 ? 1 : 2;     // P = 10: more CTAs per SM
-  static constexpr size_t smem() {
-    return 128 + (size_t)(STAGES * 8 + 3) * K * P * P * P * sizeof(float);
+  // stages, work arrays, then one ClsProb per problem of the class
+  static constexpr size_t smem(int ncls) {
+    return 128 + (size_t)(STAGES * 8 + 3) * K * P * P * P * sizeof(float) +
+           (size_t)ncls * 48;
   }
 };
+
+// what the batched Ax reads of one problem, copied to shared memory per CTA
+struct ClsProb {
+  const float* p;
+  const float* G;
+  const float* B;
+  float* w;
+  int E;
+  float h1, h2;
+  int pad;
+};
+static_assert(sizeof(ClsProb) == 48, "ClsProb layout");
 
 __constant__ float c_b32_D[kMaxP + 1][kMaxP * kMaxP];   // FP32 D of every order
 
@@ -74,6 +88,32 @@ __device__ __forceinline__ int find_prob(const long long* off, int n, long long 
   return lo;
 }
 
+// Per-block view of the vector work items for one launch: the first item of
+// every problem and whether the problem's inner solve is finished, read once;
+// a block then steps over a finished problem's items in one jump.
+struct ItemWalk {
+  int voff[kMaxBatch + 1];
+  int done[kMaxBatch];
+  __device__ __forceinline__ void load(const BProb* __restrict__ probs, int nprob, int nitems) {
+    for (int q = threadIdx.x; q < nprob; q += blockDim.x) {
+      voff[q] = probs[q].v_off;
+      done[q] = probs[q].st->done;
+    }
+    if (threadIdx.x == 0) voff[nprob] = nitems;
+    __syncthreads();
+  }
+  // first item at or after it, in steps of stride, whose problem is running
+  __device__ __forceinline__ int next(const int* __restrict__ item_prob, int it, int stride,
+                                      int nitems) const {
+    while (it < nitems) {
+      const int pi = item_prob[it];
+      if (!done[pi]) break;
+      it += (voff[pi + 1] - it + stride - 1) / stride * stride;
+    }
+    return it;
+  }
+};
+
 // ---------------------------------------------------------------- batched Ax
 // Persistent bulk-copy Ax over every element of the problems of one order P;
 // CTAs of K P^2 threads take work items of K consecutive elements of one
@@ -92,11 +132,23 @@ bax_kernel(const BProb* __restrict__ probs, const int* __restrict__ cls_prob,
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   float* stage0 = reinterpret_cast<float*>(smem_raw + 128);
   float* work = stage0 + STAGES * SV;
+  ClsProb* cp = reinterpret_cast<ClsProb*>(work + 3 * K * P3);
   const int tid = threadIdx.x;
   for (int q = tid; q < ncls; q += blockDim.x) {
     s_off[q] = cls_ioff[q];
     s_prob[q] = cls_prob[q];
-    s_skip[q] = probs[cls_prob[q]].st->done;
+    const BProb& b = probs[cls_prob[q]];
+    s_skip[q] = b.st->done;
+    ClsProb c;
+    c.p = b.p;
+    c.G = b.G;
+    c.B = b.B;
+    c.w = b.w;
+    c.E = b.E;
+    c.h1 = b.h1;
+    c.h2 = b.h2;
+    c.pad = 0;
+    cp[q] = c;
   }
   if (tid == 0) {
 #pragma unroll
@@ -118,7 +170,7 @@ bax_kernel(const BProb* __restrict__ probs, const int* __restrict__ cls_prob,
   };
   auto issue = [&](long long g, int s) {
     const int c = find_prob(s_off, ncls, g);
-    const BProb& pr = probs[s_prob[c]];
+    const ClsProb& pr = cp[c];
     const long long e0 = (g - s_off[c]) * K;
     const int cnt = (int)min((long long)K, (long long)pr.E - e0);
     const uint32_t FB = (uint32_t)(P3 * cnt) * 4u;
@@ -149,7 +201,7 @@ bax_kernel(const BProb* __restrict__ probs, const int* __restrict__ cls_prob,
     const int s = n % STAGES;
     const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)(n / STAGES) & 1u, err, timeout_ns);
     const int c = find_prob(s_off, ncls, g);
-    const BProb& pr = probs[s_prob[c]];
+    const ClsProb& pr = cp[c];
     const long long e0 = (g - s_off[c]) * K;
     const int cnt = (int)min((long long)K, (long long)pr.E - e0);
     const bool act = slot < cnt;
@@ -175,7 +227,11 @@ bax_kernel(const BProb* __restrict__ probs, const int* __restrict__ cls_prob,
       ahead = next(ahead + G);
     }
     if (act)
-      tile_backward<P, float>(t, swr, swsT, wt, uc, bk, pr.h2, helm, pr.w + (e0 + slot) * P3, Dm);
+    {
+      float* we = pr.w + (e0 + slot) * P3;
+      tile_backward<P, float>(t, swr, swsT, wt, uc, bk, pr.h2, helm, Dm,
+                              [&](int k, float v) { we[k * P2 + t.lt] = v; });
+    }
   }
 }
 
@@ -353,12 +409,14 @@ binit_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob,
 }
 
 __global__ void __launch_bounds__(256)
-bpw_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob, int nitems,
-           double* partials, unsigned* tickets) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+bpw_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob, int nprob,
+           int nitems, double* partials, unsigned* tickets) {
+  __shared__ ItemWalk wk;
+  wk.load(probs, nprob, nitems);
+  for (int it = wk.next(item_prob, blockIdx.x, gridDim.x, nitems); it < nitems;
+       it = wk.next(item_prob, it + gridDim.x, gridDim.x, nitems)) {
     const int pi = item_prob[it];
     const BProb& b = probs[pi];
-    if (b.st->done) continue;
     const long long lo = (long long)(it - b.v_off) * kChunk;
     const long long hi = min(lo + kChunk, b.nL);
     const float4* p4 = reinterpret_cast<const float4*>(b.p + lo);
@@ -400,12 +458,14 @@ __device__ __forceinline__ void upd1(float& x, float& r, float p, float w, float
 }
 
 __global__ void __launch_bounds__(256)
-bupdate_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob, int nitems,
-               double* partials, unsigned* tickets) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+bupdate_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob, int nprob,
+               int nitems, double* partials, unsigned* tickets) {
+  __shared__ ItemWalk wk;
+  wk.load(probs, nprob, nitems);
+  for (int it = wk.next(item_prob, blockIdx.x, gridDim.x, nitems); it < nitems;
+       it = wk.next(item_prob, it + gridDim.x, gridDim.x, nitems)) {
     const int pi = item_prob[it];
     const BProb& b = probs[pi];
-    if (b.st->done) continue;
     const float alpha = (float)b.st->alpha;
     const long long lo = (long long)(it - b.v_off) * kChunk;
     const long long hi = min(lo + kChunk, b.nL);
@@ -452,11 +512,14 @@ bupdate_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_pro
 }
 
 __global__ void __launch_bounds__(256)
-bpupd_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob, int nitems) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+bpupd_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob, int nprob,
+             int nitems) {
+  __shared__ ItemWalk wk;
+  wk.load(probs, nprob, nitems);
+  for (int it = wk.next(item_prob, blockIdx.x, gridDim.x, nitems); it < nitems;
+       it = wk.next(item_prob, it + gridDim.x, gridDim.x, nitems)) {
     const int pi = item_prob[it];
     const BProb& b = probs[pi];
-    if (b.st->done) continue;
     const float beta = (float)b.st->beta;
     const long long lo = (long long)(it - b.v_off) * kChunk;
     const long long hi = min(lo + kChunk, b.nL);
@@ -513,20 +576,21 @@ static void batch_upload_d(const sem_handle* h) {
 }
 
 template <int P>
-static int bax_occupancy() {
+static int bax_occupancy(int ncls) {
   using C = BaxCfg<P>;
   auto kern = bax_kernel<P, C::STAGES>;
   SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)C::smem()));
+                                (int)C::smem(kMaxBatch)));
   int occ = 0;
-  SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::THREADS, C::smem()));
+  SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::THREADS,
+                                                         C::smem(ncls)));
   return occ;
 }
 
 template <int P>
 static void launch_bax(sem_batch* bt, cudaStream_t s) {
   using C = BaxCfg<P>;
-  bax_kernel<P, C::STAGES><<<bt->bax_grid_cls[P], C::THREADS, C::smem(), s>>>(
+  bax_kernel<P, C::STAGES><<<bt->bax_grid_cls[P], C::THREADS, C::smem(bt->ncls[P]), s>>>(
       bt->probs.ptr, bt->cls_prob[P].ptr, bt->cls_ioff[P].ptr, bt->ncls[P], bt->Icls[P],
       bt->hs[0]->dev_err.ptr, kWaitTimeoutNs);
   SEM_CHECK_LAUNCH();
@@ -549,13 +613,13 @@ static void batch_iteration(sem_batch* bt, cudaStream_t s) {
   bdssum_kernel<<<dblocks, 256, 0, s>>>(bt->probs.ptr, bt->d_off.ptr, n, bt->Dtot);
   SEM_CHECK_LAUNCH();
   const int vblocks = std::min(bt->nitems, 8 * kNumSMs);
-  bpw_kernel<<<vblocks, 256, 0, s>>>(bt->probs.ptr, bt->item_prob.ptr, bt->nitems,
+  bpw_kernel<<<vblocks, 256, 0, s>>>(bt->probs.ptr, bt->item_prob.ptr, n, bt->nitems,
                                      bt->partials.ptr, bt->tickets.ptr);
   SEM_CHECK_LAUNCH();
-  bupdate_kernel<<<vblocks, 256, 0, s>>>(bt->probs.ptr, bt->item_prob.ptr, bt->nitems,
+  bupdate_kernel<<<vblocks, 256, 0, s>>>(bt->probs.ptr, bt->item_prob.ptr, n, bt->nitems,
                                          bt->partials.ptr, bt->tickets.ptr);
   SEM_CHECK_LAUNCH();
-  bpupd_kernel<<<vblocks, 256, 0, s>>>(bt->probs.ptr, bt->item_prob.ptr, bt->nitems);
+  bpupd_kernel<<<vblocks, 256, 0, s>>>(bt->probs.ptr, bt->item_prob.ptr, n, bt->nitems);
   SEM_CHECK_LAUNCH();
 }
 
@@ -644,11 +708,11 @@ extern "C" sem_status sem_batch_create(sem_handle* const* handles, int n, sem_ba
       bt->cls_ioff[P].upload(ioff.data(), ioff.size(), nullptr);
       int occ = 0;
       switch (P) {
-        case 2: occ = bax_occupancy<2>(); break;
-        case 4: occ = bax_occupancy<4>(); break;
-        case 6: occ = bax_occupancy<6>(); break;
-        case 8: occ = bax_occupancy<8>(); break;
-        default: occ = bax_occupancy<10>(); break;
+        case 2: occ = bax_occupancy<2>((int)ids.size()); break;
+        case 4: occ = bax_occupancy<4>((int)ids.size()); break;
+        case 6: occ = bax_occupancy<6>((int)ids.size()); break;
+        case 8: occ = bax_occupancy<8>((int)ids.size()); break;
+        default: occ = bax_occupancy<10>((int)ids.size()); break;
       }
       bt->bax_grid_cls[P] = (int)std::min<long long>(items, (long long)std::max(1, occ) * nsm);
     }

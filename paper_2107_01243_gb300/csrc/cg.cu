@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <initializer_list>
+#include <type_traits>
 
 #include "sem_internal.cuh"
 #include "reduce.cuh"
@@ -164,6 +165,89 @@ k_pupd_v(int64_t nv, typename Vec<T>::V* __restrict__ p, const typename Vec<T>::
 #pragma unroll
     for (int l = 0; l < VT::L; ++l) pe[l] = de[l] * re[l] + beta * pe[l];
     p[q] = pq;
+  }
+}
+
+// ---- FP64 forms with fewer FP64-pipe operations (that pipe, not HBM, bounds
+// the FP64 vector kernels on GB300).  1/mult is a power of two (mult = 1, 2,
+// 4 or 8 copies on the box), so it is widened to double by moving its
+// exponent bits instead of a conversion instruction; <r, z> uses the
+// precomputed dinv / mult:  <p, w>: 2 FP64 operations per point,
+// update: x, r, r^2, <r,z>, <r,r>: 5.
+__device__ __forceinline__ double pow2_widen(float f) {
+  return __longlong_as_double((long long)((__float_as_uint(f) >> 23) + 896u) << 52);
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_pw_v64(int64_t nv, const double2* __restrict__ p, const double2* __restrict__ w,
+         const float2* __restrict__ imult, CGState* __restrict__ st,
+         double* __restrict__ partials) {
+  if (st->done) return;
+  double acc = 0.0;
+#pragma unroll 4
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = p[q], b = w[q];
+    const float2 m = imult[q];
+    acc = fma(a.x * b.x, pow2_widen(m.x), acc);
+    acc = fma(a.y * b.y, pow2_widen(m.y), acc);
+  }
+  double v[1] = {acc};
+  double tot[1];
+  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    st->pw = tot[0];
+    if (!(tot[0] > 0.0)) {
+      st->status = SEM_ERR_BREAKDOWN;
+      st->done = 1;
+    } else {
+      st->alpha = st->rz / tot[0];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_update_v64(int64_t nv, double2* __restrict__ x, double2* __restrict__ r,
+             const double2* __restrict__ p, const double2* __restrict__ w,
+             const double2* __restrict__ dmi, const float2* __restrict__ imult,
+             CGState* __restrict__ st, double* __restrict__ partials) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  double rz = 0.0, rr = 0.0;
+#pragma unroll 2
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    double2 xq = x[q], rq = r[q];
+    const double2 pq = p[q], wq = w[q], dq = dmi[q];
+    const float2 mq = imult[q];
+    xq.x = fma(alpha, pq.x, xq.x);
+    xq.y = fma(alpha, pq.y, xq.y);
+    rq.x = fma(-alpha, wq.x, rq.x);
+    rq.y = fma(-alpha, wq.y, rq.y);
+    const double sx = rq.x * rq.x, sy = rq.y * rq.y;
+    rz = fma(sx, dq.x, rz);
+    rz = fma(sy, dq.y, rz);
+    rr = fma(sx, pow2_widen(mq.x), rr);
+    rr = fma(sy, pow2_widen(mq.y), rr);
+    x[q] = xq;
+    r[q] = rq;
+  }
+  double v[2] = {rz, rr};
+  double tot[2];
+  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    st->iter += 1;
+    st->rr = tot[1];
+    if (!(tot[1] == tot[1]) || !(tot[0] == tot[0])) {
+      st->status = SEM_ERR_BREAKDOWN;
+      st->done = 1;
+    } else if (tot[1] <= st->tol2) {
+      st->done = 1;
+    } else if (st->iter >= st->maxit) {
+      st->status = SEM_ERR_NOCONV;
+      st->done = 1;
+    } else {
+      st->beta = tot[0] / st->rz;
+      st->rz = tot[0];
+    }
   }
 }
 
@@ -320,11 +404,13 @@ __global__ void k_addx(int64_t n, double* __restrict__ x, const float* __restric
 }
 
 __global__ void k_dinv(int64_t n, const double* __restrict__ dg, const uint8_t* __restrict__ mask,
-                       double* __restrict__ dinv, float* __restrict__ dinv32) {
+                       const float* __restrict__ imult, double* __restrict__ dinv,
+                       double* __restrict__ dmi, float* __restrict__ dinv32) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
     double v = mask[q] ? 1.0 / dg[q] : 0.0;
     dinv[q] = v;
+    dmi[q] = v * (double)imult[q];
     if (dinv32) dinv32[q] = (float)v;
   }
 }
@@ -381,6 +467,7 @@ struct PcgArgs {
   const T* h1f;
   T h1, h2;
   CGState* st;
+  const T* dmi = nullptr;     // dinv / mult (FP64 solves)
 };
 
 // true when the vectorised kernels apply: n a multiple of the lane count and
@@ -393,13 +480,35 @@ static bool vec_ok(int64_t n, std::initializer_list<const T*> ptrs, const float*
   return reinterpret_cast<uintptr_t>(imult) % (Vec<T>::L * sizeof(float)) == 0;
 }
 
+// FP64 pw / update / p-update with the reduced-FP64-operation kernels
+static void launch_vec64(sem_handle* h, const PcgArgs<double>& a, cudaStream_t s) {
+  const int64_t nv = h->nL / 2;
+  k_pw_v64<<<kRedBlocks, kRedThreads, 0, s>>>(nv, (const double2*)a.p, (const double2*)a.w,
+                                              (const float2*)h->imult.ptr, a.st, h->partials.ptr);
+  SEM_CHECK_LAUNCH();
+  k_update_v64<<<kRedBlocks, kRedThreads, 0, s>>>(
+      nv, (double2*)a.x, (double2*)a.r, (const double2*)a.p, (const double2*)a.w,
+      (const double2*)a.dmi, (const float2*)h->imult.ptr, a.st, h->partials.ptr);
+  SEM_CHECK_LAUNCH();
+  k_pupd_v<double><<<kRedBlocks, kRedThreads, 0, s>>>(nv, (double2*)a.p, (const double2*)a.r,
+                                                      (const double2*)a.dinv, a.st);
+  SEM_CHECK_LAUNCH();
+}
+
 template <class T>
 static void pcg_iterations(sem_handle* h, const PcgArgs<T>& a, int count, cudaStream_t s) {
   const int64_t n = h->nL;
-  const bool vec = vec_ok<T>(n, {a.x, a.r, a.p, a.w, a.dinv}, h->imult.ptr);
+  const bool vec = vec_ok<T>(n, {a.x, a.r, a.p, a.w, a.dinv, a.dmi}, h->imult.ptr);
   for (int c = 0; c < count; ++c) {
-    launch_ax<T>(h, *a.op, a.p, a.w, a.h1, a.h2, a.h1f, a.st, s);
-    launch_dssum<T>(h, a.w, true, a.st, s);
+    launch_apply<T>(h, *a.op, a.p, a.w, a.h1, a.h2, a.h1f, a.st, SEM_APPLY_FULL, s);
+    bool done64 = false;
+    if constexpr (std::is_same<T, double>::value) {
+      if (vec && a.dmi) {
+        launch_vec64(h, a, s);
+        done64 = true;
+      }
+    }
+    if (done64) continue;
     if (vec) {
       using V = typename Vec<T>::V;
       using M = typename Vec<T>::M;
@@ -477,11 +586,13 @@ static void ensure_dinv(sem_handle* h, double h1, double h2, const double* h1f, 
               (!need32 || h->f32.dinv.ptr);
   if (same && !h1f) return;      // a field may have changed in place: recompute
   ensure(h->f64.dinv, n);
+  ensure(h->f64.dmi, n);
   if (need32) ensure(h->f32.dinv, n);
   ensure(h->tmp64, n);
   launch_local_diag<double>(h, h->f64, h->tmp64.ptr, h1, h2, h1f, s);
   launch_dssum<double>(h, h->tmp64.ptr, false, nullptr, s);
-  k_dinv<<<ew_grid(n), 256, 0, s>>>(n, h->tmp64.ptr, h->mask.ptr, h->f64.dinv.ptr,
+  k_dinv<<<ew_grid(n), 256, 0, s>>>(n, h->tmp64.ptr, h->mask.ptr, h->imult.ptr,
+                                   h->f64.dinv.ptr, h->f64.dmi.ptr,
                                    need32 ? h->f32.dinv.ptr : nullptr);
   SEM_CHECK_LAUNCH();
   h->dinv_h1 = h1;
@@ -494,8 +605,7 @@ static void ensure_dinv(sem_handle* h, double h1, double h2, const double* h1f, 
 static void residual64(sem_handle* h, const double* b, const double* x, double h1, double h2,
                        const double* h1f, float* r32, CGState* st, cudaStream_t s) {
   const int64_t n = h->nL;
-  launch_ax<double>(h, h->f64, x, h->w.ptr, h1, h2, h1f, nullptr, s);
-  launch_dssum<double>(h, h->w.ptr, true, nullptr, s);
+  launch_apply<double>(h, h->f64, x, h->w.ptr, h1, h2, h1f, nullptr, SEM_APPLY_FULL, s);
   k_resid<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, h->w.ptr, h->r.ptr, r32, h->imult.ptr, st,
                                              h->partials.ptr);
   SEM_CHECK_LAUNCH();
@@ -521,7 +631,7 @@ static void solve_fp64(sem_handle* h, const double* b, double* x, const sem_solv
                                                     o.maxit, 0);
   SEM_CHECK_LAUNCH();
   PcgArgs<double> a{&h->f64, x, h->r.ptr, h->p.ptr, h->w.ptr, h->f64.dinv.ptr, o.h1_field,
-                    o.h1, o.h2, st};
+                    o.h1, o.h2, st, h->f64.dmi.ptr};
   CGState fin = run_pcg<double>(h, a, o, s);
   // true residual of the returned x
   residual64(h, b, x, o.h1, o.h2, o.h1_field, nullptr, st, s);
@@ -726,14 +836,13 @@ extern "C" sem_status sem_apply_host(sem_handle* h, const void* u_host, void* w_
     const size_t bytes = n * (dtype == SEM_F64 ? sizeof(double) : sizeof(float));
     SEM_CUDA(cudaMemcpyAsync(h->stage_in.ptr, u_host, bytes, cudaMemcpyHostToDevice, s));
     if (dtype == SEM_F64) {
-      launch_ax<double>(h, h->f64, h->stage_in.ptr, h->stage_out.ptr, 1.0, 0.0, nullptr, nullptr, s);
-      launch_dssum<double>(h, h->stage_out.ptr, true, nullptr, s);
+      launch_apply<double>(h, h->f64, h->stage_in.ptr, h->stage_out.ptr, 1.0, 0.0, nullptr,
+                           nullptr, SEM_APPLY_FULL, s);
     } else {
       if (!h->f32.G.ptr) throw Error(SEM_ERR_STATE, "sem_apply_host: no FP32 geometry");
       float* in = (float*)h->stage_in.ptr;
       float* out = (float*)h->stage_out.ptr;
-      launch_ax<float>(h, h->f32, in, out, 1.0f, 0.0f, nullptr, nullptr, s);
-      launch_dssum<float>(h, out, true, nullptr, s);
+      launch_apply<float>(h, h->f32, in, out, 1.0f, 0.0f, nullptr, nullptr, SEM_APPLY_FULL, s);
     }
     SEM_CUDA(cudaMemcpyAsync(w_host, h->stage_out.ptr, bytes, cudaMemcpyDeviceToHost, s));
     int herr = 0;

@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
+#include <type_traits>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -123,6 +124,7 @@ struct OpData {
   DevBuf<T> B;      // [E][p^3]
   DevBuf<T> D;      // [p][p] row-major D[i][l] = l_l'(xi_i)
   DevBuf<T> dinv;   // Jacobi inverse diagonal (mask folded in)
+  DevBuf<T> dmi;    // dinv / mult (FP64 only: <r, z> = sum r^2 dinv / mult)
   DevBuf<T> h1f;    // per-point h1 in this precision (mixed solves)
 };
 
@@ -190,6 +192,12 @@ void launch_ax(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1,
 // bulk-copy staged variant (even P, 16-byte aligned vectors)
 template <class T>
 bool tma_ax_supported(const sem_handle* h, const void* u, const void* w, const void* h1f);
+// the assembled operator (apply.cu); phase = SEM_APPLY_* bits
+template <class T>
+bool apply_fused_supported(const sem_handle* h, const void* u, const void* w, const void* h1f);
+template <class T>
+void launch_apply(sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2, const T* h1f,
+                  const CGState* st, int phase, cudaStream_t s);
 template <class T>
 void launch_ax_tma(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
                    const T* h1f, const CGState* state, int* err, uint64_t timeout_ns,

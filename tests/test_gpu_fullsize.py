@@ -8,9 +8,11 @@ The oracle cannot hold these meshes, so it works on samples:
     placed where the element sits (the deformation is a function of the
     physical position, so this reproduces the element's coordinates);
   * dssum on the whole mesh (a bincount over 16.7M local points);
-  * the solve's assembled residual at every point of the elements a 3x3x3
-    patch of elements fully covers (all copies of such a point lie in the
-    patch), checked against |r_g| <= ||r|| <= tol ||b||;
+  * the assembled operator (sem_apply) at every point of the elements that
+    3x3x3 patches of elements fully cover (all copies of such a point lie in
+    the patch);
+  * the solve's assembled residual at the covered points of such patches,
+    checked against |r_g| <= ||r|| <= tol ||b||;
   * the dL/dh1 kernel on sampled elements with seeded fields;
   * the adjoint gradient against central finite differences of the loss.
 """
@@ -98,13 +100,10 @@ def _covered(start, nel):
     return out
 
 
-def _patch_residual(cfg, start, x_dev, b_dev, h1=1.0, h2=0.0):
-    """Oracle residual b - mask QQ^T A x at every point of the covered
-    elements of a 3x3x3 patch; also returns the oracle's b there and the
-    GPU's b at the same points."""
+def _patch_oracle(cfg, start):
+    """Oracle problem of the 3x3x3 element patch at start, the patch's
+    elements in the full mesh (patch order) and the covered ones."""
     nx, ny, nz = cfg["nel"]
-    N = cfg["N"]
-    p = N + 1
     hs = [cfg["length"][a] / cfg["nel"][a] for a in range(3)]
     faces = 0
     faces |= mesh.FACE_XMIN if start[0] == 0 else 0
@@ -114,20 +113,51 @@ def _patch_residual(cfg, start, x_dev, b_dev, h1=1.0, h2=0.0):
     faces |= mesh.FACE_ZMIN if start[2] == 0 else 0
     faces |= mesh.FACE_ZMAX if start[2] + 3 == nz else 0
     x0 = tuple(start[a] * hs[a] for a in range(3))
-    o = OracleProblem((3, 3, 3), N, x0=x0, length=tuple(3 * v for v in hs),
+    o = OracleProblem((3, 3, 3), cfg["N"], x0=x0, length=tuple(3 * v for v in hs),
                       deform=cfg["deform"], faces=faces)
-    # the patch's elements, in the patch's own order, taken from the full mesh
     full = [(start[0] + a) + nx * ((start[1] + b) + ny * (start[2] + c))
             for c in range(3) for b in range(3) for a in range(3)]
+    cov = _covered(start, cfg["nel"])
+    sel = [a + 3 * (b + 3 * c) for c in cov[2] for b in cov[1] for a in cov[0]]
+    return o, full, sel
+
+
+def _patch_residual(cfg, start, x_dev, b_dev, h1=1.0, h2=0.0):
+    """Oracle residual b - mask QQ^T A x at every point of the covered
+    elements of a 3x3x3 patch; also returns the oracle's b there and the
+    GPU's b at the same points."""
+    p = cfg["N"] + 1
+    o, full, sel = _patch_oracle(cfg, start)
     idx = torch.tensor(full, device=DEV)
     xp = x_dev.view(-1, p, p, p)[idx].cpu().numpy()
     bp_gpu = b_dev.view(-1, p, p, p)[idx].cpu().numpy()
     f = si.eval_fourier(si.fourier_modes(cfg["seed"]), o.x, o.y, o.z)
     bp = o.rhs(f)
     r = bp - o.matvec(xp, h1, h2)
-    cov = _covered(start, cfg["nel"])
-    sel = [a + 3 * (b + 3 * c) for c in cov[2] for b in cov[1] for a in cov[0]]
     return r[sel], bp[sel], bp_gpu[sel]
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
+def test_apply_patches_fullsize(throughput_handle, dtype, tol):
+    """The assembled operator (fused element kernel + split gather-scatter)
+    on the whole 32^3 mesh, checked by the oracle's assembled operator at
+    every point of the elements covered by 3x3x3 patches."""
+    cfg = si.THROUGHPUT
+    h = throughput_handle
+    p = cfg["N"] + 1
+    u = si.uniform((h.E, p, p, p), cfg["seed"])
+    if dtype == torch.float32:
+        u = u.astype(np.float32).astype(np.float64)
+    ud = torch.from_numpy(u).to(DEV, dtype).view(-1)
+    w = torch.empty_like(ud)
+    sem.sem_apply(h, ud, w)
+    sem.sem_sync(h)
+    wv = w.view(h.E, p, p, p)
+    for start in [(0, 0, 0), (13, 7, 21), (29, 29, 29), (0, 15, 29), (30 - 1, 0, 12)]:
+        o, full, sel = _patch_oracle(cfg, start)
+        ref = o.matvec(u[full])[sel]
+        got = wv[torch.tensor(full, device=DEV)].double().cpu().numpy()[sel]
+        assert rel_inf(got, ref) < tol, start
 
 
 @pytest.fixture(scope="module")
