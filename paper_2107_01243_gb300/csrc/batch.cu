@@ -7,6 +7,11 @@
 //           one order (one launch per order present, each with the tile and
 //           shared-memory stages of its own order)
 //   bdssum  index-free gather-scatter over all problems' shared points
+// or, when every order runs one element per CTA (N = 5, 7, 9), the assembled
+// operator with the gather-scatter split by direction (batch_apply.cuh):
+//   bapply  per order class, the element kernel summing x-neighbour pairs
+//           inside segments of four elements and zeroing masked points
+//   bcut, bsy, bsz  per class, x-pairs between segments, y- and z-pairs
 //   bpw, bupdate, bpupd  vector updates over fixed-size chunks; the chunk
 //           partial sums of one problem are reduced, in a fixed order, by the
 //           last chunk block to finish (a ticket per problem)
@@ -113,6 +118,12 @@ struct ItemWalk {
     return it;
   }
 };
+
+}  // namespace sem
+
+#include "batch_apply.cuh"
+
+namespace sem {
 
 // ---------------------------------------------------------------- batched Ax
 // Persistent bulk-copy Ax over every element of the problems of one order P;
@@ -560,6 +571,14 @@ struct sem_batch {
   DevBuf<int> cls_prob[kMaxP + 1];
   DevBuf<long long> cls_ioff[kMaxP + 1];
   int bax_grid_cls[kMaxP + 1] = {};
+  // fused operator (every class with one element per CTA): per class the
+  // segment offsets, and the work-item offsets of the three finishing passes
+  bool fused = false;
+  long long Scls[kMaxP + 1] = {}, Tcut[kMaxP + 1] = {}, Tsy[kMaxP + 1] = {},
+            Tsz[kMaxP + 1] = {};
+  DevBuf<long long> cls_soff[kMaxP + 1], cut_off[kMaxP + 1], sy_off[kMaxP + 1],
+      sz_off[kMaxP + 1];
+  int bapply_grid[kMaxP + 1] = {};
   int nitems = 0, maxP = 0;
   cudaStream_t stream = nullptr;
 };
@@ -596,10 +615,69 @@ static void launch_bax(sem_batch* bt, cudaStream_t s) {
   SEM_CHECK_LAUNCH();
 }
 
+template <int P>
+static int bapply_occupancy(int ncls) {
+  using C = BApplyCfg<P>;
+  auto kern = bapply_kernel<P, C::STAGES>;
+  SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)C::smem(kMaxBatch)));
+  int occ = 0;
+  SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::THREADS,
+                                                         C::smem(ncls)));
+  return occ;
+}
+
+static int pass_blocks(long long total) {
+  return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 16LL * kNumSMs));
+}
+
+template <int P>
+static void launch_bapply(sem_batch* bt, cudaStream_t s) {
+  using C = BApplyCfg<P>;
+  bapply_kernel<P, C::STAGES><<<bt->bapply_grid[P], C::THREADS, C::smem(bt->ncls[P]), s>>>(
+      bt->probs.ptr, bt->cls_prob[P].ptr, bt->cls_soff[P].ptr, bt->ncls[P], bt->Scls[P],
+      bt->hs[0]->dev_err.ptr, kWaitTimeoutNs);
+  SEM_CHECK_LAUNCH();
+}
+
+template <int P>
+static void launch_bfinish(sem_batch* bt, cudaStream_t s) {
+  const int nc = bt->ncls[P];
+  if (bt->Tcut[P] > 0) {
+    bcut_kernel<P><<<pass_blocks(bt->Tcut[P]), 256, 0, s>>>(bt->probs.ptr, bt->cls_prob[P].ptr,
+                                                            bt->cut_off[P].ptr, nc, bt->Tcut[P]);
+    SEM_CHECK_LAUNCH();
+  }
+  if (bt->Tsy[P] > 0) {
+    bsy_kernel<P><<<pass_blocks(bt->Tsy[P]), 256, 0, s>>>(bt->probs.ptr, bt->cls_prob[P].ptr,
+                                                          bt->sy_off[P].ptr, nc, bt->Tsy[P]);
+    SEM_CHECK_LAUNCH();
+  }
+  if (bt->Tsz[P] > 0) {
+    bsz_kernel<P><<<pass_blocks(bt->Tsz[P]), 256, 0, s>>>(bt->probs.ptr, bt->cls_prob[P].ptr,
+                                                          bt->sz_off[P].ptr, nc, bt->Tsz[P]);
+    SEM_CHECK_LAUNCH();
+  }
+}
+
 // one inner iteration over the batch (captured into a graph)
 static void batch_iteration(sem_batch* bt, cudaStream_t s) {
   const int n = (int)bt->hs.size();
-  for (int P = 2; P <= kMaxP; P += 2) {
+  if (bt->fused) {
+    for (int P = 6; P <= kMaxP; P += 2) {
+      if (!bt->ncls[P]) continue;
+      if (P == 6) launch_bapply<6>(bt, s);
+      else if (P == 8) launch_bapply<8>(bt, s);
+      else launch_bapply<10>(bt, s);
+    }
+    for (int P = 6; P <= kMaxP; P += 2) {
+      if (!bt->ncls[P]) continue;
+      if (P == 6) launch_bfinish<6>(bt, s);
+      else if (P == 8) launch_bfinish<8>(bt, s);
+      else launch_bfinish<10>(bt, s);
+    }
+  }
+  for (int P = 2; P <= kMaxP && !bt->fused; P += 2) {
     if (!bt->ncls[P]) continue;
     switch (P) {
       case 2: launch_bax<2>(bt, s); break;
@@ -609,9 +687,11 @@ static void batch_iteration(sem_batch* bt, cudaStream_t s) {
       default: launch_bax<10>(bt, s); break;
     }
   }
-  const int dblocks = (int)std::min<long long>((bt->Dtot + 255) / 256, 32LL * kNumSMs);
-  bdssum_kernel<<<dblocks, 256, 0, s>>>(bt->probs.ptr, bt->d_off.ptr, n, bt->Dtot);
-  SEM_CHECK_LAUNCH();
+  if (!bt->fused) {
+    const int dblocks = (int)std::min<long long>((bt->Dtot + 255) / 256, 32LL * kNumSMs);
+    bdssum_kernel<<<dblocks, 256, 0, s>>>(bt->probs.ptr, bt->d_off.ptr, n, bt->Dtot);
+    SEM_CHECK_LAUNCH();
+  }
   const int vblocks = std::min(bt->nitems, 8 * kNumSMs);
   bpw_kernel<<<vblocks, 256, 0, s>>>(bt->probs.ptr, bt->item_prob.ptr, n, bt->nitems,
                                      bt->partials.ptr, bt->tickets.ptr);
@@ -715,6 +795,41 @@ extern "C" sem_status sem_batch_create(sem_handle* const* handles, int n, sem_ba
         default: occ = bax_occupancy<10>((int)ids.size()); break;
       }
       bt->bax_grid_cls[P] = (int)std::min<long long>(items, (long long)std::max(1, occ) * nsm);
+    }
+    // fused operator when every order present runs one element per CTA
+    bt->fused = bt->ncls[2] == 0 && bt->ncls[4] == 0;
+    for (int P = 6; P <= kMaxP && bt->fused; P += 2) {
+      if (!bt->ncls[P]) continue;
+      std::vector<long long> soff, coff, yoff, zoff;
+      long long S = 0, C = 0, Y = 0, Z = 0;
+      for (int p = 0; p < n; ++p) {
+        const BProb& b = bt->hp[p];
+        if (b.P != P) continue;
+        const long long nseg = (b.E + kFuseSeg - 1) / kFuseSeg;
+        soff.push_back(S);
+        coff.push_back(C);
+        yoff.push_back(Y);
+        zoff.push_back(Z);
+        S += nseg;
+        C += (nseg - 1) * P * P;
+        Y += (long long)b.nelx * (b.nely - 1) * b.nelz * P * (P / 2);
+        Z += (long long)b.nelx * b.nely * (b.nelz - 1) * (P * P / 4);
+      }
+      bt->Scls[P] = S;
+      bt->Tcut[P] = C;
+      bt->Tsy[P] = Y;
+      bt->Tsz[P] = Z;
+      DevBuf<long long>* bufs[4] = {&bt->cls_soff[P], &bt->cut_off[P], &bt->sy_off[P],
+                                    &bt->sz_off[P]};
+      std::vector<long long>* vals[4] = {&soff, &coff, &yoff, &zoff};
+      for (int a = 0; a < 4; ++a) {
+        bufs[a]->alloc(vals[a]->size());
+        bufs[a]->upload(vals[a]->data(), vals[a]->size(), nullptr);
+      }
+      const int ncl = bt->ncls[P];
+      const int occ = P == 6 ? bapply_occupancy<6>(ncl)
+                    : P == 8 ? bapply_occupancy<8>(ncl) : bapply_occupancy<10>(ncl);
+      bt->bapply_grid[P] = (int)std::min<long long>(S, (long long)std::max(1, occ) * nsm);
     }
     bt->d_off.alloc(n);
     bt->d_off.upload(d_off.data(), n, nullptr);

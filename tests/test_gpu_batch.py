@@ -12,13 +12,20 @@ from tests.helpers import OracleProblem, rel_inf, TWO_PI
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
+# with orders N = 1, 3 the batch runs the element kernel and the gather-scatter
+# kernel; with N in {5, 7, 9} only, the fused operator (segments of four
+# elements, split gather-scatter): partial segments, single-element rows and
+# meshes one element thick are included
 PROBLEMS = [((3, 2, 2), 5, 0.7), ((2, 2, 2), 7, 3.1), ((4, 3, 2), 3, 0.1), ((1, 1, 2), 9, 9.5),
             ((3, 3, 3), 7, 1.7), ((3, 3, 2), 1, 2.0)]
+PROBLEMS_FUSED = [((3, 2, 2), 5, 0.7), ((2, 2, 2), 7, 3.1), ((1, 1, 2), 9, 9.5),
+                  ((3, 3, 3), 7, 1.7), ((5, 1, 3), 5, 0.4), ((7, 3, 1), 7, 2.2),
+                  ((6, 5, 4), 9, 0.9)]
 
 
-def _setup():
+def _setup(problems):
     hs, oracles, bs = [], [], []
-    for q, (nel, N, lam) in enumerate(PROBLEMS):
+    for q, (nel, N, lam) in enumerate(problems):
         h = sem.sem_setup(nel, N, length=(TWO_PI,) * 3, deform=0.1)
         o = OracleProblem(nel, N, length=(TWO_PI,) * 3, deform=0.1)
         f = si.eval_fourier(si.fourier_modes(2000 + q), o.x, o.y, o.z)
@@ -30,11 +37,12 @@ def _setup():
 
 
 @pytest.mark.parametrize("use_graph", [True, False])
-def test_batch_matches_oracle_and_single_solves(use_graph):
-    hs, oracles, bs = _setup()
+@pytest.mark.parametrize("problems", [PROBLEMS, PROBLEMS_FUSED], ids=["unfused", "fused"])
+def test_batch_matches_oracle_and_single_solves(use_graph, problems):
+    hs, oracles, bs = _setup(problems)
     batch = sem.sem_batch_create(hs)
     xs = [torch.empty_like(b) for _, b in bs]
-    lams = [lam for _, _, lam in PROBLEMS]
+    lams = [lam for _, _, lam in problems]
     infos = sem.sem_batch_solve(batch, [b for _, b in bs], xs, [1.0] * len(hs), lams, tol=1e-8,
                                 check_every=5, use_graph=use_graph)
     for q, (h, o, (b_ref, b), x, info) in enumerate(zip(hs, oracles, bs, xs, infos)):
