@@ -27,10 +27,10 @@
 
 namespace sem {
 
-int launch_ax_tma_fused(const sem_handle* h, const float* u, float* w, float h1, float h2,
-                        const float* h1f, const CGState* st, cudaStream_t s);
-int launch_ax_df_fused(const sem_handle* h, const double* u, double* w, double h1, double h2,
-                       const CGState* st, cudaStream_t s);
+bool launch_ax_tma_fused(const sem_handle* h, const float* u, float* w, float h1, float h2,
+                         const float* h1f, const CGState* st, CGState* pwst, cudaStream_t s);
+bool launch_ax_df_fused(const sem_handle* h, const double* u, double* w, double h1, double h2,
+                        const CGState* st, CGState* pwst, cudaStream_t s);
 bool df_ax_supported(const sem_handle* h, const void* u, const void* w, const void* h1f);
 
 namespace {
@@ -175,28 +175,31 @@ bool apply_fused_supported<double>(const sem_handle* h, const void* u, const voi
 }
 
 template <class T>
-void launch_apply(sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2, const T* h1f,
-                  const CGState* st, int phase, cudaStream_t s) {
+bool launch_apply(sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2, const T* h1f,
+                  const CGState* st, int phase, cudaStream_t s, CGState* pwst) {
   if (!apply_fused_supported<T>(h, u, w, h1f)) {
     // element kernel and the gather-scatter kernel, in the full phase
     if (phase & SEM_APPLY_LOCAL) launch_ax<T>(h, op, u, w, h1, h2, h1f, st, s);
     if (phase & SEM_APPLY_FINISH) launch_dssum<T>(h, w, true, st, s);
-    return;
+    return false;
   }
+  bool pw = false;
   if (phase & SEM_APPLY_LOCAL) {
     if constexpr (std::is_same<T, float>::value)
-      launch_ax_tma_fused(h, u, w, h1, h2, h1f, st, s);
+      pw = launch_ax_tma_fused(h, u, w, h1, h2, h1f, st, pwst, s);
     else
-      launch_ax_df_fused(h, u, w, h1, h2, st, s);
+      pw = launch_ax_df_fused(h, u, w, h1, h2, st, pwst, s);
   }
   if (phase & SEM_APPLY_FINISH) finish<T>(h, w, st, s);
+  return pw;
 }
 
-template void launch_apply<float>(sem_handle*, const OpData<float>&, const float*, float*, float,
-                                  float, const float*, const CGState*, int, cudaStream_t);
-template void launch_apply<double>(sem_handle*, const OpData<double>&, const double*, double*,
+template bool launch_apply<float>(sem_handle*, const OpData<float>&, const float*, float*, float,
+                                  float, const float*, const CGState*, int, cudaStream_t,
+                                  CGState*);
+template bool launch_apply<double>(sem_handle*, const OpData<double>&, const double*, double*,
                                    double, double, const double*, const CGState*, int,
-                                   cudaStream_t);
+                                   cudaStream_t, CGState*);
 
 }  // namespace sem
 

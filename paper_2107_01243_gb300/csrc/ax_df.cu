@@ -23,6 +23,7 @@
 #include "tma.cuh"
 #include "df.cuh"
 #include "ax_tile.cuh"
+#include "reduce.cuh"
 
 namespace sem {
 
@@ -123,7 +124,8 @@ template <int P, int STAGES, bool FUSE>
 __global__ void __launch_bounds__(3 * P * P, P == 8 ? 5 : 1)     // P = 8: five CTAs per SM
 ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2* __restrict__ G,
              const float2* __restrict__ B, DFScal C, int E, const CGState* __restrict__ st,
-             int* __restrict__ err, uint64_t timeout_ns, FuseBox fb) {
+             int* __restrict__ err, uint64_t timeout_ns, FuseBox fb, CGState* __restrict__ pwst,
+             double* __restrict__ partials) {
   using L = DFLayout<P>;
   constexpr int P2 = P * P, P3 = P2 * P, NT = 3 * P2;
   constexpr uint32_t UB = P3 * sizeof(double), GB = 6 * P3 * sizeof(float2),
@@ -183,6 +185,9 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
 
   BoxWalk bw;                          // thread 0 (FUSE)
   __shared__ unsigned s_fl;            // FusedStore flags of the current element
+  // FUSE with pwst: <p, H p> = sum over local points of p (H_L p) (p continuous
+  // and zero on Dirichlet points), accumulated per thread in pair arithmetic
+  float pw_s = 0.0f, pw_e = 0.0f;
   int n = 0;
   for (int e = seq.first(); e < E; e = seq.next(e), ++n) {
     const int s = n % STAGES;
@@ -205,7 +210,7 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
         for (int nn = n; nn < issued; ++nn)
           mbar_wait_bounded(&bar[nn % STAGES], (uint32_t)(nn / STAGES) & 1u, err, timeout_ns);
       }
-      return;
+      break;                           // the reduction below still counts this CTA
     }
     if (FUSE && tid == 0) {            // box position of e, read back in the output phase
       if (e % kFuseSeg == 0) bw.start(e, fb); else bw.step(fb);
@@ -270,6 +275,10 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
         dfmul(C.h2h, C.h2l, bv.x, bv.y, bh, bl);
         tmac(bh, bl, uv.x, uv.y, S, er);
       }
+      if (FUSE && pwst) {
+        const float2 pv = U[at];
+        tmac(pv.x, pv.y, S, er, pw_s, pw_e);
+      }
       const double val = (double)S + (double)er;   // exact widenings, one rounding
       if constexpr (FUSE)
         fs.store(q % P, (q / P) % P, q / P2, val);
@@ -284,6 +293,21 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
           issue(ahead, s);
           ahead = seq.next(ahead);
           ++issued;
+        }
+      }
+    }
+  }
+  if constexpr (FUSE && (3 * P * P) % 32 == 0) {
+    if (pwst) {
+      double v[1] = {(double)pw_s + (double)pw_e};
+      double tot[1];
+      if (grid_sum<1>(v, partials, &pwst->counter, tot) && threadIdx.x == 0) {
+        pwst->pw = tot[0];
+        if (!(tot[0] > 0.0)) {
+          pwst->status = SEM_ERR_BREAKDOWN;
+          pwst->done = 1;
+        } else {
+          pwst->alpha = pwst->rz / tot[0];
         }
       }
     }
@@ -345,7 +369,7 @@ static void df_upload_d(const sem_handle* h) {
 // returns the grid it launched (the fused operator's later passes need it)
 template <int P, int STAGES, bool FUSE = false>
 static int launch_df_p(const sem_handle* h, const double* u, double* w, double h1, double h2,
-                       const CGState* st, cudaStream_t s) {
+                       const CGState* st, cudaStream_t s, CGState* pwst = nullptr) {
   const bool helm = (float)h2 != 0.0f;
   const size_t smem = df_smem_bytes<P, STAGES>(helm);
   auto kern = ax_df_kernel<P, STAGES, FUSE>;
@@ -372,9 +396,10 @@ static int launch_df_p(const sem_handle* h, const double* u, double* w, double h
   const int E = (int)h->E;
   int grid = (int)std::min<int64_t>(E, (int64_t)o * df_num_sms());
   if (grid < 1) grid = 1;
+  if (pwst) grid = std::min(grid, kFusedPartials);
   const FuseBox fb{h->nelx, h->nely, h->nelz, h->faces};
   kern<<<grid, 3 * P * P, smem, s>>>(u, w, h->gdf.ptr, h->bdf.ptr, c, E, st, h->dev_err.ptr,
-                                     kWaitTimeoutNs, fb);
+                                     kWaitTimeoutNs, fb, pwst, h->partials.ptr + 4 * kRedBlocks);
   SEM_CHECK_LAUNCH();
   return grid;
 }
@@ -405,16 +430,24 @@ void launch_ax_df(const sem_handle* h, const double* u, double* w, double h1, do
   }
 }
 
-int launch_ax_df_fused(const sem_handle* h, const double* u, double* w, double h1, double h2,
-                       const CGState* st, cudaStream_t s) {
+// pwst (may be NULL): state that receives <p, H p> and alpha, for the order
+// whose CTAs are whole warps (P = 8); returns whether it was computed
+bool launch_ax_df_fused(const sem_handle* h, const double* u, double* w, double h1, double h2,
+                        const CGState* st, CGState* pwst, cudaStream_t s) {
   const bool two = h->tune.df_variant != 0;
   switch (h->P) {
-    case 6: return two ? launch_df_p<6, 2, true>(h, u, w, h1, h2, st, s)
-                       : launch_df_p<6, 1, true>(h, u, w, h1, h2, st, s);
-    case 8: return two ? launch_df_p<8, 2, true>(h, u, w, h1, h2, st, s)
-                       : launch_df_p<8, 1, true>(h, u, w, h1, h2, st, s);
-    case 10: return two ? launch_df_p<10, 2, true>(h, u, w, h1, h2, st, s)
-                        : launch_df_p<10, 1, true>(h, u, w, h1, h2, st, s);
+    case 6:
+      if (two) launch_df_p<6, 2, true>(h, u, w, h1, h2, st, s);
+      else launch_df_p<6, 1, true>(h, u, w, h1, h2, st, s);
+      return false;
+    case 8:
+      if (two) launch_df_p<8, 2, true>(h, u, w, h1, h2, st, s, pwst);
+      else launch_df_p<8, 1, true>(h, u, w, h1, h2, st, s, pwst);
+      return pwst != nullptr;
+    case 10:
+      if (two) launch_df_p<10, 2, true>(h, u, w, h1, h2, st, s);
+      else launch_df_p<10, 1, true>(h, u, w, h1, h2, st, s);
+      return false;
     default: throw Error(SEM_ERR_ARG, "launch_ax_df_fused: unsupported order");
   }
 }

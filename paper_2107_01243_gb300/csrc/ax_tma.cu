@@ -15,6 +15,7 @@
 #include "sem_internal.cuh"
 #include "tma.cuh"
 #include "ax_tile.cuh"
+#include "reduce.cuh"
 
 namespace sem {
 
@@ -26,7 +27,8 @@ __global__ void __launch_bounds__(K * P * P)
 ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ G,
               const T* __restrict__ B, const T* __restrict__ h1f, T h1, T h2, DMat<P, T> D,
               int E, const CGState* __restrict__ st, int* __restrict__ err, uint64_t timeout_ns,
-              uint32_t starve_bytes, FuseBox fb) {
+              uint32_t starve_bytes, FuseBox fb, CGState* __restrict__ pwst,
+              double* __restrict__ partials) {
   static_assert(!FUSE || K == 1, "the fused output needs one element per CTA");
   constexpr int P2 = P * P, P3 = P2 * P;
   constexpr uint32_t FB = P3 * sizeof(T);          // bytes of one field of one element
@@ -85,6 +87,10 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
     }
   }
 
+  // FUSE with pwst: <p, H p> = sum over local points of p (H_L p), which
+  // equals the unique-dof product of p with the assembled, masked H p (p is
+  // continuous and zero on Dirichlet points), accumulated here per thread
+  float pw_s = 0.0f, pw_c = 0.0f;      // Kahan-compensated
   int n = 0;
   for (int it = seq.first(); it < nitems; it = seq.next(it), ++n) {
     const int s = n % STAGES;
@@ -104,7 +110,7 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
         for (int nn = n; nn < issued; ++nn)
           mbar_wait_bounded(&bar[nn % STAGES], (uint32_t)(nn / STAGES) & 1u, err, timeout_ns);
       }
-      return;
+      break;                           // the reduction below still counts this CTA
     }
     if (FUSE && tid == 0) {            // box position of e0, read back in the output phase
       if (e0 % kFuseSeg == 0) bw.start(e0, fb); else bw.step(fb);
@@ -123,12 +129,37 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
       FusedStore<P, T> fs;
       fs.we = w + (size_t)e0 * P3;
       fs.fl = s_fl;
-      tile_backward<P, T>(t, swr, swsT, wt, uc, bk, h2, helm, Dm,
-                          [&](int k, T v) { fs.store(t.i, t.j, k, v); });
+      if (pwst) {
+        tile_backward<P, T>(t, swr, swsT, wt, uc, bk, h2, helm, Dm, [&](int k, T v) {
+          const float y = __fsub_rn(__fmul_rn((float)uc[k], (float)v), pw_c);
+          const float tt = __fadd_rn(pw_s, y);
+          pw_c = __fsub_rn(__fsub_rn(tt, pw_s), y);
+          pw_s = tt;
+          fs.store(t.i, t.j, k, v);
+        });
+      } else {
+        tile_backward<P, T>(t, swr, swsT, wt, uc, bk, h2, helm, Dm,
+                            [&](int k, T v) { fs.store(t.i, t.j, k, v); });
+      }
     } else {
       T* we = w + (size_t)(e0 + slot) * P3;
       tile_backward<P, T>(t, swr, swsT, wt, uc, bk, h2, helm, Dm,
                           [&](int k, T v) { we[k * P2 + t.lt] = v; });
+    }
+  }
+  if constexpr (FUSE && (K * P * P) % 32 == 0) {
+    if (pwst) {
+      double v[1] = {(double)pw_s - (double)pw_c};
+      double tot[1];
+      if (grid_sum<1>(v, partials, &pwst->counter, tot) && threadIdx.x == 0) {
+        pwst->pw = tot[0];
+        if (!(tot[0] > 0.0)) {
+          pwst->status = SEM_ERR_BREAKDOWN;
+          pwst->done = 1;
+        } else {
+          pwst->alpha = pwst->rz / tot[0];
+        }
+      }
     }
   }
 }
@@ -154,7 +185,7 @@ static int num_sms() {
 template <int P, class T, int STAGES, int K, bool FUSE = false>
 static int launch_tma_p(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
                         const T* h1f, const CGState* st, int* err, uint64_t timeout_ns,
-                        uint32_t starve, cudaStream_t s) {
+                        uint32_t starve, cudaStream_t s, CGState* pwst = nullptr) {
   const int nf = 7 + (h2 != T(0) ? 1 : 0) + (h1f ? 1 : 0);
   const size_t smem = tma_smem_bytes<P, T, STAGES, K>(nf);
   auto kern = ax_tma_kernel<P, T, STAGES, K, FUSE>;
@@ -176,9 +207,11 @@ static int launch_tma_p(const sem_handle* h, const OpData<T>& op, const T* u, T*
   const int nitems = (E + K - 1) / K;
   int grid = std::min<int64_t>(nitems, (int64_t)o * num_sms());
   if (grid < 1) grid = 1;
+  if (pwst) grid = std::min(grid, kFusedPartials);
   const FuseBox fb{h->nelx, h->nely, h->nelz, h->faces};
   kern<<<grid, K * P * P, smem, s>>>(u, w, op.G.ptr, op.B.ptr, h1f, h1, h2, D, E, st, err,
-                                     timeout_ns, starve, fb);
+                                     timeout_ns, starve, fb, pwst,
+                                     h->partials.ptr + 4 * kRedBlocks);
   SEM_CHECK_LAUNCH();
   return grid;
 }
@@ -225,26 +258,29 @@ void launch_ax_tma(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T
 // faces = the Dirichlet faces to zero (0: none).  Returns the grid.
 template <int P>
 static int launch_tma_fused_p(const sem_handle* h, const float* u, float* w, float h1, float h2,
-                              const float* h1f, const CGState* st, cudaStream_t s) {
+                              const float* h1f, const CGState* st, CGState* pwst,
+                              cudaStream_t s) {
   const int stages = kTmaVariantStages[h->tune.ax32_variant];
   if (stages == 1)
     return launch_tma_p<P, float, 1, 1, true>(h, h->f32, u, w, h1, h2, h1f, st,
-                                              h->dev_err.ptr, kWaitTimeoutNs, 0, s);
+                                              h->dev_err.ptr, kWaitTimeoutNs, 0, s, pwst);
   if (stages == 2)
     return launch_tma_p<P, float, 2, 1, true>(h, h->f32, u, w, h1, h2, h1f, st,
-                                              h->dev_err.ptr, kWaitTimeoutNs, 0, s);
+                                              h->dev_err.ptr, kWaitTimeoutNs, 0, s, pwst);
   return launch_tma_p<P, float, 3, 1, true>(h, h->f32, u, w, h1, h2, h1f, st, h->dev_err.ptr,
-                                            kWaitTimeoutNs, 0, s);
+                                            kWaitTimeoutNs, 0, s, pwst);
 }
 
-int launch_ax_tma_fused(const sem_handle* h, const float* u, float* w, float h1, float h2,
-                        const float* h1f, const CGState* st, cudaStream_t s) {
+// pwst (may be NULL): state that receives <p, H p> and alpha, for orders whose
+// CTAs are whole warps (P = 8); returns whether it was computed
+bool launch_ax_tma_fused(const sem_handle* h, const float* u, float* w, float h1, float h2,
+                         const float* h1f, const CGState* st, CGState* pwst, cudaStream_t s) {
   switch (h->P) {
-    case 2: return launch_tma_fused_p<2>(h, u, w, h1, h2, h1f, st, s);
-    case 4: return launch_tma_fused_p<4>(h, u, w, h1, h2, h1f, st, s);
-    case 6: return launch_tma_fused_p<6>(h, u, w, h1, h2, h1f, st, s);
-    case 8: return launch_tma_fused_p<8>(h, u, w, h1, h2, h1f, st, s);
-    case 10: return launch_tma_fused_p<10>(h, u, w, h1, h2, h1f, st, s);
+    case 2: launch_tma_fused_p<2>(h, u, w, h1, h2, h1f, st, nullptr, s); return false;
+    case 4: launch_tma_fused_p<4>(h, u, w, h1, h2, h1f, st, nullptr, s); return false;
+    case 6: launch_tma_fused_p<6>(h, u, w, h1, h2, h1f, st, nullptr, s); return false;
+    case 8: launch_tma_fused_p<8>(h, u, w, h1, h2, h1f, st, pwst, s); return pwst != nullptr;
+    case 10: launch_tma_fused_p<10>(h, u, w, h1, h2, h1f, st, nullptr, s); return false;
     default: throw Error(SEM_ERR_ARG, "launch_ax_tma_fused: unsupported order");
   }
 }

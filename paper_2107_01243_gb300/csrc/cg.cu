@@ -481,11 +481,14 @@ static bool vec_ok(int64_t n, std::initializer_list<const T*> ptrs, const float*
 }
 
 // FP64 pw / update / p-update with the reduced-FP64-operation kernels
-static void launch_vec64(sem_handle* h, const PcgArgs<double>& a, cudaStream_t s) {
+static void launch_vec64(sem_handle* h, const PcgArgs<double>& a, bool pw_done, cudaStream_t s) {
   const int64_t nv = h->nL / 2;
-  k_pw_v64<<<kRedBlocks, kRedThreads, 0, s>>>(nv, (const double2*)a.p, (const double2*)a.w,
-                                              (const float2*)h->imult.ptr, a.st, h->partials.ptr);
-  SEM_CHECK_LAUNCH();
+  if (!pw_done) {
+    k_pw_v64<<<kRedBlocks, kRedThreads, 0, s>>>(nv, (const double2*)a.p, (const double2*)a.w,
+                                                (const float2*)h->imult.ptr, a.st,
+                                                h->partials.ptr);
+    SEM_CHECK_LAUNCH();
+  }
   k_update_v64<<<kRedBlocks, kRedThreads, 0, s>>>(
       nv, (double2*)a.x, (double2*)a.r, (const double2*)a.p, (const double2*)a.w,
       (const double2*)a.dmi, (const float2*)h->imult.ptr, a.st, h->partials.ptr);
@@ -500,11 +503,13 @@ static void pcg_iterations(sem_handle* h, const PcgArgs<T>& a, int count, cudaSt
   const int64_t n = h->nL;
   const bool vec = vec_ok<T>(n, {a.x, a.r, a.p, a.w, a.dinv, a.dmi}, h->imult.ptr);
   for (int c = 0; c < count; ++c) {
-    launch_apply<T>(h, *a.op, a.p, a.w, a.h1, a.h2, a.h1f, a.st, SEM_APPLY_FULL, s);
+    // the element kernel may take <p, w> and alpha itself (FP32, P = 8)
+    const bool pw_done =
+        launch_apply<T>(h, *a.op, a.p, a.w, a.h1, a.h2, a.h1f, a.st, SEM_APPLY_FULL, s, a.st);
     bool done64 = false;
     if constexpr (std::is_same<T, double>::value) {
       if (vec && a.dmi) {
-        launch_vec64(h, a, s);
+        launch_vec64(h, a, pw_done, s);
         done64 = true;
       }
     }
@@ -513,9 +518,12 @@ static void pcg_iterations(sem_handle* h, const PcgArgs<T>& a, int count, cudaSt
       using V = typename Vec<T>::V;
       using M = typename Vec<T>::M;
       const int64_t nv = n / Vec<T>::L;
-      k_pw_v<T><<<kRedBlocks, kRedThreads, 0, s>>>(nv, (const V*)a.p, (const V*)a.w,
-                                                   (const M*)h->imult.ptr, a.st, h->partials.ptr);
-      SEM_CHECK_LAUNCH();
+      if (!pw_done) {
+        k_pw_v<T><<<kRedBlocks, kRedThreads, 0, s>>>(nv, (const V*)a.p, (const V*)a.w,
+                                                     (const M*)h->imult.ptr, a.st,
+                                                     h->partials.ptr);
+        SEM_CHECK_LAUNCH();
+      }
       k_update_v<T><<<kRedBlocks, kRedThreads, 0, s>>>(nv, (V*)a.x, (V*)a.r, (const V*)a.p,
                                                        (const V*)a.w, (const V*)a.dinv,
                                                        (const M*)h->imult.ptr, a.st,
@@ -525,8 +533,11 @@ static void pcg_iterations(sem_handle* h, const PcgArgs<T>& a, int count, cudaSt
                                                      (const V*)a.dinv, a.st);
       SEM_CHECK_LAUNCH();
     } else {
-      k_pw<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, a.p, a.w, h->imult.ptr, a.st, h->partials.ptr);
-      SEM_CHECK_LAUNCH();
+      if (!pw_done) {
+        k_pw<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, a.p, a.w, h->imult.ptr, a.st,
+                                                   h->partials.ptr);
+        SEM_CHECK_LAUNCH();
+      }
       k_update<T><<<kRedBlocks, kRedThreads, 0, s>>>(n, a.x, a.r, a.p, a.w, a.dinv, h->imult.ptr,
                                                      a.st, h->partials.ptr);
       SEM_CHECK_LAUNCH();

@@ -19,6 +19,7 @@ constexpr int kMaxP = kMaxN + 1;
 constexpr int kNumSMs = 152;         // GB300: 2 dies x 76 SMs
 constexpr int kRedBlocks = 4 * kNumSMs;   // blocks of every reduction kernel
 constexpr int kRedThreads = 256;
+constexpr int kFusedPartials = 2048;   // partials of the element kernels' fused <p, Hp>
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;   // bounded device waits give up after 2 s
 
 // ------------------------------------------------------------------ errors
@@ -192,12 +193,14 @@ void launch_ax(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1,
 // bulk-copy staged variant (even P, 16-byte aligned vectors)
 template <class T>
 bool tma_ax_supported(const sem_handle* h, const void* u, const void* w, const void* h1f);
-// the assembled operator (apply.cu); phase = SEM_APPLY_* bits
+// the assembled operator (apply.cu); phase = SEM_APPLY_* bits.  pwst (may be
+// NULL): a CG state that the element kernel gives <p, H p> and alpha (p = u);
+// returns whether it did
 template <class T>
 bool apply_fused_supported(const sem_handle* h, const void* u, const void* w, const void* h1f);
 template <class T>
-void launch_apply(sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2, const T* h1f,
-                  const CGState* st, int phase, cudaStream_t s);
+bool launch_apply(sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2, const T* h1f,
+                  const CGState* st, int phase, cudaStream_t s, CGState* pwst = nullptr);
 template <class T>
 void launch_ax_tma(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
                    const T* h1f, const CGState* state, int* err, uint64_t timeout_ns,

@@ -434,7 +434,7 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
     SEM_CUDA(cudaMemsetAsync(h->dev_err.ptr, 0, sizeof(int), s));
     h->state.alloc(3);
     SEM_CUDA(cudaMemsetAsync(h->state.ptr, 0, 3 * sizeof(CGState), s));
-    h->partials.alloc(4 * kRedBlocks);
+    h->partials.alloc(4 * kRedBlocks + kFusedPartials);
     SEM_CUDA(cudaStreamSynchronize(s));
     *out = h.release();
   });

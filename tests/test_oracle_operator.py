@@ -219,3 +219,24 @@ def test_assembled_masked_operator_spd(nel, N):
         wL = operator.matvec(eg[m["gid"]], m["G"], m["D"], m["gid"], mask)
         expect = (A[:, col] * interior)[m["gid"]]
         np.testing.assert_allclose(wL, expect, atol=1e-12 * np.abs(A).max())
+
+
+@pytest.mark.parametrize("h2", [0.0, 1.7])
+def test_energy_from_local_products(h2):
+    """<p, mask QQ^T H_L p> on unique dofs equals sum_L p_L (H_L p)_L when p is
+    continuous and zero on Dirichlet points (the identity the element kernels
+    use to form <p, w> of CG without the gather-scatter)."""
+    m = build((3, 2, 3), 5, length=(2 * math.pi,) * 3, deform=0.1)
+    gid, mult = m["gid"], m["mult"]
+    mask = mesh.dirichlet_mask(3, 2, 3, 5)
+    pg = si.uniform(int(gid.max()) + 1, 9)
+    p = pg[gid] * mask                      # continuous, zero on the boundary
+    w = operator.matvec(p, m["G"], m["D"], gid, mask, 1.0, h2, m["B"])
+    lhs = operator.weighted_dot(p, w, mult)
+    rhs = float(np.sum(p * operator.ax_local(p, m["G"], m["D"], 1.0, h2, m["B"])))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    # a p that is not continuous breaks it: the identity is not a tautology
+    q = p + 1e-3 * si.uniform(p.shape, 10) * mask
+    wq = operator.matvec(q, m["G"], m["D"], gid, mask, 1.0, h2, m["B"])
+    assert abs(operator.weighted_dot(q, wq, mult) -
+               float(np.sum(q * operator.ax_local(q, m["G"], m["D"], 1.0, h2, m["B"])))) > 1e-9
