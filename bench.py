@@ -366,6 +366,7 @@ def main():
         line["batch"] = run_batch(sem, torch, dev)
     if not args.no_solve:
         line["manufactured"] = run_manufactured(sem, torch, dev)
+        line["projection"] = run_projection(sem, torch, dev)
         line["adjoint"] = run_adjoint(sem, torch, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -467,6 +468,46 @@ def _coords(sem, torch, h, dev):
     for t, f in zip(xs, (sem.SEM_FIELD_X, sem.SEM_FIELD_Y, sem.SEM_FIELD_Z)):
         sem.sem_get_field(h, f, t)
     return [t.cpu().numpy() for t in xs]
+
+
+def run_projection(sem, torch, dev, nsolve=8, m=20):
+    """Successive right-hand sides (8 Fourier modes whose phases drift, as
+    successive time steps produce) on the 32^3 throughput mesh, N = 7,
+    mixed-precision PCG to 1e-8: from zero each time, and from the projection
+    onto the space of previous solutions (m = 20, as Neko keeps for its
+    pressure solves)."""
+    cfg = WORKLOAD
+    h = sem.sem_setup(cfg["nel"], cfg["N"], length=cfg["length"], deform=cfg["deform"])
+    sem.sem_autotune(h)
+    X, Y, Z = _coords(sem, torch, h, dev)
+    bs = []
+    for k in range(nsolve):
+        f = torch.from_numpy(si.eval_fourier(si.drifting_modes(cfg["seed"] + 1, k), X, Y, Z)).to(dev)
+        b = torch.empty_like(f)
+        sem.sem_rhs(h, f, b)
+        bs.append(b)
+    del X, Y, Z
+    x = torch.empty_like(bs[0])
+    sem.sem_cg_solve(h, bs[0], x, tol=1e-8, precision=sem.SEM_SOLVE_MIXED)   # warm-up
+    out = {"workload": f"{nsolve} successive right-hand sides (drifting Fourier modes), 32^3 "
+                       "deformed elements, N=7, mixed precision to 1e-8", "space": m}
+    for name in ("plain", "projected"):
+        p = sem.sem_proj_create(h, m) if name == "projected" else None
+        its = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b in bs:
+            if p is None:
+                info = sem.sem_cg_solve(h, b, x, tol=1e-8, precision=sem.SEM_SOLVE_MIXED)
+            else:
+                info = sem.sem_proj_solve(p, b, x, tol=1e-8, precision=sem.SEM_SOLVE_MIXED)
+            its.append(info["iters"])
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "iters": its}
+        if p is not None:
+            sem.sem_proj_destroy(p)
+    sem.sem_destroy(h)
+    return out
 
 
 def run_manufactured(sem, torch, dev):

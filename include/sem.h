@@ -35,6 +35,7 @@ extern "C" {
 
 typedef struct sem_handle sem_handle;
 typedef struct sem_batch sem_batch;
+typedef struct sem_proj sem_proj;
 
 typedef enum {
   SEM_OK = 0,
@@ -308,6 +309,30 @@ sem_status sem_batch_solve(sem_batch* b, const double* const* b_L, double* const
                            const double* h1, const double* h2, const sem_solve_opts* opts,
                            sem_solve_info* infos);
 sem_status sem_batch_destroy(sem_batch* b);
+
+/*
+ * Projection onto previous solutions for successive right-hand sides (§4,
+ * Table 2: Neko keeps 20 previous pressure solutions).  A space of at most m
+ * previous solutions of H x = b on handle h is kept H-orthonormal in the
+ * unique-dof inner product, with H X stored beside it (2 m FP64 L-vectors,
+ * owned by the space).  sem_proj_solve(b, x): x_bar = X X^T b (the best
+ * approximation in the H-norm from the space, no matvec), then PCG (any
+ * sem_solve_opts precision) on the remainder to ||b - H x|| <= tol ||b||,
+ * x = x_bar + correction; the correction is H-orthonormalised against the
+ * space (Gram-Schmidt twice, one matvec) and appended, and a full space
+ * restarts from x alone.  info->iters counts the PCG iterations of the
+ * correction (0 when the projection already meets tol), info->rel_res is
+ * ||b - H x|| / ||b|| of the returned x.  Constant h1 only (h1_field must be
+ * NULL); the same h1, h2 must be used for every solve of a space (reset it
+ * otherwise).  Synchronises the stream.  Errors: SEM_ERR_ARG (m outside
+ * [0, 64], null pointers), the statuses of sem_cg_solve.
+ */
+sem_status sem_proj_create(sem_handle* h, int m, sem_proj** out);
+sem_status sem_proj_solve(sem_proj* p, const double* b_L, double* x_L,
+                          const sem_solve_opts* opts, sem_solve_info* info);
+sem_status sem_proj_size(const sem_proj* p, int* l);     /* vectors in the space */
+sem_status sem_proj_reset(sem_proj* p);                  /* empty the space */
+sem_status sem_proj_destroy(sem_proj* p);
 
 /*
  * sem_helmholtz_grad --g_L = -(D^ lambda)^T G (D^ u) at every local point,

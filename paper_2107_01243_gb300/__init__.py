@@ -19,5 +19,6 @@ from .api import (Handle, sem_setup, sem_destroy, sem_get_sizes, sem_get_field, 
                   sem_selftest_timeout, sem_set_f64_kernel, sem_set_dssum_kernel,
                   sem_autotune, sem_set_tuning,
                   sem_dot_noalloc, Batch, sem_batch_create, sem_batch_solve,
-                  sem_batch_destroy)
+                  sem_batch_destroy, Projection, sem_proj_create, sem_proj_solve,
+                  sem_proj_size, sem_proj_reset, sem_proj_destroy)
 from .autograd import HelmholtzSolve, helmholtz_solve

@@ -77,6 +77,12 @@ SIGNATURES = {
     "sem_dssum": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P]),
     "sem_apply": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_double, _P,
                                  ctypes.c_int, ctypes.c_int, _P]),
+    "sem_proj_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "sem_proj_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(SolveOpts),
+                                      ctypes.POINTER(SolveInfo)]),
+    "sem_proj_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "sem_proj_reset": (ctypes.c_int, [_P]),
+    "sem_proj_destroy": (ctypes.c_int, [_P]),
     "sem_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
     "sem_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "sem_cg_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(SolveOpts),

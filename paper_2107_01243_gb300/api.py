@@ -311,3 +311,67 @@ def sem_batch_solve(batch, bs, xs, h1s, h2s, tol=1e-8, maxit=20000, inner_tol=1e
     check(lib.sem_batch_solve(batch.ptr, pb, px, c1, c2, ctypes.byref(o), infos))
     return [dict(iters=i.iters, outer_iters=i.outer_iters, rel_res=i.rel_res,
                  status=STATUS_NAMES.get(i.status, i.status)) for i in infos]
+
+
+class Projection:
+    """Owns a sem_proj* (space of previous solutions) on a Handle that must outlive it."""
+
+    def __init__(self, h, m=20):
+        out = ctypes.c_void_p()
+        check(_lib.load().sem_proj_create(h.ptr, int(m), ctypes.byref(out)))
+        self.h = h
+        self.m = int(m)
+        self.ptr = out
+
+    def __del__(self):
+        try:
+            sem_proj_destroy(self)
+        except Exception:
+            pass
+
+
+def sem_proj_create(h, m=20):
+    """Space of at most m previous solutions of H x = b on handle h."""
+    return Projection(h, m)
+
+
+def sem_proj_destroy(p):
+    if p is not None and p.ptr:
+        ptr, p.ptr = p.ptr, None
+        check(_lib.load().sem_proj_destroy(ptr))
+
+
+def sem_proj_size(p):
+    n = ctypes.c_int()
+    check(_lib.load().sem_proj_size(p.ptr, ctypes.byref(n)))
+    return n.value
+
+
+def sem_proj_reset(p):
+    check(_lib.load().sem_proj_reset(p.ptr))
+
+
+def sem_proj_solve(p, b, x, h1=1.0, h2=0.0, tol=1e-8, maxit=20000, precision=SEM_SOLVE_F64,
+                   inner_tol=1e-4, max_outer=30, check_every=16, use_graph=True, stream=None,
+                   raise_on_fail=True):
+    """Solve H x = b starting from the projection onto the space p, then add
+    the correction to the space; returns the info dict."""
+    lib = _lib.load()
+    h = p.h
+    o = SolveOpts()
+    lib.sem_solve_opts_default(ctypes.byref(o))
+    o.h1, o.h2 = float(h1), float(h2)
+    o.tol, o.maxit = float(tol), int(maxit)
+    o.precision = int(precision)
+    o.inner_tol, o.max_outer = float(inner_tol), int(max_outer)
+    o.check_every, o.use_graph = int(check_every), int(bool(use_graph))
+    o.stream = _stream(stream).value
+    pb = h._vec(b, "b", torch.float64)
+    px = h._vec(x, "x", torch.float64)
+    info = SolveInfo()
+    st = lib.sem_proj_solve(p.ptr, pb, px, ctypes.byref(o), ctypes.byref(info))
+    res = dict(iters=info.iters, outer_iters=info.outer_iters, rel_res=info.rel_res,
+               status=STATUS_NAMES.get(info.status, info.status))
+    if st != 0 and (raise_on_fail or st not in (SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN)):
+        check(st)
+    return res

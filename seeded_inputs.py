@@ -46,6 +46,15 @@ def eval_fourier(modes, x, y, z):
     return f
 
 
+def drifting_modes(seed, step, rate=0.05, n_modes=8, kmax=4):
+    """The modes of fourier_modes(seed) with every phase advanced by
+    step * rate * omega_m (omega_m ~ U(0.5, 1.5), seeded): a sequence of
+    slowly varying right-hand sides, as successive time steps produce."""
+    a, k, phi = fourier_modes(seed, n_modes, kmax)
+    omega = np.random.default_rng(seed + 7919).uniform(0.5, 1.5, size=n_modes)
+    return a, k, phi + step * rate * omega
+
+
 def manufactured_u(x, y, z):
     return np.sin(math.pi * x) * np.sin(math.pi * y) * np.sin(math.pi * z)
 
