@@ -449,7 +449,13 @@ def run_solves(sem, torch, dev):
     sem.sem_rhs(h, f, b)
     out = {"workload": "Poisson, 48^3 deformed hex elements, N=7, 8 Fourier-mode RHS",
            "local_points": n, "tol": cfg["tol"]}
-    for name, prec in (("fp64", sem.SEM_SOLVE_F64), ("mixed", sem.SEM_SOLVE_MIXED)):
+    # mixed: FP32 inner PCG on global (unique-dof) vectors; mixed_local_inner:
+    # the same solve with the inner PCG on L-vectors (assembled operator with
+    # gather-scatter passes)
+    for name, prec, inner in (("fp64", sem.SEM_SOLVE_F64, sem.SEM_INNER_AUTO),
+                              ("mixed", sem.SEM_SOLVE_MIXED, sem.SEM_INNER_GLOBAL),
+                              ("mixed_local_inner", sem.SEM_SOLVE_MIXED, sem.SEM_INNER_LOCAL)):
+        sem.sem_set_inner_vectors(h, inner)
         x = torch.empty_like(b)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -459,6 +465,8 @@ def run_solves(sem, torch, dev):
         out[name] = {"seconds": el, "iters": info["iters"], "outer": info["outer_iters"],
                      "rel_res": info["rel_res"], "status": info["status"]}
     out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    out["speedup_global_vs_local_inner"] = (out["mixed_local_inner"]["seconds"] /
+                                            out["mixed"]["seconds"])
     sem.sem_destroy(h)
     return out
 

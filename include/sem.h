@@ -67,6 +67,12 @@ enum { SEM_DSSUM_BOX = 0,       /* copies computed from the box topology (defaul
        SEM_DSSUM_SEGMENTS = 1   /* precomputed segment lists of shared local points */
 };
 
+/* vectors of the FP32 inner solves of SEM_SOLVE_MIXED (sem_set_inner_vectors) */
+enum { SEM_INNER_AUTO = 0,      /* global where supported (constant h1, odd N), else local */
+       SEM_INNER_LOCAL = 1,     /* L-vectors, assembled operator with gather-scatter passes */
+       SEM_INNER_GLOBAL = 2     /* unique-dof vectors, element kernels assemble by atomics */
+};
+
 /* phases of sem_apply */
 enum { SEM_APPLY_LOCAL = 1,     /* element operator, x-neighbour sums inside CTAs, mask */
        SEM_APPLY_FINISH = 2,    /* remaining gather-scatter passes */
@@ -226,6 +232,41 @@ sem_status sem_set_tuning(sem_handle* h, const sem_tuning* t);
  */
 sem_status sem_apply(sem_handle* h, const void* u_L, void* w_L, double h1, double h2,
                      const void* h1_field, int dtype, int phase, void* stream);
+
+/*
+ * sem_apply_global -- the same operator on global (unique-dof) vectors:
+ * w_g = mask o Q^T (h1 A_L + h2 B_L) Q u_g (§2, Eq. 9-10 with the scatter Q
+ * and gather Q^T applied by the element kernel itself).  u_g and w_g are
+ * distinct FP32 device arrays of n_G values (sem_get_sizes), numbered
+ * g = ix + gx (iy + gy iz) on the GLL lattice of the box, gx = N nelx + 1,
+ * gy = N nely + 1 (the numbering of SEM_FIELD_GID).  Each element reads its
+ * values from u_g, stores the points inside it and adds those on its faces
+ * to w_g with atomics, so results can differ in the last bits from run to
+ * run.  Needs FP32 geometry, odd N (even P) and n_L < 2^31; SEM_ERR_ARG
+ * otherwise.  dtype must be SEM_F32.  Asynchronous on stream.
+ */
+sem_status sem_apply_global(sem_handle* h, const void* u_g, void* w_g, double h1, double h2,
+                            int dtype, void* stream);
+
+/*
+ * sem_to_global -- out_g[g] = in_L at a local copy of g (FP32 out_g of n_G
+ * values; in_L an L-vector of dtype SEM_F32 or SEM_F64 that must be
+ * continuous, every copy of a point holding the same value, as sem_dssum or
+ * sem_apply leave it).  Needs n_L < 2^31.  Asynchronous on stream.
+ */
+sem_status sem_to_global(sem_handle* h, const void* in_L, void* out_g, int dtype, void* stream);
+
+/*
+ * sem_set_inner_vectors -- choose the vectors of the FP32 inner PCG of
+ * SEM_SOLVE_MIXED: SEM_INNER_LOCAL runs it on L-vectors with sem_apply's
+ * operator; SEM_INNER_GLOBAL on global vectors with sem_apply_global's
+ * (a third fewer bytes per vector pass at N = 7, no gather-scatter passes);
+ * SEM_INNER_AUTO (the default) takes the global form where it is supported
+ * (constant h1, odd N) and the local one elsewhere.  SEM_INNER_GLOBAL on an
+ * unsupported problem falls back to the local form.  The FP64 outer
+ * refinement is the same in all cases.
+ */
+sem_status sem_set_inner_vectors(sem_handle* h, int kind);
 
 /*
  * sem_dssum -- in place w_L <- QQ^T w_L: every local copy of a global point

@@ -53,6 +53,14 @@ class Handle:
         except Exception:
             pass
 
+    def _gvec(self, t, name):
+        """A contiguous FP32 CUDA tensor of n_G values (a global vector)."""
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+            raise SemError(1, f"{name} must be a contiguous CUDA tensor")
+        if t.numel() != self.n_global or t.dtype != torch.float32:
+            raise SemError(1, f"{name} must hold n_G = {self.n_global} float32 values")
+        return ctypes.c_void_p(t.data_ptr())
+
     def _vec(self, t, name, dtype=None):
         if not isinstance(t, torch.Tensor):
             raise SemError(1, f"{name} must be a torch tensor")
@@ -130,6 +138,28 @@ def sem_apply(h, u, w, h1=1.0, h2=0.0, h1_field=None, phase=_lib.SEM_APPLY_FULL,
     check(_lib.load().sem_apply(h.ptr, pu, pw, float(h1), float(h2), pf, _dtype_code(u),
                                 int(phase), _stream(stream)))
     return w
+
+
+def sem_apply_global(h, u_g, w_g, h1=1.0, h2=0.0, stream=None):
+    """w_g = mask o Q^T (h1 A_L + h2 B_L) Q u_g on FP32 global vectors (n_G values)."""
+    pu = h._gvec(u_g, "u_g")
+    pw = h._gvec(w_g, "w_g")
+    check(_lib.load().sem_apply_global(h.ptr, pu, pw, float(h1), float(h2), SEM_F32,
+                                       _stream(stream)))
+    return w_g
+
+
+def sem_to_global(h, u, out_g, stream=None):
+    """out_g[g] = u at a local copy of g (u continuous, FP64 or FP32; out_g FP32)."""
+    pu = h._vec(u, "u")
+    po = h._gvec(out_g, "out_g")
+    check(_lib.load().sem_to_global(h.ptr, pu, po, _dtype_code(u), _stream(stream)))
+    return out_g
+
+
+def sem_set_inner_vectors(h, kind):
+    """Vectors of the FP32 inner solves: SEM_INNER_AUTO, SEM_INNER_LOCAL or SEM_INNER_GLOBAL."""
+    check(_lib.load().sem_set_inner_vectors(h.ptr, int(kind)))
 
 
 def sem_dssum(h, w, apply_mask=True, stream=None):

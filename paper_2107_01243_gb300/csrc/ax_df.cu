@@ -24,6 +24,7 @@
 #include "df.cuh"
 #include "ax_tile.cuh"
 #include "reduce.cuh"
+#include "cg_state.cuh"
 
 namespace sem {
 
@@ -302,13 +303,7 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       double v[1] = {(double)pw_s + (double)pw_e};
       double tot[1];
       if (grid_sum<1>(v, partials, &pwst->counter, tot) && threadIdx.x == 0) {
-        pwst->pw = tot[0];
-        if (!(tot[0] > 0.0)) {
-          pwst->status = SEM_ERR_BREAKDOWN;
-          pwst->done = 1;
-        } else {
-          pwst->alpha = pwst->rz / tot[0];
-        }
+        st_after_pw(pwst, tot[0]);
       }
     }
   }

@@ -16,6 +16,7 @@
 #include "tma.cuh"
 #include "ax_tile.cuh"
 #include "reduce.cuh"
+#include "cg_state.cuh"
 
 namespace sem {
 
@@ -152,13 +153,7 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
       double v[1] = {(double)pw_s - (double)pw_c};
       double tot[1];
       if (grid_sum<1>(v, partials, &pwst->counter, tot) && threadIdx.x == 0) {
-        pwst->pw = tot[0];
-        if (!(tot[0] > 0.0)) {
-          pwst->status = SEM_ERR_BREAKDOWN;
-          pwst->done = 1;
-        } else {
-          pwst->alpha = pwst->rz / tot[0];
-        }
+        st_after_pw(pwst, tot[0]);
       }
     }
   }

@@ -27,6 +27,7 @@
 #include "sem_internal.cuh"
 #include "tma.cuh"
 #include "reduce.cuh"
+#include "cg_state.cuh"
 #include "ax_tile.cuh"
 
 namespace sem {
@@ -447,13 +448,7 @@ bpw_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob, i
     if (item_sum<1>(v, partials, it, b.v_off, b.v_cnt, &tickets[pi], tot, nitems) &&
         threadIdx.x == 0) {
       CGState* st = b.st;
-      st->pw = tot[0];
-      if (!(tot[0] > 0.0)) {
-        st->status = SEM_ERR_BREAKDOWN;
-        st->done = 1;
-      } else {
-        st->alpha = st->rz / tot[0];
-      }
+      st_after_pw(st, tot[0]);
     }
     __syncthreads();
   }
@@ -503,20 +498,7 @@ bupdate_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_pro
     if (item_sum<2>(v, partials, it, b.v_off, b.v_cnt, &tickets[pi], tot, nitems) &&
         threadIdx.x == 0) {
       CGState* st = b.st;
-      st->iter += 1;
-      st->rr = tot[1];
-      if (!(tot[1] == tot[1]) || !(tot[0] == tot[0])) {
-        st->status = SEM_ERR_BREAKDOWN;
-        st->done = 1;
-      } else if (tot[1] <= st->tol2) {
-        st->done = 1;
-      } else if (st->iter >= st->maxit) {
-        st->status = SEM_ERR_NOCONV;
-        st->done = 1;
-      } else {
-        st->beta = tot[0] / st->rz;
-        st->rz = tot[0];
-      }
+      st_after_update(st, tot);
     }
     __syncthreads();
   }

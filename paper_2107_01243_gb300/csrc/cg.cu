@@ -16,6 +16,7 @@
 
 #include "sem_internal.cuh"
 #include "reduce.cuh"
+#include "cg_state.cuh"
 
 namespace sem {
 
@@ -83,15 +84,7 @@ k_pw_v(int64_t nv, const typename Vec<T>::V* __restrict__ p, const typename Vec<
   }
   double v[1] = {a0.value()};
   double tot[1];
-  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
-    st->pw = tot[0];
-    if (!(tot[0] > 0.0)) {
-      st->status = SEM_ERR_BREAKDOWN;
-      st->done = 1;
-    } else {
-      st->alpha = st->rz / tot[0];
-    }
-  }
+  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) st_after_pw(st, tot[0]);
 }
 
 template <class T>
@@ -129,22 +122,7 @@ k_update_v(int64_t nv, typename Vec<T>::V* __restrict__ x, typename Vec<T>::V* _
   }
   double v[2] = {a0.value(), a1.value()};
   double tot[2];
-  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
-    st->iter += 1;
-    st->rr = tot[1];
-    if (!(tot[1] == tot[1]) || !(tot[0] == tot[0])) {
-      st->status = SEM_ERR_BREAKDOWN;
-      st->done = 1;
-    } else if (tot[1] <= st->tol2) {
-      st->done = 1;
-    } else if (st->iter >= st->maxit) {
-      st->status = SEM_ERR_NOCONV;
-      st->done = 1;
-    } else {
-      st->beta = tot[0] / st->rz;
-      st->rz = tot[0];
-    }
-  }
+  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) st_after_update(st, tot);
 }
 
 template <class T>
@@ -166,6 +144,77 @@ k_pupd_v(int64_t nv, typename Vec<T>::V* __restrict__ p, const typename Vec<T>::
     for (int l = 0; l < VT::L; ++l) pe[l] = de[l] * re[l] + beta * pe[l];
     p[q] = pq;
   }
+}
+
+// ---- FP32 CG on global (unique-dof) vectors, padded with zeros to a
+// multiple of 4 values: plain dots (every point counted once), and the
+// update pass also clears w for the next operator's atomic assembly.
+__device__ __forceinline__ void rz_rr4(const float4& r, const float4& z, Acc<float>& a0,
+                                       Acc<float>& a1) {
+  a0.add(r.x, z.x, 1.0f); a0.add(r.y, z.y, 1.0f); a0.add(r.z, z.z, 1.0f); a0.add(r.w, z.w, 1.0f);
+  a1.add(r.x, r.x, 1.0f); a1.add(r.y, r.y, 1.0f); a1.add(r.z, r.z, 1.0f); a1.add(r.w, r.w, 1.0f);
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_ginit(int64_t nv, const float4* __restrict__ r, const float4* __restrict__ dinv,
+        float4* __restrict__ p, float4* __restrict__ x, float4* __restrict__ w,
+        CGState* __restrict__ st, double* __restrict__ partials, double tol, int maxit) {
+  Acc<float> a0, a1;
+  const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const float4 rq = r[q], dq = dinv[q];
+    const float4 z = make_float4(dq.x * rq.x, dq.y * rq.y, dq.z * rq.z, dq.w * rq.w);
+    p[q] = z;
+    x[q] = zero;
+    w[q] = zero;
+    rz_rr4(rq, z, a0, a1);
+  }
+  double v[2] = {a0.value(), a1.value()};
+  double tot[2];
+  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0)
+    st_after_init(st, tot, tol, maxit, 1);
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_gpw(int64_t nv, const float4* __restrict__ p, const float4* __restrict__ w,
+      CGState* __restrict__ st, double* __restrict__ partials) {
+  if (st->done) return;
+  Acc<float> a0;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const float4 a = p[q], b = w[q];
+    a0.add(a.x, b.x, 1.0f); a0.add(a.y, b.y, 1.0f); a0.add(a.z, b.z, 1.0f); a0.add(a.w, b.w, 1.0f);
+  }
+  double v[1] = {a0.value()};
+  double tot[1];
+  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) st_after_pw(st, tot[0]);
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_gupdate(int64_t nv, float4* __restrict__ x, float4* __restrict__ r, const float4* __restrict__ p,
+          float4* __restrict__ w, const float4* __restrict__ dinv, CGState* __restrict__ st,
+          double* __restrict__ partials) {
+  if (st->done) return;
+  const float alpha = (float)st->alpha;
+  const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  Acc<float> a0, a1;
+#pragma unroll 2
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    float4 xq = x[q], rq = r[q];
+    const float4 pq = p[q], wq = w[q], dq = dinv[q];
+    xq.x += alpha * pq.x; xq.y += alpha * pq.y; xq.z += alpha * pq.z; xq.w += alpha * pq.w;
+    rq.x -= alpha * wq.x; rq.y -= alpha * wq.y; rq.z -= alpha * wq.z; rq.w -= alpha * wq.w;
+    const float4 z = make_float4(dq.x * rq.x, dq.y * rq.y, dq.z * rq.z, dq.w * rq.w);
+    rz_rr4(rq, z, a0, a1);
+    x[q] = xq;
+    r[q] = rq;
+    w[q] = zero;
+  }
+  double v[2] = {a0.value(), a1.value()};
+  double tot[2];
+  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) st_after_update(st, tot);
 }
 
 // ---- FP64 forms with fewer FP64-pipe operations (that pipe, not HBM, bounds
@@ -194,15 +243,7 @@ k_pw_v64(int64_t nv, const double2* __restrict__ p, const double2* __restrict__ 
   }
   double v[1] = {acc};
   double tot[1];
-  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
-    st->pw = tot[0];
-    if (!(tot[0] > 0.0)) {
-      st->status = SEM_ERR_BREAKDOWN;
-      st->done = 1;
-    } else {
-      st->alpha = st->rz / tot[0];
-    }
-  }
+  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) st_after_pw(st, tot[0]);
 }
 
 __global__ void __launch_bounds__(kRedThreads)
@@ -233,22 +274,7 @@ k_update_v64(int64_t nv, double2* __restrict__ x, double2* __restrict__ r,
   }
   double v[2] = {rz, rr};
   double tot[2];
-  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
-    st->iter += 1;
-    st->rr = tot[1];
-    if (!(tot[1] == tot[1]) || !(tot[0] == tot[0])) {
-      st->status = SEM_ERR_BREAKDOWN;
-      st->done = 1;
-    } else if (tot[1] <= st->tol2) {
-      st->done = 1;
-    } else if (st->iter >= st->maxit) {
-      st->status = SEM_ERR_NOCONV;
-      st->done = 1;
-    } else {
-      st->beta = tot[0] / st->rz;
-      st->rz = tot[0];
-    }
-  }
+  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) st_after_update(st, tot);
 }
 
 template <class T>
@@ -270,18 +296,8 @@ k_init(int64_t n, const T* __restrict__ r, const T* __restrict__ dinv,
   }
   double v[2] = {a0.value(), a1.value()};
   double tot[2];
-  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
-    st->rz = tot[0];
-    st->rr = tot[1];
-    if (bb_from_rr) st->bb = tot[1];
-    st->tol2 = tol * tol * st->bb;
-    st->iter = 0;
-    st->status = SEM_OK;
-    st->maxit = maxit;
-    st->alpha = st->beta = 0.0;
-    st->done = (tot[1] <= st->tol2 || st->bb == 0.0 || maxit <= 0) ? 1 : 0;
-    if (st->done && !(tot[1] <= st->tol2 || st->bb == 0.0)) st->status = SEM_ERR_NOCONV;
-  }
+  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0)
+    st_after_init(st, tot, tol, maxit, bb_from_rr);
 }
 
 template <class T>
@@ -295,15 +311,7 @@ k_pw(int64_t n, const T* __restrict__ p, const T* __restrict__ w, const float* _
     a0.add(p[q], w[q], imult[q]);
   double v[1] = {a0.value()};
   double tot[1];
-  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
-    st->pw = tot[0];
-    if (!(tot[0] > 0.0)) {
-      st->status = SEM_ERR_BREAKDOWN;
-      st->done = 1;
-    } else {
-      st->alpha = st->rz / tot[0];
-    }
-  }
+  if (grid_sum<1>(v, partials, &st->counter, tot) && threadIdx.x == 0) st_after_pw(st, tot[0]);
 }
 
 template <class T>
@@ -326,22 +334,7 @@ k_update(int64_t n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ 
   }
   double v[2] = {a0.value(), a1.value()};
   double tot[2];
-  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
-    st->iter += 1;
-    st->rr = tot[1];
-    if (!(tot[1] == tot[1]) || !(tot[0] == tot[0])) {
-      st->status = SEM_ERR_BREAKDOWN;
-      st->done = 1;
-    } else if (tot[1] <= st->tol2) {
-      st->done = 1;
-    } else if (st->iter >= st->maxit) {
-      st->status = SEM_ERR_NOCONV;
-      st->done = 1;
-    } else {
-      st->beta = tot[0] / st->rz;
-      st->rz = tot[0];
-    }
-  }
+  if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) st_after_update(st, tot);
 }
 
 template <class T>
@@ -547,11 +540,35 @@ static void pcg_iterations(sem_handle* h, const PcgArgs<T>& a, int count, cudaSt
   }
 }
 
-// Runs iterations until the device state says done; returns the final state.
-template <class T>
-static CGState run_pcg(sem_handle* h, const PcgArgs<T>& a, const sem_solve_opts& o,
-                       cudaStream_t s) {
-  CGState hs = read_state(a.st, s);
+// FP32 PCG iterations on the global vectors of the handle
+static void glob_iterations(sem_handle* h, CGState* st, float h1, float h2, int count,
+                            cudaStream_t s) {
+  const int64_t nv = glob_padded(h) / 4;
+  float4* x = reinterpret_cast<float4*>(h->xg.ptr);
+  float4* r = reinterpret_cast<float4*>(h->rg.ptr);
+  float4* p = reinterpret_cast<float4*>(h->pg.ptr);
+  float4* w = reinterpret_cast<float4*>(h->wg.ptr);
+  const float4* d = reinterpret_cast<const float4*>(h->dinvg.ptr);
+  for (int c = 0; c < count; ++c) {
+    const bool pw_done = launch_apply_global(h, h->pg.ptr, h->wg.ptr, h1, h2, st, st, s);
+    if (!pw_done) {
+      k_gpw<<<kRedBlocks, kRedThreads, 0, s>>>(nv, p, w, st, h->partials.ptr);
+      SEM_CHECK_LAUNCH();
+    }
+    k_gupdate<<<kRedBlocks, kRedThreads, 0, s>>>(nv, x, r, p, w, d, st, h->partials.ptr);
+    SEM_CHECK_LAUNCH();
+    k_pupd_v<float><<<kRedBlocks, kRedThreads, 0, s>>>(nv, p, r, d, st);
+    SEM_CHECK_LAUNCH();
+  }
+}
+
+// Runs iterations(count) until the device state st says done (check_every
+// iterations per host check, captured once in a CUDA graph when use_graph);
+// returns the final state.
+template <class F>
+static CGState run_pcg_loop(sem_handle* h, CGState* st, const sem_solve_opts& o, cudaStream_t s,
+                            F iterations) {
+  CGState hs = read_state(st, s);
   if (hs.done) return hs;
   const int batch = std::max(1, o.check_every);
   cudaGraphExec_t exec = nullptr;
@@ -559,7 +576,7 @@ static CGState run_pcg(sem_handle* h, const PcgArgs<T>& a, const sem_solve_opts&
     cudaGraph_t graph = nullptr;
     SEM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     try {
-      pcg_iterations<T>(h, a, batch, s);
+      iterations(batch);
     } catch (...) {
       cudaStreamEndCapture(s, &graph);
       if (graph) cudaGraphDestroy(graph);
@@ -574,8 +591,8 @@ static CGState run_pcg(sem_handle* h, const PcgArgs<T>& a, const sem_solve_opts&
   try {
     while (true) {
       if (exec) SEM_CUDA(cudaGraphLaunch(exec, s));
-      else pcg_iterations<T>(h, a, batch, s);
-      hs = read_state(a.st, s, h->dev_err.ptr);
+      else iterations(batch);
+      hs = read_state(st, s, h->dev_err.ptr);
       if (hs.done) break;
     }
   } catch (...) {
@@ -584,6 +601,12 @@ static CGState run_pcg(sem_handle* h, const PcgArgs<T>& a, const sem_solve_opts&
   }
   if (exec) cudaGraphExecDestroy(exec);
   return hs;
+}
+
+template <class T>
+static CGState run_pcg(sem_handle* h, const PcgArgs<T>& a, const sem_solve_opts& o,
+                       cudaStream_t s) {
+  return run_pcg_loop(h, a.st, o, s, [&](int count) { pcg_iterations<T>(h, a, count, s); });
 }
 
 static void ensure(DevBuf<double>& b, int64_t n) { if (b.n < (size_t)n) b.alloc(n); }
@@ -664,13 +687,30 @@ double inner_target(double inner_tol, double tol, double rel) {
   return std::max(inner_tol, std::min(0.5, need));
 }
 
+// global inner vectors (allocated zeroed, so that the padding stays zero) and
+// the Jacobi diagonal in global form
+static void glob_prepare(sem_handle* h, cudaStream_t s) {
+  const int64_t n = glob_padded(h);
+  for (DevBuf<float>* b : {&h->rg, &h->pg, &h->wg, &h->xg, &h->dinvg}) {
+    if (b->n < (size_t)n) {
+      b->alloc(n);
+      SEM_CUDA(cudaMemsetAsync(b->ptr, 0, n * sizeof(float), s));
+    }
+  }
+  to_global<float>(h, h->f32.dinv.ptr, h->dinvg.ptr, s);
+}
+
 static void solve_mixed(sem_handle* h, const double* b, double* x, const sem_solve_opts& o,
                         sem_solve_info& info, cudaStream_t s) {
   const int64_t n = h->nL;
   if (!h->f32.G.ptr) throw Error(SEM_ERR_STATE, "mixed solve needs FP32 geometry (SEM_PREC_F32)");
+  const bool glob = h->inner_vectors != SEM_INNER_LOCAL && !o.h1_field && glob_supported(h);
   ensure(h->r, n); ensure(h->w, n);
-  ensure(h->r32, n); ensure(h->p32, n); ensure(h->w32, n); ensure(h->x32, n);
+  if (!glob) {
+    ensure(h->r32, n); ensure(h->p32, n); ensure(h->w32, n); ensure(h->x32, n);
+  }
   ensure_dinv(h, o.h1, o.h2, o.h1_field, true, s);
+  if (glob) glob_prepare(h, s);
   const float* h1f32 = nullptr;
   if (o.h1_field) {
     ensure(h->f32.h1f, n);
@@ -687,27 +727,43 @@ static void solve_mixed(sem_handle* h, const double* b, double* x, const sem_sol
   int status = SEM_ERR_NOCONV;
   double rel = 0.0;
   for (;;) {
-    residual64(h, b, x, o.h1, o.h2, o.h1_field, h->r32.ptr, st0, s);
+    residual64(h, b, x, o.h1, o.h2, o.h1_field, glob ? nullptr : h->r32.ptr, st0, s);
     CGState hs = read_state(st0, s);
     rel = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
     if (!(rel == rel)) { status = SEM_ERR_BREAKDOWN; break; }
     if (rel <= o.tol) { status = SEM_OK; break; }
     if (outer >= o.max_outer || total >= o.maxit) { status = SEM_ERR_NOCONV; break; }
-    // inner FP32 PCG on H d = r32, d = 0 initially
-    k_init<float><<<kRedBlocks, kRedThreads, 0, s>>>(n, h->r32.ptr, h->f32.dinv.ptr,
-                                                     h->imult.ptr, h->p32.ptr, h->x32.ptr, st1,
-                                                     h->partials.ptr,
-                                                     inner_target(o.inner_tol, o.tol, rel),
-                                                     o.maxit - total, 1);
-    SEM_CHECK_LAUNCH();
-    PcgArgs<float> a{&h->f32, h->x32.ptr, h->r32.ptr, h->p32.ptr, h->w32.ptr, h->f32.dinv.ptr,
-                     h1f32, (float)o.h1, (float)o.h2, st1};
-    CGState in = run_pcg<float>(h, a, o, s);
+    // inner FP32 PCG on H d = r, d = 0 initially
+    const double itol = inner_target(o.inner_tol, o.tol, rel);
+    CGState in;
+    if (glob) {
+      to_global<double>(h, h->r.ptr, h->rg.ptr, s);
+      const int64_t nv = glob_padded(h) / 4;
+      k_ginit<<<kRedBlocks, kRedThreads, 0, s>>>(
+          nv, (const float4*)h->rg.ptr, (const float4*)h->dinvg.ptr, (float4*)h->pg.ptr,
+          (float4*)h->xg.ptr, (float4*)h->wg.ptr, st1, h->partials.ptr, itol, o.maxit - total);
+      SEM_CHECK_LAUNCH();
+      in = run_pcg_loop(h, st1, o, s, [&](int count) {
+        glob_iterations(h, st1, (float)o.h1, (float)o.h2, count, s);
+      });
+    } else {
+      k_init<float><<<kRedBlocks, kRedThreads, 0, s>>>(n, h->r32.ptr, h->f32.dinv.ptr,
+                                                       h->imult.ptr, h->p32.ptr, h->x32.ptr, st1,
+                                                       h->partials.ptr, itol, o.maxit - total, 1);
+      SEM_CHECK_LAUNCH();
+      PcgArgs<float> a{&h->f32, h->x32.ptr, h->r32.ptr, h->p32.ptr, h->w32.ptr,
+                       h->f32.dinv.ptr, h1f32, (float)o.h1, (float)o.h2, st1};
+      in = run_pcg<float>(h, a, o, s);
+    }
     total += in.iter;
     ++outer;
     if (in.status == SEM_ERR_BREAKDOWN && in.iter == 0) { status = SEM_ERR_BREAKDOWN; break; }
-    k_addx<<<ew_grid(n), 256, 0, s>>>(n, x, h->x32.ptr);
-    SEM_CHECK_LAUNCH();
+    if (glob) {
+      add_from_global(h, x, h->xg.ptr, s);
+    } else {
+      k_addx<<<ew_grid(n), 256, 0, s>>>(n, x, h->x32.ptr);
+      SEM_CHECK_LAUNCH();
+    }
   }
   info.iters = total;
   info.outer_iters = outer;
@@ -810,6 +866,15 @@ extern "C" sem_status sem_cg_solve(sem_handle* h, const double* b_L, double* x_L
     return (sem_status)local.status;
   }
   return SEM_OK;
+}
+
+extern "C" sem_status sem_set_inner_vectors(sem_handle* h, int kind) {
+  return guarded([&] {
+    SEM_REQUIRE(h, "sem_set_inner_vectors: null handle");
+    SEM_REQUIRE(kind == SEM_INNER_AUTO || kind == SEM_INNER_LOCAL || kind == SEM_INNER_GLOBAL,
+                "sem_set_inner_vectors: unknown kind");
+    h->inner_vectors = kind;
+  });
 }
 
 extern "C" sem_status sem_rhs(sem_handle* h, const double* f_L, double* b_L, void* stream) {

@@ -169,6 +169,10 @@ struct sem_handle {
   // solver scratch (allocated on first use)
   sem::DevBuf<double> r, p, w, x64, tmp64;
   sem::DevBuf<float> r32, p32, w32, x32;
+  // FP32 inner solves on global vectors (n_G values padded with zeros to a
+  // multiple of 4): residual, direction, H p, correction, Jacobi diagonal
+  sem::DevBuf<float> rg, pg, wg, xg, dinvg;
+  int inner_vectors = SEM_INNER_AUTO;       // sem_set_inner_vectors
   sem::DevBuf<double> partials;             // reduction partials: [0,2B) solves, [2B,3B) sem_dot
   sem::DevBuf<sem::CGState> state;          // [3]: outer/FP64, inner/FP32, sem_dot ticket
   // host staging for sem_apply_host
@@ -232,6 +236,16 @@ void outer_residual(sem_handle* h, const double* b, const double* x, const sem_s
                     cudaStream_t s);                                   // r, r32, <r,r> -> state[0]
 void outer_update(sem_handle* h, double* x, cudaStream_t s);          // x += x32
 CGState state_to_host(const CGState* d, cudaStream_t s, int* dev_err);
+
+// ---- global.cu: the FP32 operator on global vectors, w_g = mask Q^T H_L Q u_g
+// (w_g must hold zeros at unmasked element-face points); pwst as launch_apply
+bool glob_supported(const sem_handle* h);
+int64_t glob_padded(const sem_handle* h);          // n_G rounded up to a multiple of 4
+bool launch_apply_global(const sem_handle* h, const float* u, float* w, float h1, float h2,
+                         const CGState* st, CGState* pwst, cudaStream_t s);
+template <class Tin>
+void to_global(const sem_handle* h, const Tin* in, float* out, cudaStream_t s);  // owner copies
+void add_from_global(const sem_handle* h, double* x, const float* d, cudaStream_t s);
 
 // ---- grad.cu
 void launch_grad(const sem_handle* h, const double* u, const double* lam, double* g,
