@@ -47,11 +47,11 @@ def peaks():
 # FP64 Ax kernel on the 32^3, N=7 throughput mesh, from one ncu capture of the
 # kernel as it now stands (summary and command under profiles/); a kernel
 # variant that no capture covers reports null.
-AX_TRAFFIC = {"ax_df_kernel<8, 1, 1>": 939_649_792 + 124_298_240}
+AX_TRAFFIC = {"ax_df_kernel<8, 1, 1>": 939_960_320 + 124_171_008}
 # smsp__inst_executed.sum per launch from the same capture: the double-float
 # kernel is bound by instruction issue on the FP32 pipe, so its second roof is
 # the issue rate, 152 SMs x 4 schedulers x the maximum SM clock.
-AX_WARP_INSTR = {"ax_df_kernel<8, 1, 1>": 306_102_072}
+AX_WARP_INSTR = {"ax_df_kernel<8, 1, 1>": 301_503_392}
 ISSUE_PEAK = 152 * 4 * 2.07e9         # warp instructions per second
 
 
@@ -304,6 +304,14 @@ def main():
                              lambda: sem.sem_apply(h, u32, w32, phase=sem.SEM_APPLY_FINISH))
     sep64 = split_times(lambda: sem.sem_ax(h, u, w), lambda: sem.sem_dssum(h, w))
     sep32 = split_times(lambda: sem.sem_ax(h, u32, w32), lambda: sem.sem_dssum(h, w32))
+    # FP32 operator on global vectors (the inner-solve operator): clearing w_g,
+    # then the element kernel that gathers u_g and assembles w_g by reductions
+    ng = h.n_global
+    ug32 = torch.empty(ng, dtype=torch.float32, device=dev)
+    sem.sem_to_global(h, u32, ug32)
+    wg32 = torch.empty_like(ug32)
+    glob32 = sum(split_times(lambda: sem.sem_apply_global(h, ug32, wg32), lambda: None))
+    glob_bytes = 24 * n + 8 * ng            # G 6 x 4 per local point, u_g and w_g 4 + 4 per global
 
     # end to end through the host-buffer call
     w_host = torch.empty_like(u_host).pin_memory()
@@ -345,6 +353,13 @@ def main():
                     "gs_finish_f32_ms": ds32,
                     "ax_f64_gdofs": n / (ax_ms / 1e3) / 1e9,
                     "operator_f32_gdofs": n / ((ax32 + ds32) / 1e3) / 1e9,
+                    "global_f32": {"note": "sem_apply_global: w_g cleared, then gather of "
+                                           "u_g and assembly of w_g by L2 reductions; "
+                                           "GDOF/s counted in local points",
+                                   "ms": glob32, "gdofs": n / (glob32 / 1e3) / 1e9,
+                                   "global_points": ng,
+                                   "algorithmic_gbs": glob_bytes / (glob32 / 1e3) / 1e9,
+                                   "frac": glob_bytes / (glob32 / 1e3) / 1e9 / hbm},
                     "separate": {"note": "sem_ax then sem_dssum (increasing-index gather-scatter)",
                                  "ax_f64_ms": sep64[0], "dssum_f64_ms": sep64[1],
                                  "dssum_f64_gbs": ds_bytes / (sep64[1] / 1e3) / 1e9,
@@ -357,7 +372,7 @@ def main():
         "autotune": tiles,
         "clocks": clk.summary(),
     }
-    del w, w32, u32
+    del w, w32, u32, ug32, wg32
     sem.sem_destroy(h)
 
     if not args.no_solve:
