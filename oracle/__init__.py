@@ -21,6 +21,12 @@ computational fluid dynamics", arXiv 2107.01243) by eye:
                    last paragraph; §4 velocity solver)
 * ``adjoint``   -- the per-point gradient of a loss with respect to a
                    variable diffusion coefficient (structure of Eq. 9)
+* ``projection``-- projection onto previous solutions for successive
+                   right-hand sides (§4, Table 2)
+* ``schwarz``   -- the two-level additive overlapping Schwarz preconditioner:
+                   fast-diagonalisation local solves on grown elements and a
+                   trilinear coarse level solved by a few CG iterations (§4)
+* ``gmres``     -- flexible GMRES(m) with right preconditioning (§4, Table 2)
 * ``dense``     -- brute-force dense element matrices and assembly for tiny
                    meshes, from explicit basis gradients (§2, Eq. 3 and Eq. 9)
 
