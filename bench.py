@@ -382,6 +382,7 @@ def main():
     if not args.no_solve:
         line["manufactured"] = run_manufactured(sem, torch, dev)
         line["projection"] = run_projection(sem, torch, dev)
+        line["pressure"] = run_pressure(sem, torch, dev)
         line["adjoint"] = run_adjoint(sem, torch, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -491,6 +492,60 @@ def _coords(sem, torch, h, dev):
     for t, f in zip(xs, (sem.SEM_FIELD_X, sem.SEM_FIELD_Y, sem.SEM_FIELD_Z)):
         sem.sem_get_field(h, f, t)
     return [t.cpu().numpy() for t in xs]
+
+
+def run_pressure(sem, torch, dev, restart=30):
+    """Neko's pressure-solver path (§4, Table 2) on the 48^3 solve mesh: flexible
+    GMRES(30) preconditioned by the two-level Schwarz method (10 coarse CG
+    iterations), FP64 to 1e-8 (Jacobi-PCG on the same problem is the "solve"
+    section; point-Jacobi GMRES(30) took 9779 iterations, 119 s, and is not
+    rerun here)."""
+    cfg = SOLVE
+    h = sem.sem_setup(cfg["nel"], cfg["N"], length=cfg["length"], deform=cfg["deform"])
+    X, Y, Z = _coords(sem, torch, h, dev)
+    f = torch.from_numpy(si.eval_fourier(si.fourier_modes(cfg["seed"]), X, Y, Z)).to(dev)
+    del X, Y, Z
+    b = torch.empty_like(f)
+    sem.sem_rhs(h, f, b)
+    del f
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pre = sem.sem_schwarz_create(h, 1.0, 0.0, coarse_iters=10)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    out = {"workload": "Poisson, 48^3 deformed hex elements, N=7, 8 Fourier-mode RHS, "
+                       "FP64 to 1e-8", "schwarz_setup_seconds": t_setup}
+    for name, prec in (("gmres_schwarz", pre),):
+        x = torch.empty_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = sem.sem_gmres_solve(h, b, x, tol=cfg["tol"], restart=restart, precond=prec,
+                                   maxit=20000, raise_on_fail=False)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "iters": info["iters"],
+                     "restarts": info["outer_iters"], "rel_res": info["rel_res"],
+                     "status": info["status"]}
+    # one preconditioner application and one FP64 operator, CUDA events
+    r = b.clone()
+    z = torch.empty_like(b)
+    w = torch.empty_like(b)
+    for _ in range(2):
+        sem.sem_schwarz_apply(pre, r, z)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    for _ in range(5):
+        sem.sem_schwarz_apply(pre, r, z)
+    e[1].record()
+    e[2].record()
+    for _ in range(5):
+        sem.sem_apply(h, r, w)
+    e[3].record()
+    torch.cuda.synchronize()
+    out["schwarz_apply_ms"] = e[0].elapsed_time(e[1]) / 5
+    out["operator_f64_ms"] = e[2].elapsed_time(e[3]) / 5
+    sem.sem_schwarz_destroy(pre)
+    sem.sem_destroy(h)
+    return out
 
 
 def run_projection(sem, torch, dev, nsolve=8, m=20):

@@ -36,6 +36,7 @@ extern "C" {
 typedef struct sem_handle sem_handle;
 typedef struct sem_batch sem_batch;
 typedef struct sem_proj sem_proj;
+typedef struct sem_schwarz sem_schwarz;
 
 typedef enum {
   SEM_OK = 0,
@@ -71,6 +72,12 @@ enum { SEM_DSSUM_BOX = 0,       /* copies computed from the box topology (defaul
 enum { SEM_INNER_AUTO = 0,      /* global where supported (constant h1, odd N), else local */
        SEM_INNER_LOCAL = 1,     /* L-vectors, assembled operator with gather-scatter passes */
        SEM_INNER_GLOBAL = 2     /* unique-dof vectors, element kernels assemble by atomics */
+};
+
+/* levels of the Schwarz preconditioner (sem_schwarz_create) */
+enum { SEM_SCHWARZ_LOCAL = 1,   /* overlapping element subdomains, fast diagonalisation */
+       SEM_SCHWARZ_COARSE = 2,  /* trilinear coarse level, fixed-count CG */
+       SEM_SCHWARZ_BOTH = 3     /* the two-level additive method */
 };
 
 /* phases of sem_apply */
@@ -330,6 +337,46 @@ void sem_solve_opts_default(sem_solve_opts* o);
  */
 sem_status sem_cg_solve(sem_handle* h, const double* b_L, double* x_L,
                         const sem_solve_opts* opts, sem_solve_info* info);
+
+/*
+ * Two-level additive overlapping Schwarz preconditioner (§4: Neko's pressure
+ * preconditioner, M^-1 = R_0^T A_0^-1 R_0 + sum_e R_e^T A~_e^-1 R_e).
+ * Local level: each element grown by one GLL point into its neighbours
+ * ((N+3)^3 lattice points, none outside the box, no Dirichlet points); A~_e
+ * is the Kronecker sum of the 1D stiffness and mass matrices of the element
+ * and its neighbours on the undeformed box spacing (len / nel of the mesh
+ * description), inverted by fast diagonalisation; overlapping corrections
+ * add.  Coarse level: trilinear functions on the element vertices, Galerkin
+ * A_0 = R_0 H R_0^T from 8 x 8 element matrices, solved by coarse_iters
+ * Jacobi-CG iterations from zero.  Applied in FP32 (FP64 in and out).
+ * sem_schwarz_create: for H = h1 A + h2 B (h1 > 0, h2 >= 0) and N >= 2 (so
+ * that the point a subdomain takes from a neighbour lies inside it); levels is a
+ * SEM_SCHWARZ_* value; synchronises the stream.  The object refers to h,
+ * which must outlive it.  sem_schwarz_apply: z_L = M^-1 r_L for a continuous,
+ * masked FP64 L-vector r_L (distinct from z_L); z_L is continuous and
+ * masked.  Asynchronous on stream.
+ */
+sem_status sem_schwarz_create(sem_handle* h, double h1, double h2, int levels, int coarse_iters,
+                              void* stream, sem_schwarz** out);
+sem_status sem_schwarz_apply(sem_schwarz* s, const double* r_L, double* z_L, void* stream);
+sem_status sem_schwarz_destroy(sem_schwarz* s);
+
+/*
+ * sem_gmres_solve -- flexible GMRES(restart) with right preconditioning (§4,
+ * Table 2: Neko's pressure solver) for mask o QQ^T (h1 A_L + h2 B_L) x = b in
+ * FP64: Arnoldi with classical Gram-Schmidt applied twice in the unique-dof
+ * inner product, Givens rotations, x formed from the preconditioned
+ * directions; restarts from the true residual.  precond: a Schwarz object
+ * made for the same handle (and coefficients), or NULL for point Jacobi.
+ * opts: h1, h2, tol (relative residual), maxit (iterations), x0_is_zero,
+ * stream as for sem_cg_solve (h1_field must be NULL, precision is ignored).
+ * Allocates 2 restart + 1 L-vectors for the call.  Synchronises once per
+ * iteration.  info: iterations, restarts in outer_iters, final relative
+ * residual.  restart in [1, 200].
+ */
+sem_status sem_gmres_solve(sem_handle* h, const double* b_L, double* x_L,
+                           const sem_solve_opts* opts, int restart, sem_schwarz* precond,
+                           sem_solve_info* info);
 
 /*
  * Batched solves.  sem_batch_create groups n (<= 256) handles, each built with

@@ -14,7 +14,9 @@ method it cites) are:
 
 * subdomain k is element e grown by one GLL point into each neighbour: the
   lattice points N e_d - 1 .. N e_d + N + 1 along each direction d, without
-  points outside the box and without Dirichlet points;
+  points outside the box and without Dirichlet points.  N >= 2, so that the
+  point taken from a neighbour lies inside that neighbour (for N = 1 it would
+  be the neighbour's far vertex, shared with the next element);
 * A~_e is separable, the Kronecker sum of one-dimensional operators on those
   points, h1 (Bz x By x Ax + Bz x Ay x Bx + Az x By x Bx) + h2 Bz x By x Bx,
   where Ad, Bd are the 1D spectral-element stiffness (2/L) D^T W D and lumped
@@ -121,6 +123,7 @@ class Schwarz:
 
     def __init__(self, nel, N, G, B, length=(1.0, 1.0, 1.0), faces=mesh.ALL_FACES, h1=1.0,
                  h2=0.0, coarse_iters=10):
+        assert N >= 2, "the grown subdomains need N >= 2"
         self.nel = tuple(nel)
         self.N = N
         self.faces = faces

@@ -25,6 +25,7 @@ SEM_F64_KERNEL_AUTO, SEM_F64_KERNEL_NATIVE, SEM_F64_KERNEL_DOUBLEFLOAT = 0, 1, 2
 SEM_DSSUM_BOX, SEM_DSSUM_SEGMENTS = 0, 1
 SEM_APPLY_LOCAL, SEM_APPLY_FINISH, SEM_APPLY_FULL = 1, 2, 3
 SEM_INNER_AUTO, SEM_INNER_LOCAL, SEM_INNER_GLOBAL = 0, 1, 2
+SEM_SCHWARZ_LOCAL, SEM_SCHWARZ_COARSE, SEM_SCHWARZ_BOTH = 1, 2, 3
 (SEM_FIELD_X, SEM_FIELD_Y, SEM_FIELD_Z, SEM_FIELD_G, SEM_FIELD_B, SEM_FIELD_MULT,
  SEM_FIELD_MASK, SEM_FIELD_GID, SEM_FIELD_DINV) = range(9)
 
@@ -106,6 +107,12 @@ SIGNATURES = {
                                         ctypes.c_int, _P]),
     "sem_to_global": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "sem_set_inner_vectors": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sem_schwarz_create": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int, _P, ctypes.POINTER(ctypes.c_void_p)]),
+    "sem_schwarz_apply": (ctypes.c_int, [_P, _P, _P, _P]),
+    "sem_schwarz_destroy": (ctypes.c_int, [_P]),
+    "sem_gmres_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.c_int, _P,
+                                       ctypes.POINTER(SolveInfo)]),
     "sem_selftest_timeout": (ctypes.c_int, [_P, ctypes.c_double, _P]),
     "sem_dot_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P]),
 }

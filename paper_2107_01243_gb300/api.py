@@ -405,3 +405,69 @@ def sem_proj_solve(p, b, x, h1=1.0, h2=0.0, tol=1e-8, maxit=20000, precision=SEM
     if st != 0 and (raise_on_fail or st not in (SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN)):
         check(st)
     return res
+
+
+class Schwarz:
+    """Owns a sem_schwarz* (two-level Schwarz preconditioner) on a Handle that
+    must outlive it."""
+
+    def __init__(self, h, h1=1.0, h2=0.0, levels=_lib.SEM_SCHWARZ_BOTH, coarse_iters=10,
+                 stream=None):
+        out = ctypes.c_void_p()
+        check(_lib.load().sem_schwarz_create(h.ptr, float(h1), float(h2), int(levels),
+                                             int(coarse_iters), _stream(stream),
+                                             ctypes.byref(out)))
+        self.h = h
+        self.ptr = out
+
+    def __del__(self):
+        try:
+            sem_schwarz_destroy(self)
+        except Exception:
+            pass
+
+
+def sem_schwarz_create(h, h1=1.0, h2=0.0, levels=_lib.SEM_SCHWARZ_BOTH, coarse_iters=10,
+                       stream=None):
+    """Two-level additive Schwarz preconditioner for H = h1 A + h2 B on handle h."""
+    return Schwarz(h, h1, h2, levels, coarse_iters, stream)
+
+
+def sem_schwarz_destroy(sw):
+    if sw is not None and sw.ptr:
+        ptr, sw.ptr = sw.ptr, None
+        check(_lib.load().sem_schwarz_destroy(ptr))
+
+
+def sem_schwarz_apply(sw, r, z, stream=None):
+    """z = M^-1 r (continuous, masked FP64 L-vectors)."""
+    h = sw.h
+    check(_lib.load().sem_schwarz_apply(sw.ptr, h._vec(r, "r", torch.float64),
+                                        h._vec(z, "z", torch.float64), _stream(stream)))
+    return z
+
+
+def sem_gmres_solve(h, b, x, h1=1.0, h2=0.0, tol=1e-8, maxit=5000, restart=30, precond=None,
+                    x0=None, stream=None, raise_on_fail=True):
+    """Flexible GMRES(restart) for mask o QQ^T H x = b, right-preconditioned by a
+    Schwarz object (or point Jacobi when precond is None); returns the info dict
+    (outer_iters = restart cycles)."""
+    lib = _lib.load()
+    o = SolveOpts()
+    lib.sem_solve_opts_default(ctypes.byref(o))
+    o.h1, o.h2 = float(h1), float(h2)
+    o.tol, o.maxit = float(tol), int(maxit)
+    pb = h._vec(b, "b", torch.float64)
+    px = h._vec(x, "x", torch.float64)
+    if x0 is not None:
+        x.copy_(x0)
+        o.x0_is_zero = 0
+    o.stream = _stream(stream).value
+    info = SolveInfo()
+    st = lib.sem_gmres_solve(h.ptr, pb, px, ctypes.byref(o), int(restart),
+                             precond.ptr if precond is not None else None, ctypes.byref(info))
+    res = dict(iters=info.iters, outer_iters=info.outer_iters, rel_res=info.rel_res,
+               status=STATUS_NAMES.get(info.status, info.status))
+    if st != 0 and (raise_on_fail or st not in (SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN)):
+        check(st)
+    return res

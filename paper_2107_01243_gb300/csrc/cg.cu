@@ -217,6 +217,35 @@ k_gupdate(int64_t nv, float4* __restrict__ x, float4* __restrict__ r, const floa
   if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) st_after_update(st, tot);
 }
 
+void vcg_init(int64_t nv4, const float* r, const float* dinv, float* p, float* x, float* w,
+              CGState* st, double* partials, double tol, int maxit, cudaStream_t s) {
+  k_ginit<<<kRedBlocks, kRedThreads, 0, s>>>(nv4, (const float4*)r, (const float4*)dinv,
+                                             (float4*)p, (float4*)x, (float4*)w, st, partials,
+                                             tol, maxit);
+  SEM_CHECK_LAUNCH();
+}
+
+void vcg_pw(int64_t nv4, const float* p, const float* w, CGState* st, double* partials,
+            cudaStream_t s) {
+  k_gpw<<<kRedBlocks, kRedThreads, 0, s>>>(nv4, (const float4*)p, (const float4*)w, st,
+                                           partials);
+  SEM_CHECK_LAUNCH();
+}
+
+void vcg_update(int64_t nv4, float* x, float* r, const float* p, float* w, const float* dinv,
+                CGState* st, double* partials, cudaStream_t s) {
+  k_gupdate<<<kRedBlocks, kRedThreads, 0, s>>>(nv4, (float4*)x, (float4*)r, (const float4*)p,
+                                               (float4*)w, (const float4*)dinv, st, partials);
+  SEM_CHECK_LAUNCH();
+}
+
+void vcg_pupd(int64_t nv4, float* p, const float* r, const float* dinv, const CGState* st,
+              cudaStream_t s) {
+  k_pupd_v<float><<<kRedBlocks, kRedThreads, 0, s>>>(nv4, (float4*)p, (const float4*)r,
+                                                     (const float4*)dinv, st);
+  SEM_CHECK_LAUNCH();
+}
+
 // ---- FP64 forms with fewer FP64-pipe operations (that pipe, not HBM, bounds
 // the FP64 vector kernels on GB300).  1/mult is a power of two (mult = 1, 2,
 // 4 or 8 copies on the box), so it is widened to double by moving its
@@ -543,22 +572,13 @@ static void pcg_iterations(sem_handle* h, const PcgArgs<T>& a, int count, cudaSt
 // FP32 PCG iterations on the global vectors of the handle
 static void glob_iterations(sem_handle* h, CGState* st, float h1, float h2, int count,
                             cudaStream_t s) {
-  const int64_t nv = glob_padded(h) / 4;
-  float4* x = reinterpret_cast<float4*>(h->xg.ptr);
-  float4* r = reinterpret_cast<float4*>(h->rg.ptr);
-  float4* p = reinterpret_cast<float4*>(h->pg.ptr);
-  float4* w = reinterpret_cast<float4*>(h->wg.ptr);
-  const float4* d = reinterpret_cast<const float4*>(h->dinvg.ptr);
+  const int64_t nv4 = glob_padded(h) / 4;
   for (int c = 0; c < count; ++c) {
     const bool pw_done = launch_apply_global(h, h->pg.ptr, h->wg.ptr, h1, h2, st, st, s);
-    if (!pw_done) {
-      k_gpw<<<kRedBlocks, kRedThreads, 0, s>>>(nv, p, w, st, h->partials.ptr);
-      SEM_CHECK_LAUNCH();
-    }
-    k_gupdate<<<kRedBlocks, kRedThreads, 0, s>>>(nv, x, r, p, w, d, st, h->partials.ptr);
-    SEM_CHECK_LAUNCH();
-    k_pupd_v<float><<<kRedBlocks, kRedThreads, 0, s>>>(nv, p, r, d, st);
-    SEM_CHECK_LAUNCH();
+    if (!pw_done) vcg_pw(nv4, h->pg.ptr, h->wg.ptr, st, h->partials.ptr, s);
+    vcg_update(nv4, h->xg.ptr, h->rg.ptr, h->pg.ptr, h->wg.ptr, h->dinvg.ptr, st,
+               h->partials.ptr, s);
+    vcg_pupd(nv4, h->pg.ptr, h->rg.ptr, h->dinvg.ptr, st, s);
   }
 }
 
@@ -738,11 +758,8 @@ static void solve_mixed(sem_handle* h, const double* b, double* x, const sem_sol
     CGState in;
     if (glob) {
       to_global<double>(h, h->r.ptr, h->rg.ptr, s);
-      const int64_t nv = glob_padded(h) / 4;
-      k_ginit<<<kRedBlocks, kRedThreads, 0, s>>>(
-          nv, (const float4*)h->rg.ptr, (const float4*)h->dinvg.ptr, (float4*)h->pg.ptr,
-          (float4*)h->xg.ptr, (float4*)h->wg.ptr, st1, h->partials.ptr, itol, o.maxit - total);
-      SEM_CHECK_LAUNCH();
+      vcg_init(glob_padded(h) / 4, h->rg.ptr, h->dinvg.ptr, h->pg.ptr, h->xg.ptr, h->wg.ptr,
+               st1, h->partials.ptr, itol, o.maxit - total, s);
       in = run_pcg_loop(h, st1, o, s, [&](int count) {
         glob_iterations(h, st1, (float)o.h1, (float)o.h2, count, s);
       });
@@ -812,6 +829,19 @@ void outer_residual(sem_handle* h, const double* b, const double* x, const sem_s
 
 void outer_update(sem_handle* h, double* x, cudaStream_t s) {
   k_addx<<<ew_grid(h->nL), 256, 0, s>>>(h->nL, x, h->x32.ptr);
+  SEM_CHECK_LAUNCH();
+}
+
+const double* jacobi_dinv64(sem_handle* h, double h1, double h2, cudaStream_t s) {
+  ensure_dinv(h, h1, h2, nullptr, false, s);
+  return h->f64.dinv.ptr;
+}
+
+void residual_f64(sem_handle* h, const double* b, const double* x, double h1, double h2,
+                  double* w, double* r, CGState* st, cudaStream_t s) {
+  launch_apply<double>(h, h->f64, x, w, h1, h2, nullptr, nullptr, SEM_APPLY_FULL, s);
+  k_resid<<<kRedBlocks, kRedThreads, 0, s>>>(h->nL, b, w, r, nullptr, h->imult.ptr, st,
+                                             h->partials.ptr);
   SEM_CHECK_LAUNCH();
 }
 

@@ -1,0 +1,251 @@
+// Flexible GMRES(m) with right preconditioning (arXiv 2107.01243 §4 and
+// Table 2: Neko solves the pressure Poisson equation by preconditioned GMRES,
+// the preconditioner being the two-level Schwarz method whose coarse level is
+// solved only approximately, so the preconditioner varies between
+// applications; the flexible form keeps the preconditioned directions).
+//
+// FP64 L-vectors, unique-dof inner product.  Per iteration j:
+//   z_j = M^-1 v_j;  w = mask o QQ^T H z_j;
+//   h = V^T w, w -= V h, twice (classical Gram-Schmidt repeated);
+//   h_{j+1,j} = ||w||;  v_{j+1} = w / h_{j+1,j}
+// The (m+1) x m Hessenberg matrix, its Givens rotations and the residual
+// estimate live on the host (one synchronisation per iteration); x += Z y at
+// the end of a cycle, and each cycle starts from the true residual.
+#include <cmath>
+#include <memory>
+#include <vector>
+
+#include "sem_internal.cuh"
+#include "reduce.cuh"
+#include "krylov.cuh"
+
+namespace sem {
+namespace {
+
+constexpr int kMaxRestart = 200;
+
+// hcol[i] += coef[i], i < cnt
+__global__ void k_hacc(int cnt, const double* __restrict__ coef, double* __restrict__ hcol) {
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) hcol[i] += coef[i];
+}
+
+// out = s v
+__global__ void k_scale(int64_t n, const double* __restrict__ v, double sc,
+                        double* __restrict__ out) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    out[q] = sc * v[q];
+}
+
+// z = d o v
+__global__ void k_hadamard(int64_t n, const double* __restrict__ d, const double* __restrict__ v,
+                           double* __restrict__ z) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    z[q] = d[q] * v[q];
+}
+
+struct Gmres {
+  sem_handle* h;
+  int m;
+  std::vector<std::unique_ptr<DevBuf<double>>> V, Z;
+  DevBuf<double> w;
+  DevBuf<const double*> vptr, zptr, one;
+  DevBuf<double> coef, hcol, dots, partials;
+  DevBuf<unsigned> counter;
+  double* pin = nullptr;
+  Gmres(sem_handle* hh, int mm, cudaStream_t s) : h(hh), m(mm) {
+    const int64_t n = h->nL;
+    for (int i = 0; i <= m; ++i) {
+      V.emplace_back(new DevBuf<double>());
+      V.back()->alloc(n);
+    }
+    for (int i = 0; i < m; ++i) {
+      Z.emplace_back(new DevBuf<double>());
+      Z.back()->alloc(n);
+    }
+    w.alloc(n);
+    std::vector<const double*> pv, pz;
+    for (auto& b : V) pv.push_back(b->ptr);
+    for (auto& b : Z) pz.push_back(b->ptr);
+    vptr.alloc(m + 1);
+    zptr.alloc(m);
+    one.alloc(1);
+    SEM_CUDA(cudaMemcpyAsync(vptr.ptr, pv.data(), pv.size() * sizeof(double*),
+                             cudaMemcpyHostToDevice, s));
+    SEM_CUDA(cudaMemcpyAsync(zptr.ptr, pz.data(), pz.size() * sizeof(double*),
+                             cudaMemcpyHostToDevice, s));
+    coef.alloc(m + 1);
+    hcol.alloc(m + 2);
+    dots.alloc(1);
+    partials.alloc((size_t)kDotChunk * kRedBlocks);
+    counter.alloc(1);
+    SEM_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned), s));
+    SEM_CUDA(cudaMallocHost(&pin, (m + 4) * sizeof(double)));
+  }
+  ~Gmres() {
+    if (pin) cudaFreeHost(pin);
+  }
+  // out[i] = <V_i, b>, i < cnt (device)
+  void mdot(const double* const* Vp, int cnt, const double* b, double* out, cudaStream_t s) {
+    for (int i0 = 0; i0 < cnt; i0 += kDotChunk) {
+      const int c = std::min(kDotChunk, cnt - i0);
+      k_mdot<kDotChunk><<<kRedBlocks, kRedThreads, 0, s>>>(h->nL, Vp, i0, c, b, h->imult.ptr,
+                                                           out, partials.ptr, counter.ptr);
+      SEM_CHECK_LAUNCH();
+    }
+  }
+  double norm2_host(const double* a, cudaStream_t s) {
+    const double* p[1] = {a};
+    SEM_CUDA(cudaMemcpyAsync(one.ptr, p, sizeof(p), cudaMemcpyHostToDevice, s));
+    mdot(one.ptr, 1, a, dots.ptr, s);
+    SEM_CUDA(cudaMemcpyAsync(pin, dots.ptr, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    return pin[0];
+  }
+};
+
+void check_timeout(sem_handle* h, cudaStream_t s) {
+  int herr = 0;
+  SEM_CUDA(cudaMemcpyAsync(&herr, h->dev_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  if (herr) {
+    SEM_CUDA(cudaMemsetAsync(h->dev_err.ptr, 0, sizeof(int), s));
+    throw Error(SEM_ERR_TIMEOUT, "a bounded device wait timed out during the solve");
+  }
+}
+
+void gmres_solve(sem_handle* h, const double* b, double* x, const sem_solve_opts& o, int m,
+                 sem_schwarz* M, sem_solve_info& info, cudaStream_t s) {
+  const int64_t n = h->nL;
+  Gmres g(h, m, s);
+  const double* dinv = M ? nullptr : jacobi_dinv64(h, o.h1, o.h2, s);
+  const double bnorm = std::sqrt(g.norm2_host(b, s));
+  if (o.x0_is_zero) SEM_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  info = sem_solve_info{0, 0, 0.0, SEM_OK};
+  if (bnorm == 0.0) {
+    SEM_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    return;
+  }
+  CGState* st = h->state.ptr;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  int total = 0, cycles = 0;
+  for (;;) {
+    // true residual into V_0
+    residual_f64(h, b, x, o.h1, o.h2, g.w.ptr, g.V[0]->ptr, st, s);
+    const CGState hs = state_to_host(st, s, h->dev_err.ptr);
+    const double beta = std::sqrt(hs.rr);
+    info.rel_res = beta / bnorm;
+    if (!(beta == beta)) { info.status = SEM_ERR_BREAKDOWN; break; }
+    if (beta <= o.tol * bnorm) { info.status = SEM_OK; break; }
+    if (total >= o.maxit) { info.status = SEM_ERR_NOCONV; break; }
+    ++cycles;
+    k_scale<<<lin_grid(n), 256, 0, s>>>(n, g.V[0]->ptr, 1.0 / beta, g.V[0]->ptr);
+    SEM_CHECK_LAUNCH();
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      double* zj = g.Z[j]->ptr;
+      if (M) {
+        schwarz_apply(M, g.V[j]->ptr, zj, s);
+      } else {
+        k_hadamard<<<lin_grid(n), 256, 0, s>>>(n, dinv, g.V[j]->ptr, zj);
+        SEM_CHECK_LAUNCH();
+      }
+      launch_apply<double>(h, h->f64, zj, g.w.ptr, o.h1, o.h2, nullptr, nullptr, SEM_APPLY_FULL,
+                           s);
+      SEM_CUDA(cudaMemsetAsync(g.hcol.ptr, 0, (j + 1) * sizeof(double), s));
+      for (int pass = 0; pass < 2; ++pass) {
+        g.mdot(g.vptr.ptr, j + 1, g.w.ptr, g.coef.ptr, s);
+        k_mcomb<<<lin_grid(n), 256, 0, s>>>(n, g.vptr.ptr, j + 1, g.coef.ptr, -1.0, g.w.ptr,
+                                            g.w.ptr);
+        SEM_CHECK_LAUNCH();
+        k_hacc<<<1, 256, 0, s>>>(j + 1, g.coef.ptr, g.hcol.ptr);
+        SEM_CHECK_LAUNCH();
+      }
+      const double* wp[1] = {g.w.ptr};
+      SEM_CUDA(cudaMemcpyAsync(g.one.ptr, wp, sizeof(wp), cudaMemcpyHostToDevice, s));
+      g.mdot(g.one.ptr, 1, g.w.ptr, g.dots.ptr, s);
+      SEM_CUDA(cudaMemcpyAsync(g.pin, g.hcol.ptr, (j + 1) * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+      SEM_CUDA(cudaMemcpyAsync(g.pin + m + 2, g.dots.ptr, sizeof(double), cudaMemcpyDeviceToHost,
+                               s));
+      check_timeout(h, s);                    // synchronises
+      for (int i = 0; i <= j; ++i) H[i * m + j] = g.pin[i];
+      const double hn = std::sqrt(std::max(0.0, g.pin[m + 2]));
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t;
+      }
+      const double a = H[j * m + j];
+      if (hn == 0.0) {
+        cs[j] = 1.0;
+        sn[j] = 0.0;
+      } else {
+        const double r = std::hypot(a, hn);
+        cs[j] = a / r;
+        sn[j] = hn / r;
+      }
+      H[j * m + j] = cs[j] * a + sn[j] * hn;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      k = j + 1;
+      ++total;
+      if (!(H[j * m + j] != 0.0) || !(hn == hn)) { info.status = SEM_ERR_BREAKDOWN; break; }
+      if (std::fabs(gv[j + 1]) <= o.tol * bnorm || total >= o.maxit || hn == 0.0) break;
+      k_scale<<<lin_grid(n), 256, 0, s>>>(n, g.w.ptr, 1.0 / hn, g.V[j + 1]->ptr);
+      SEM_CHECK_LAUNCH();
+    }
+    if (info.status == SEM_ERR_BREAKDOWN) break;
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = gv[i];
+      for (int l = i + 1; l < k; ++l) acc -= H[i * m + l] * y[l];
+      y[i] = acc / H[i * m + i];
+    }
+    SEM_CUDA(cudaMemcpyAsync(g.coef.ptr, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+    k_mcomb<<<lin_grid(n), 256, 0, s>>>(n, g.zptr.ptr, k, g.coef.ptr, 1.0, x, x);
+    SEM_CHECK_LAUNCH();
+  }
+  info.iters = total;
+  info.outer_iters = cycles;
+  SEM_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" sem_status sem_gmres_solve(sem_handle* h, const double* b_L, double* x_L,
+                                      const sem_solve_opts* opts, int restart,
+                                      sem_schwarz* precond, sem_solve_info* info) {
+  sem_solve_info local{};
+  sem_status st = guarded([&] {
+    SEM_REQUIRE(h && b_L && x_L, "sem_gmres_solve: null handle or vector");
+    sem_solve_opts o;
+    if (opts) o = *opts; else sem_solve_opts_default(&o);
+    SEM_REQUIRE(o.tol >= 0.0 && o.maxit >= 0, "sem_gmres_solve: bad tol or maxit");
+    SEM_REQUIRE(o.h1_field == nullptr, "sem_gmres_solve: a per-point h1 is not supported");
+    SEM_REQUIRE(restart >= 1 && restart <= kMaxRestart, "sem_gmres_solve: restart in [1, 200]");
+    SEM_REQUIRE(!precond || schwarz_handle(precond) == h,
+                "sem_gmres_solve: the preconditioner belongs to another handle");
+    SEM_REQUIRE(b_L != x_L, "sem_gmres_solve: b and x must not alias");
+    cudaStream_t s = (cudaStream_t)o.stream;
+    gmres_solve(h, b_L, x_L, o, restart, precond, local, s);
+  });
+  if (info) *info = local;
+  if (st != SEM_OK) {
+    if (info) info->status = st;
+    return st;
+  }
+  if (local.status != SEM_OK) {
+    set_last_error(local.status == SEM_ERR_NOCONV ? "sem_gmres_solve: no convergence within maxit"
+                                                  : "sem_gmres_solve: breakdown");
+    return (sem_status)local.status;
+  }
+  return SEM_OK;
+}

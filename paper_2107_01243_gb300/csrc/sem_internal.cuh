@@ -137,6 +137,7 @@ struct sem_handle {
   int64_t E = 0, nL = 0, nG = 0;
   int prec_flags = 0;
   int faces = 0;
+  double len[3] = {1.0, 1.0, 1.0};         // box lengths of the mesh description
   std::vector<double> xi, wq, Dh;          // host GLL nodes, weights, D
 
   sem::DevBuf<double> coords;               // [3][nL]
@@ -246,6 +247,28 @@ bool launch_apply_global(const sem_handle* h, const float* u, float* w, float h1
 template <class Tin>
 void to_global(const sem_handle* h, const Tin* in, float* out, cudaStream_t s);  // owner copies
 void add_from_global(const sem_handle* h, double* x, const float* d, cudaStream_t s);
+
+// ---- cg.cu: FP32 CG steps on vectors padded to a multiple of 4 with zeros
+// (nv4 = padded length / 4), plain dots (each entry counted once); w must
+// hold zeros before an operator assembles into it (init and update clear it).
+// Used by the global-vector inner solves and the Schwarz coarse level.
+void vcg_init(int64_t nv4, const float* r, const float* dinv, float* p, float* x, float* w,
+              CGState* st, double* partials, double tol, int maxit, cudaStream_t s);
+void vcg_pw(int64_t nv4, const float* p, const float* w, CGState* st, double* partials,
+            cudaStream_t s);
+void vcg_update(int64_t nv4, float* x, float* r, const float* p, float* w, const float* dinv,
+                CGState* st, double* partials, cudaStream_t s);
+void vcg_pupd(int64_t nv4, float* p, const float* r, const float* dinv, const CGState* st,
+              cudaStream_t s);
+// Jacobi inverse diagonal of (h1, h2) for the FP64 operator (L-vector, masked)
+const double* jacobi_dinv64(sem_handle* h, double h1, double h2, cudaStream_t s);
+// w = mask o QQ^T H x, r = b - w and <r, r> into st->rr (FP64 L-vectors)
+void residual_f64(sem_handle* h, const double* b, const double* x, double h1, double h2,
+                  double* w, double* r, CGState* st, cudaStream_t s);
+
+// ---- schwarz.cu: z = M^-1 r (FP64 L-vectors)
+void schwarz_apply(sem_schwarz* sw, const double* r, double* z, cudaStream_t s);
+sem_handle* schwarz_handle(const sem_schwarz* sw);
 
 // ---- grad.cu
 void launch_grad(const sem_handle* h, const double* u, const double* lam, double* g,

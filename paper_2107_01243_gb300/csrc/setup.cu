@@ -371,6 +371,7 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
     SEM_REQUIRE(h->nL < (int64_t)INT32_MAX, "sem_setup: more than 2^31 local points");
     h->prec_flags = precision_flags | SEM_PREC_F64;   // FP64 geometry is always kept
     h->faces = mesh->dirichlet_faces & SEM_FACE_ALL;
+    for (int d = 0; d < 3; ++d) h->len[d] = mesh->len[d];
     h->tune.ax32_variant = h->P <= 4 ? 2 : 1;     // 3 stages for small elements, else 2
     gll_host(N, h->xi, h->wq, h->Dh);
 
