@@ -370,9 +370,10 @@ sem_status sem_schwarz_destroy(sem_schwarz* s);
  * made for the same handle (and coefficients), or NULL for point Jacobi.
  * opts: h1, h2, tol (relative residual), maxit (iterations), x0_is_zero,
  * stream as for sem_cg_solve (h1_field must be NULL, precision is ignored).
- * Allocates 2 restart + 1 L-vectors for the call.  Synchronises once per
- * iteration.  info: iterations, restarts in outer_iters, final relative
- * residual.  restart in [1, 200].
+ * The workspace (2 restart + 2 FP64 L-vectors) is allocated on the first
+ * solve and kept on the handle until it is destroyed.  Synchronises once per
+ * iteration.  info: iterations, restart cycles in outer_iters, final
+ * relative residual.  restart in [1, 32].
  */
 sem_status sem_gmres_solve(sem_handle* h, const double* b_L, double* x_L,
                            const sem_solve_opts* opts, int restart, sem_schwarz* precond,

@@ -217,9 +217,15 @@ k_gupdate(int64_t nv, float4* __restrict__ x, float4* __restrict__ r, const floa
   if (grid_sum<2>(v, partials, &st->counter, tot) && threadIdx.x == 0) st_after_update(st, tot);
 }
 
+// grid of the padded-vector CG kernels: a thread per float4 up to kRedBlocks
+// blocks (small vectors, such as the Schwarz coarse level, take fewer)
+static int vcg_grid(int64_t nv4) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kRedBlocks, (nv4 + kRedThreads - 1) / kRedThreads));
+}
+
 void vcg_init(int64_t nv4, const float* r, const float* dinv, float* p, float* x, float* w,
               CGState* st, double* partials, double tol, int maxit, cudaStream_t s) {
-  k_ginit<<<kRedBlocks, kRedThreads, 0, s>>>(nv4, (const float4*)r, (const float4*)dinv,
+  k_ginit<<<vcg_grid(nv4), kRedThreads, 0, s>>>(nv4, (const float4*)r, (const float4*)dinv,
                                              (float4*)p, (float4*)x, (float4*)w, st, partials,
                                              tol, maxit);
   SEM_CHECK_LAUNCH();
@@ -227,22 +233,23 @@ void vcg_init(int64_t nv4, const float* r, const float* dinv, float* p, float* x
 
 void vcg_pw(int64_t nv4, const float* p, const float* w, CGState* st, double* partials,
             cudaStream_t s) {
-  k_gpw<<<kRedBlocks, kRedThreads, 0, s>>>(nv4, (const float4*)p, (const float4*)w, st,
-                                           partials);
+  k_gpw<<<vcg_grid(nv4), kRedThreads, 0, s>>>(nv4, (const float4*)p, (const float4*)w, st,
+                                              partials);
   SEM_CHECK_LAUNCH();
 }
 
 void vcg_update(int64_t nv4, float* x, float* r, const float* p, float* w, const float* dinv,
                 CGState* st, double* partials, cudaStream_t s) {
-  k_gupdate<<<kRedBlocks, kRedThreads, 0, s>>>(nv4, (float4*)x, (float4*)r, (const float4*)p,
-                                               (float4*)w, (const float4*)dinv, st, partials);
+  k_gupdate<<<vcg_grid(nv4), kRedThreads, 0, s>>>(nv4, (float4*)x, (float4*)r,
+                                                  (const float4*)p, (float4*)w,
+                                                  (const float4*)dinv, st, partials);
   SEM_CHECK_LAUNCH();
 }
 
 void vcg_pupd(int64_t nv4, float* p, const float* r, const float* dinv, const CGState* st,
               cudaStream_t s) {
-  k_pupd_v<float><<<kRedBlocks, kRedThreads, 0, s>>>(nv4, (float4*)p, (const float4*)r,
-                                                     (const float4*)dinv, st);
+  k_pupd_v<float><<<vcg_grid(nv4), kRedThreads, 0, s>>>(nv4, (float4*)p, (const float4*)r,
+                                                        (const float4*)dinv, st);
   SEM_CHECK_LAUNCH();
 }
 

@@ -22,12 +22,7 @@
 namespace sem {
 namespace {
 
-constexpr int kMaxRestart = 200;
-
-// hcol[i] += coef[i], i < cnt
-__global__ void k_hacc(int cnt, const double* __restrict__ coef, double* __restrict__ hcol) {
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) hcol[i] += coef[i];
-}
+constexpr int kMaxRestart = 32;         // the fused Gram-Schmidt kernels take 32 vectors
 
 // out = s v
 __global__ void k_scale(int64_t n, const double* __restrict__ v, double sc,
@@ -45,16 +40,87 @@ __global__ void k_hadamard(int64_t n, const double* __restrict__ d, const double
     z[q] = d[q] * v[q];
 }
 
-struct Gmres {
+constexpr int kGsMax = 32;            // vectors a fused Gram-Schmidt kernel takes
+
+// Gram-Schmidt kernels.  Dots: blockIdx.y takes a chunk of kGsChunk vectors
+// (eight accumulators per thread, full occupancy), each chunk reduced on its
+// own counter and partials; updates loop over the vectors with the pointers
+// and coefficients in shared memory.
+constexpr int kGsChunk = 8;
+
+// out[i] = <V_i, w>, i < cnt
+__global__ void __launch_bounds__(kRedThreads)
+k_gs_dots(int64_t n, const double* const* __restrict__ V, int cnt, const double* __restrict__ w,
+          const float* __restrict__ imult, double* __restrict__ out, double* __restrict__ partials,
+          unsigned* __restrict__ counters) {
+  const int i0 = blockIdx.y * kGsChunk;
+  const int c = min(kGsChunk, cnt - i0);
+  const double* v[kGsChunk];
+#pragma unroll
+  for (int i = 0; i < kGsChunk; ++i) v[i] = i < c ? V[i0 + i] : nullptr;
+  double acc[kGsChunk];
+#pragma unroll
+  for (int i = 0; i < kGsChunk; ++i) acc[i] = 0.0;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const double wq = w[q] * (double)imult[q];
+#pragma unroll
+    for (int i = 0; i < kGsChunk; ++i)
+      if (i < c) acc[i] = fma(v[i][q], wq, acc[i]);
+  }
+  double tot[kGsChunk];
+  if (grid_sum<kGsChunk>(acc, partials + (size_t)blockIdx.y * kGsChunk * gridDim.x,
+                         counters + blockIdx.y, tot) &&
+      threadIdx.x == 0)
+    for (int i = 0; i < c; ++i) out[i0 + i] = tot[i];
+}
+
+// w -= sum_{i < cnt} c_i V_i; with out, also out[0] = <w, w>
+__global__ void __launch_bounds__(kRedThreads)
+k_gs_update(int64_t n, const double* const* __restrict__ V, int cnt, const double* __restrict__ c,
+            double* __restrict__ w, const float* __restrict__ imult, double* __restrict__ out,
+            double* __restrict__ partials, unsigned* __restrict__ counter) {
+  __shared__ const double* sv[kGsMax];
+  __shared__ double sc[kGsMax];
+  if (threadIdx.x < kGsMax) {
+    sv[threadIdx.x] = threadIdx.x < cnt ? V[threadIdx.x] : nullptr;
+    sc[threadIdx.x] = threadIdx.x < cnt ? c[threadIdx.x] : 0.0;
+  }
+  __syncthreads();
+  double acc[1] = {0.0};
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    double wq = w[q];
+#pragma unroll 4
+    for (int i = 0; i < cnt; ++i) wq = fma(-sc[i], sv[i][q], wq);
+    w[q] = wq;
+    if (out) acc[0] = fma(wq * (double)imult[q], wq, acc[0]);
+  }
+  if (out) {
+    double tot[1];
+    if (grid_sum<1>(acc, partials, counter, tot) && threadIdx.x == 0) out[0] = tot[0];
+  }
+}
+
+// h = c1 + c2 (the two Gram-Schmidt passes' coefficients), i < cnt
+__global__ void k_hsum(int cnt, const double* __restrict__ c1, const double* __restrict__ c2,
+                       double* __restrict__ h) {
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) h[i] = c1[i] + c2[i];
+}
+
+}  // namespace
+
+// Workspace of the GMRES solver, kept on the handle between solves.
+struct GmresWork {
   sem_handle* h;
   int m;
   std::vector<std::unique_ptr<DevBuf<double>>> V, Z;
   DevBuf<double> w;
   DevBuf<const double*> vptr, zptr, one;
-  DevBuf<double> coef, hcol, dots, partials;
+  DevBuf<double> coef, coef2, hcol, dots, partials;
   DevBuf<unsigned> counter;
   double* pin = nullptr;
-  Gmres(sem_handle* hh, int mm, cudaStream_t s) : h(hh), m(mm) {
+  GmresWork(sem_handle* hh, int mm, cudaStream_t s) : h(hh), m(mm) {
     const int64_t n = h->nL;
     for (int i = 0; i <= m; ++i) {
       V.emplace_back(new DevBuf<double>());
@@ -76,14 +142,15 @@ struct Gmres {
     SEM_CUDA(cudaMemcpyAsync(zptr.ptr, pz.data(), pz.size() * sizeof(double*),
                              cudaMemcpyHostToDevice, s));
     coef.alloc(m + 1);
+    coef2.alloc(m + 1);
     hcol.alloc(m + 2);
     dots.alloc(1);
-    partials.alloc((size_t)kDotChunk * kRedBlocks);
-    counter.alloc(1);
-    SEM_CUDA(cudaMemsetAsync(counter.ptr, 0, sizeof(unsigned), s));
+    partials.alloc((size_t)kGsMax * kRedBlocks);
+    counter.alloc(kGsMax / kGsChunk + 1);      // one per dot chunk, one for the norm
+    SEM_CUDA(cudaMemsetAsync(counter.ptr, 0, (kGsMax / kGsChunk + 1) * sizeof(unsigned), s));
     SEM_CUDA(cudaMallocHost(&pin, (m + 4) * sizeof(double)));
   }
-  ~Gmres() {
+  ~GmresWork() {
     if (pin) cudaFreeHost(pin);
   }
   // out[i] = <V_i, b>, i < cnt (device)
@@ -105,6 +172,8 @@ struct Gmres {
   }
 };
 
+namespace {
+
 void check_timeout(sem_handle* h, cudaStream_t s) {
   int herr = 0;
   SEM_CUDA(cudaMemcpyAsync(&herr, h->dev_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -118,7 +187,11 @@ void check_timeout(sem_handle* h, cudaStream_t s) {
 void gmres_solve(sem_handle* h, const double* b, double* x, const sem_solve_opts& o, int m,
                  sem_schwarz* M, sem_solve_info& info, cudaStream_t s) {
   const int64_t n = h->nL;
-  Gmres g(h, m, s);
+  if (!h->gmres || h->gmres->m < m) {
+    h->gmres.reset();
+    h->gmres = std::make_shared<GmresWork>(h, m, s);
+  }
+  GmresWork& g = *h->gmres;
   const double* dinv = M ? nullptr : jacobi_dinv64(h, o.h1, o.h2, s);
   const double bnorm = std::sqrt(g.norm2_host(b, s));
   if (o.x0_is_zero) SEM_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
@@ -157,18 +230,24 @@ void gmres_solve(sem_handle* h, const double* b, double* x, const sem_solve_opts
       }
       launch_apply<double>(h, h->f64, zj, g.w.ptr, o.h1, o.h2, nullptr, nullptr, SEM_APPLY_FULL,
                            s);
-      SEM_CUDA(cudaMemsetAsync(g.hcol.ptr, 0, (j + 1) * sizeof(double), s));
-      for (int pass = 0; pass < 2; ++pass) {
-        g.mdot(g.vptr.ptr, j + 1, g.w.ptr, g.coef.ptr, s);
-        k_mcomb<<<lin_grid(n), 256, 0, s>>>(n, g.vptr.ptr, j + 1, g.coef.ptr, -1.0, g.w.ptr,
-                                            g.w.ptr);
-        SEM_CHECK_LAUNCH();
-        k_hacc<<<1, 256, 0, s>>>(j + 1, g.coef.ptr, g.hcol.ptr);
-        SEM_CHECK_LAUNCH();
-      }
-      const double* wp[1] = {g.w.ptr};
-      SEM_CUDA(cudaMemcpyAsync(g.one.ptr, wp, sizeof(wp), cudaMemcpyHostToDevice, s));
-      g.mdot(g.one.ptr, 1, g.w.ptr, g.dots.ptr, s);
+      // classical Gram-Schmidt twice: c1 = V^T w; w -= V c1, c2 = V^T w; w -= V c2, ||w||^2
+      const int cnt = j + 1;
+      const dim3 dgrid(kRedBlocks, (cnt + kGsChunk - 1) / kGsChunk);
+      k_gs_dots<<<dgrid, kRedThreads, 0, s>>>(n, g.vptr.ptr, cnt, g.w.ptr, h->imult.ptr,
+                                              g.coef.ptr, g.partials.ptr, g.counter.ptr);
+      SEM_CHECK_LAUNCH();
+      k_gs_update<<<kRedBlocks, kRedThreads, 0, s>>>(n, g.vptr.ptr, cnt, g.coef.ptr, g.w.ptr,
+                                                     h->imult.ptr, nullptr, nullptr, nullptr);
+      SEM_CHECK_LAUNCH();
+      k_gs_dots<<<dgrid, kRedThreads, 0, s>>>(n, g.vptr.ptr, cnt, g.w.ptr, h->imult.ptr,
+                                              g.coef2.ptr, g.partials.ptr, g.counter.ptr);
+      SEM_CHECK_LAUNCH();
+      k_gs_update<<<kRedBlocks, kRedThreads, 0, s>>>(n, g.vptr.ptr, cnt, g.coef2.ptr, g.w.ptr,
+                                                     h->imult.ptr, g.dots.ptr, g.partials.ptr,
+                                                     g.counter.ptr + kGsMax / kGsChunk);
+      SEM_CHECK_LAUNCH();
+      k_hsum<<<1, 64, 0, s>>>(cnt, g.coef.ptr, g.coef2.ptr, g.hcol.ptr);
+      SEM_CHECK_LAUNCH();
       SEM_CUDA(cudaMemcpyAsync(g.pin, g.hcol.ptr, (j + 1) * sizeof(double),
                                cudaMemcpyDeviceToHost, s));
       SEM_CUDA(cudaMemcpyAsync(g.pin + m + 2, g.dots.ptr, sizeof(double), cudaMemcpyDeviceToHost,
@@ -230,7 +309,7 @@ extern "C" sem_status sem_gmres_solve(sem_handle* h, const double* b_L, double* 
     if (opts) o = *opts; else sem_solve_opts_default(&o);
     SEM_REQUIRE(o.tol >= 0.0 && o.maxit >= 0, "sem_gmres_solve: bad tol or maxit");
     SEM_REQUIRE(o.h1_field == nullptr, "sem_gmres_solve: a per-point h1 is not supported");
-    SEM_REQUIRE(restart >= 1 && restart <= kMaxRestart, "sem_gmres_solve: restart in [1, 200]");
+    SEM_REQUIRE(restart >= 1 && restart <= kMaxRestart, "sem_gmres_solve: restart in [1, 32]");
     SEM_REQUIRE(!precond || schwarz_handle(precond) == h,
                 "sem_gmres_solve: the preconditioner belongs to another handle");
     SEM_REQUIRE(b_L != x_L, "sem_gmres_solve: b and x must not alias");

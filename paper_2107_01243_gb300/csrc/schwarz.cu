@@ -162,7 +162,15 @@ __device__ __forceinline__ float dot_row(const float* __restrict__ row, const fl
   return acc;
 }
 
-// One element at a time per CTA.  Box s[c][b][a] with rows padded to R.
+// One element at a time per CTA.  Thread (a, b) < PE^2 owns the z-column of
+// the grown box: it gathers the column, applies S^T along z in registers and
+// writes box[c][b][a] (rows padded to R); the x- and y-directions run as line
+// tasks through shared memory (S^T along x; along y S^T, the diagonal scaling
+// and S; S along x); the thread then reads its column back, applies S along
+// z in registers and adds the kept points to z.  Factors along different
+// directions commute, so this order gives the same A~^-1 as x, y, z first.
+// The coarse restriction is taken from the gathered columns of the element's
+// own points (a, b, c in 1 .. P).
 template <int PE>
 __global__ void __launch_bounds__(kSwThreads, 4)
 schwarz_local_kernel(const float* __restrict__ rg, float* __restrict__ zg,
@@ -176,6 +184,8 @@ schwarz_local_kernel(const float* __restrict__ rg, float* __restrict__ zg,
   for (int q = threadIdx.x; q < L::ALL; q += blockDim.x) tab[q] = tab_g[q];
   __syncthreads();
   const int tid = threadIdx.x;
+  const bool owner = tid < PE * PE;
+  const int ca = tid % PE, cb = tid / PE;          // this thread's column (a, b)
   for (int e = blockIdx.x; e < E; e += gridDim.x) {
     const uint32_t r1 = prm.dnx.div((uint32_t)e);
     const int ex = e - (int)r1 * prm.nelx;
@@ -185,32 +195,37 @@ schwarz_local_kernel(const float* __restrict__ rg, float* __restrict__ zg,
     const int vy = (ey == 0 ? 1 : 0) | (ey == prm.nely - 1 ? 2 : 0);
     const int vz = (ez == 0 ? 1 : 0) | (ez == prm.nelz - 1 ? 2 : 0);
     const unsigned kx = prm.keep[0][vx], ky = prm.keep[1][vy], kz = prm.keep[2][vz];
-    const long long org = (long long)(N * ex - 1) + (long long)prm.gx * (N * ey - 1) +
-                          prm.sk * (long long)(N * ez - 1);
-    // gather the grown box (points not kept read as zero)
-    for (int q = tid; q < PE * PE * PE; q += blockDim.x) {
-      const int a = q % PE, b = (q / PE) % PE, c = q / (PE * PE);
-      float v = 0.0f;
-      if (((kx >> a) & 1u) && ((ky >> b) & 1u) && ((kz >> c) & 1u))
-        v = rg[org + a + (long long)prm.gx * b + prm.sk * c];
-      box[(c * PE + b) * R + a] = v;
-    }
-    __syncthreads();
+    const float* tx = tab + (0 * 4 + vx) * L::TAB;
+    const float* ty = tab + (1 * 4 + vy) * L::TAB;
+    const float* tz = tab + (2 * 4 + vz) * L::TAB;
+    const bool colkeep = owner && ((kx >> ca) & 1u) && ((ky >> cb) & 1u);
+    // lattice index of (a, b, 0) of this thread's column
+    const long long cbase = (long long)(N * ex - 1 + ca) + (long long)prm.gx * (N * ey - 1 + cb) +
+                            prm.sk * (long long)(N * ez - 1);
+    float col[R];
+#pragma unroll
+    for (int c = 0; c < R; ++c)
+      col[c] = (c < PE && colkeep && ((kz >> c) & 1u)) ? rg[cbase + prm.sk * c] : 0.0f;
     if (prm.do_coarse) {
-      // restriction from the element's own points: sum phi_v r / mult
+      // restriction: sum over own points of phi_v r / mult
       float acc[8];
 #pragma unroll
       for (int v = 0; v < 8; ++v) acc[v] = 0.0f;
-      for (int q = tid; q < P * P * P; q += blockDim.x) {
-        const int i = q % P, j = (q / P) % P, k = q / (P * P);
-        const float m = ((i == 0 && ex > 0) || (i == N && ex < prm.nelx - 1) ? 0.5f : 1.0f) *
-                        ((j == 0 && ey > 0) || (j == N && ey < prm.nely - 1) ? 0.5f : 1.0f) *
-                        ((k == 0 && ez > 0) || (k == N && ez < prm.nelz - 1) ? 0.5f : 1.0f);
-        const float rv = m * box[((k + 1) * PE + j + 1) * R + i + 1];
+      if (owner && ca >= 1 && ca <= P && cb >= 1 && cb <= P) {
+        const int i = ca - 1, j = cb - 1;
+        const float mij = ((i == 0 && ex > 0) || (i == N && ex < prm.nelx - 1) ? 0.5f : 1.0f) *
+                          ((j == 0 && ey > 0) || (j == N && ey < prm.nely - 1) ? 0.5f : 1.0f);
+        float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+          const float mk = (k == 0 && ez > 0) || (k == N && ez < prm.nelz - 1) ? 0.5f : 1.0f;
+          const float rv = mk * col[k + 1];
+          s0 = fmaf(prm.phi[0][k], rv, s0);
+          s1 = fmaf(prm.phi[1][k], rv, s1);
+        }
 #pragma unroll
         for (int v = 0; v < 8; ++v)
-          acc[v] = fmaf(prm.phi[v & 1][i] * prm.phi[(v >> 1) & 1][j] * prm.phi[v >> 2][k], rv,
-                        acc[v]);
+          acc[v] = mij * prm.phi[v & 1][i] * prm.phi[(v >> 1) & 1][j] * ((v >> 2) ? s1 : s0);
       }
 #pragma unroll
       for (int v = 0; v < 8; ++v)
@@ -231,10 +246,13 @@ schwarz_local_kernel(const float* __restrict__ rg, float* __restrict__ zg,
       }
     }
     if (prm.do_local) {
-      const float* tx = tab + (0 * 4 + vx) * L::TAB;
-      const float* ty = tab + (1 * 4 + vy) * L::TAB;
-      const float* tz = tab + (2 * 4 + vz) * L::TAB;
-      // phase 1: S^T along x on lines (b, c)
+      // S^T along z in registers, to the box
+      if (owner) {
+#pragma unroll 2
+        for (int c = 0; c < PE; ++c) box[(c * PE + cb) * R + ca] = dot_row<R>(tz + c * R, col, PE);
+      }
+      __syncthreads();
+      // S^T along x on lines (b, c)
       for (int ln = tid; ln < PE * PE; ln += blockDim.x) {
         float* row = box + ln * R;
         float x[R];
@@ -247,51 +265,29 @@ schwarz_local_kernel(const float* __restrict__ rg, float* __restrict__ zg,
         for (int a = 0; a < PE; ++a) row[a] = dot_row<R>(tx + a * R, x, PE);
       }
       __syncthreads();
-      // phase 2: S^T along y on lines (a, c)
+      // along y on lines (a, c): S^T, the diagonal scaling, S
       for (int ln = tid; ln < PE * PE; ln += blockDim.x) {
         const int a = ln % PE, c = ln / PE;
-        float* col = box + c * PE * R + a;
+        float* yl = box + c * PE * R + a;
         float x[R];
 #pragma unroll
-        for (int b = 0; b < R; ++b) x[b] = b < PE ? col[b * R] : 0.0f;
-#pragma unroll 2
-        for (int b = 0; b < PE; ++b) col[b * R] = dot_row<R>(ty + b * R, x, PE);
-      }
-      __syncthreads();
-      // phase 3: along z on lines (a, b): S^T, diagonal scaling, S
-      for (int ln = tid; ln < PE * PE; ln += blockDim.x) {
-        const int a = ln % PE, b = ln / PE;
-        float* col = box + b * R + a;
-        float x[R];
-#pragma unroll
-        for (int c = 0; c < R; ++c) x[c] = c < PE ? col[c * PE * R] : 0.0f;
-        const float lab = tx[2 * PE * R + a] + ty[2 * PE * R + b];
+        for (int b = 0; b < R; ++b) x[b] = b < PE ? yl[b * R] : 0.0f;
+        const float lac = tx[2 * PE * R + a] + tz[2 * PE * R + c];
         float t[R];
 #pragma unroll
-        for (int c = 0; c < R; ++c) {
-          if (c < PE) {
-            const float d = prm.h1 * (lab + tz[2 * PE * R + c]) + prm.h2;
-            t[c] = dot_row<R>(tz + c * R, x, PE) / d;
+        for (int b = 0; b < R; ++b) {
+          if (b < PE) {
+            const float d = prm.h1 * (lac + ty[2 * PE * R + b]) + prm.h2;
+            t[b] = dot_row<R>(ty + b * R, x, PE) / d;
           } else {
-            t[c] = 0.0f;
+            t[b] = 0.0f;
           }
         }
 #pragma unroll 2
-        for (int c = 0; c < PE; ++c) col[c * PE * R] = dot_row<R>(tz + PE * R + c * R, t, PE);
+        for (int b = 0; b < PE; ++b) yl[b * R] = dot_row<R>(ty + PE * R + b * R, t, PE);
       }
       __syncthreads();
-      // phase 4: S along y
-      for (int ln = tid; ln < PE * PE; ln += blockDim.x) {
-        const int a = ln % PE, c = ln / PE;
-        float* col = box + c * PE * R + a;
-        float x[R];
-#pragma unroll
-        for (int b = 0; b < R; ++b) x[b] = b < PE ? col[b * R] : 0.0f;
-#pragma unroll 2
-        for (int b = 0; b < PE; ++b) col[b * R] = dot_row<R>(ty + PE * R + b * R, x, PE);
-      }
-      __syncthreads();
-      // phase 5: S along x
+      // S along x
       for (int ln = tid; ln < PE * PE; ln += blockDim.x) {
         float* row = box + ln * R;
         float x[R];
@@ -304,12 +300,13 @@ schwarz_local_kernel(const float* __restrict__ rg, float* __restrict__ zg,
         for (int a = 0; a < PE; ++a) row[a] = dot_row<R>(tx + PE * R + a * R, x, PE);
       }
       __syncthreads();
-      // scatter-add the kept points
-      for (int q = tid; q < PE * PE * PE; q += blockDim.x) {
-        const int a = q % PE, b = (q / PE) % PE, c = q / (PE * PE);
-        if (((kx >> a) & 1u) && ((ky >> b) & 1u) && ((kz >> c) & 1u))
-          red_add_f32(zg + org + a + (long long)prm.gx * b + prm.sk * c,
-                      box[(c * PE + b) * R + a]);
+      // S along z in registers, add the kept points
+      if (colkeep) {
+#pragma unroll
+        for (int c = 0; c < R; ++c) col[c] = c < PE ? box[(c * PE + cb) * R + ca] : 0.0f;
+#pragma unroll 2
+        for (int c = 0; c < PE; ++c)
+          if ((kz >> c) & 1u) red_add_f32(zg + cbase + prm.sk * c, dot_row<R>(tz + PE * R + c * R, col, PE));
       }
     }
     __syncthreads();                         // box and red are reused by the next element
@@ -428,24 +425,20 @@ __global__ void k_coarse_dinv(int E, const double* __restrict__ diag, float* __r
 }
 
 // z_L = mask o (z_local[g(L)] + sum_v phi_v c_v) at every local point
+template <int P>
 __global__ void k_sw_combine(int64_t nL, const float* __restrict__ zg, const float* __restrict__ xc,
-                             double* __restrict__ z, SwParams prm, FastDiv dP3, FastDiv dP,
-                             int faces) {
-  const int N = prm.N, P = N + 1;
+                             double* __restrict__ z, SwParams prm, int faces) {
+  constexpr int N = P - 1, P3 = P * P * P;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nL;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t qq = (uint32_t)q;
-    const uint32_t e = dP3.div(qq);
-    const uint32_t lq = qq - e * dP3.d;
-    const uint32_t r1 = dP.div(lq);
-    const int i = (int)(lq - r1 * (uint32_t)P);
-    const uint32_t k = dP.div(r1);
-    const int j = (int)(r1 - k * (uint32_t)P);
+    const uint32_t e = (uint32_t)q / (uint32_t)P3;    // n_L < 2^31
+    const int lq = (int)((uint32_t)q - e * (uint32_t)P3);
+    const int i = lq % P, j = (lq / P) % P, k = lq / (P * P);
     const uint32_t re = prm.dnx.div(e);
     const int ex = (int)(e - re * (uint32_t)prm.nelx);
     const uint32_t ezu = prm.dny.div(re);
     const int ey = (int)(re - ezu * (uint32_t)prm.nely), ez = (int)ezu;
-    const int ix = ex * N + i, iy = ey * N + j, iz = ez * N + (int)k;
+    const int ix = ex * N + i, iy = ey * N + j, iz = ez * N + k;
     const bool masked = ((faces & SEM_FACE_XMIN) && ix == 0) ||
                         ((faces & SEM_FACE_XMAX) && ix == prm.gx - 1) ||
                         ((faces & SEM_FACE_YMIN) && iy == 0) ||
@@ -456,16 +449,16 @@ __global__ void k_sw_combine(int64_t nL, const float* __restrict__ zg, const flo
     if (!masked) {
       v = (double)zg[(long long)ix + (long long)prm.gx * iy + prm.sk * iz];
       if (xc) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int vv = 0; vv < 8; ++vv) {
-          const long long vi = (long long)(ex + (vv & 1)) +
-                               (long long)(prm.nelx + 1) *
-                                   ((ey + ((vv >> 1) & 1)) + (long long)(prm.nely + 1) * (ez + (vv >> 2)));
-          acc = fmaf(prm.phi[vv & 1][i] * prm.phi[(vv >> 1) & 1][j] * prm.phi[vv >> 2][k], xc[vi],
-                     acc);
-        }
-        v += (double)acc;
+        const int v0 = ex + (prm.nelx + 1) * (ey + (prm.nely + 1) * ez);
+        const int sy = prm.nelx + 1, sz = (prm.nelx + 1) * (prm.nely + 1);
+        const float fx0 = prm.phi[0][i], fx1 = prm.phi[1][i];
+        const float fy0 = prm.phi[0][j], fy1 = prm.phi[1][j];
+        const float fz0 = prm.phi[0][k], fz1 = prm.phi[1][k];
+        const float c00 = fmaf(fx1, xc[v0 + 1], fx0 * xc[v0]);
+        const float c10 = fmaf(fx1, xc[v0 + sy + 1], fx0 * xc[v0 + sy]);
+        const float c01 = fmaf(fx1, xc[v0 + sz + 1], fx0 * xc[v0 + sz]);
+        const float c11 = fmaf(fx1, xc[v0 + sz + sy + 1], fx0 * xc[v0 + sz + sy]);
+        v += (double)fmaf(fz1, fmaf(fy1, c11, fy0 * c01), fz0 * fmaf(fy1, c10, fy0 * c00));
       }
     }
     z[q] = v;
@@ -627,9 +620,20 @@ void schwarz_apply(sem_schwarz* sw, const double* r, double* z, cudaStream_t s) 
       vcg_pupd(sw->nv4, sw->pc.ptr, sw->rc.ptr, sw->cdinv.ptr, st, s);
     }
   }
-  k_sw_combine<<<ew_blocks(h->nL), 256, 0, s>>>(h->nL, sw->zg.ptr, coarse ? sw->xc.ptr : nullptr,
-                                                z, sw->prm, FastDiv((uint32_t)h->P3),
-                                                FastDiv((uint32_t)h->P), h->faces);
+  const float* xcp = coarse ? sw->xc.ptr : nullptr;
+  const int cg = ew_blocks(h->nL);
+  switch (h->P) {
+    case 3: k_sw_combine<3><<<cg, 256, 0, s>>>(h->nL, sw->zg.ptr, xcp, z, sw->prm, h->faces); break;
+    case 4: k_sw_combine<4><<<cg, 256, 0, s>>>(h->nL, sw->zg.ptr, xcp, z, sw->prm, h->faces); break;
+    case 5: k_sw_combine<5><<<cg, 256, 0, s>>>(h->nL, sw->zg.ptr, xcp, z, sw->prm, h->faces); break;
+    case 6: k_sw_combine<6><<<cg, 256, 0, s>>>(h->nL, sw->zg.ptr, xcp, z, sw->prm, h->faces); break;
+    case 7: k_sw_combine<7><<<cg, 256, 0, s>>>(h->nL, sw->zg.ptr, xcp, z, sw->prm, h->faces); break;
+    case 8: k_sw_combine<8><<<cg, 256, 0, s>>>(h->nL, sw->zg.ptr, xcp, z, sw->prm, h->faces); break;
+    case 9: k_sw_combine<9><<<cg, 256, 0, s>>>(h->nL, sw->zg.ptr, xcp, z, sw->prm, h->faces); break;
+    case 10: k_sw_combine<10><<<cg, 256, 0, s>>>(h->nL, sw->zg.ptr, xcp, z, sw->prm, h->faces); break;
+    case 11: k_sw_combine<11><<<cg, 256, 0, s>>>(h->nL, sw->zg.ptr, xcp, z, sw->prm, h->faces); break;
+    default: throw Error(SEM_ERR_ARG, "schwarz: unsupported order");
+  }
   SEM_CHECK_LAUNCH();
 }
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <string>
 #include <vector>
+#include <memory>
 #include <algorithm>
 #include <cmath>
 #include <stdexcept>
@@ -13,6 +14,8 @@
 #include "../../include/sem.h"
 
 namespace sem {
+
+struct GmresWork;                    // gmres.cu
 
 constexpr int kMaxN = 10;            // highest supported polynomial order
 constexpr int kMaxP = kMaxN + 1;
@@ -178,6 +181,7 @@ struct sem_handle {
   sem::DevBuf<sem::CGState> state;          // [3]: outer/FP64, inner/FP32, sem_dot ticket
   // host staging for sem_apply_host
   sem::DevBuf<double> stage_in, stage_out;
+  std::shared_ptr<sem::GmresWork> gmres;    // GMRES workspace, kept between solves
   double dinv_h1 = NAN, dinv_h2 = NAN;
   const void* dinv_h1f = nullptr;
   int dinv_valid = 0;
