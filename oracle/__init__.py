@@ -27,6 +27,7 @@ computational fluid dynamics", arXiv 2107.01243) by eye:
                    fast-diagonalisation local solves on grown elements and a
                    trilinear coarse level solved by a few CG iterations (§4)
 * ``gmres``     -- flexible GMRES(m) with right preconditioning (§4, Table 2)
+* ``pipecg``    -- pipelined PCG, one reduction per iteration (§10 outlook)
 * ``dense``     -- brute-force dense element matrices and assembly for tiny
                    meshes, from explicit basis gradients (§2, Eq. 3 and Eq. 9)
 
