@@ -468,10 +468,15 @@ def run_solves(sem, torch, dev):
     # mixed: FP32 inner PCG on global (unique-dof) vectors; mixed_local_inner:
     # the same solve with the inner PCG on L-vectors (assembled operator with
     # gather-scatter passes)
-    for name, prec, inner in (("fp64", sem.SEM_SOLVE_F64, sem.SEM_INNER_AUTO),
-                              ("mixed", sem.SEM_SOLVE_MIXED, sem.SEM_INNER_GLOBAL),
-                              ("mixed_local_inner", sem.SEM_SOLVE_MIXED, sem.SEM_INNER_LOCAL)):
+    # fp64_pipelined: the FP64 solve with the pipelined recurrences (one
+    # reduction per iteration; more vector traffic, fewer kernels)
+    for name, prec, inner, var in (
+            ("fp64", sem.SEM_SOLVE_F64, sem.SEM_INNER_AUTO, sem.SEM_CG_STANDARD),
+            ("fp64_pipelined", sem.SEM_SOLVE_F64, sem.SEM_INNER_AUTO, sem.SEM_CG_PIPELINED),
+            ("mixed", sem.SEM_SOLVE_MIXED, sem.SEM_INNER_GLOBAL, sem.SEM_CG_STANDARD),
+            ("mixed_local_inner", sem.SEM_SOLVE_MIXED, sem.SEM_INNER_LOCAL, sem.SEM_CG_STANDARD)):
         sem.sem_set_inner_vectors(h, inner)
+        sem.sem_set_cg_variant(h, var)
         x = torch.empty_like(b)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -74,6 +74,11 @@ enum { SEM_INNER_AUTO = 0,      /* global where supported (constant h1, odd N), 
        SEM_INNER_GLOBAL = 2     /* unique-dof vectors, element kernels assemble by atomics */
 };
 
+/* CG recurrences of SEM_SOLVE_F64 (sem_set_cg_variant) */
+enum { SEM_CG_STANDARD = 0,     /* Jacobi-PCG, three kernels after the operator */
+       SEM_CG_PIPELINED = 1     /* pipelined PCG: one reduction, one vector pass */
+};
+
 /* levels of the Schwarz preconditioner (sem_schwarz_create) */
 enum { SEM_SCHWARZ_LOCAL = 1,   /* overlapping element subdomains, fast diagonalisation */
        SEM_SCHWARZ_COARSE = 2,  /* trilinear coarse level, fixed-count CG */
@@ -262,6 +267,20 @@ sem_status sem_apply_global(sem_handle* h, const void* u_g, void* w_g, double h1
  * sem_apply leave it).  Needs n_L < 2^31.  Asynchronous on stream.
  */
 sem_status sem_to_global(sem_handle* h, const void* in_L, void* out_g, int dtype, void* stream);
+
+/*
+ * sem_set_cg_variant -- choose the recurrences of the FP64 solves
+ * (SEM_SOLVE_F64) of sem_cg_solve.  SEM_CG_PIPELINED is the pipelined PCG of
+ * Ghysels and Vanroose (the non-blocking Krylov method the paper's outlook
+ * names, §10): both inner products of an iteration come from one reduction
+ * that is independent of the operator, and all vectors (x, r, u = M r,
+ * w = H u, and the z, q, s, p recurrences) are updated in one pass; in exact
+ * arithmetic its iterates are those of standard PCG.  When its recurrence
+ * residual reaches tol, the true residual is checked and the recurrences
+ * restart from it (up to 6 cycles; info.outer_iters counts them).  Needs six
+ * more FP64 L-vectors, kept on the handle.
+ */
+sem_status sem_set_cg_variant(sem_handle* h, int kind);
 
 /*
  * sem_set_inner_vectors -- choose the vectors of the FP32 inner PCG of

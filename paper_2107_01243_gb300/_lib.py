@@ -26,6 +26,7 @@ SEM_DSSUM_BOX, SEM_DSSUM_SEGMENTS = 0, 1
 SEM_APPLY_LOCAL, SEM_APPLY_FINISH, SEM_APPLY_FULL = 1, 2, 3
 SEM_INNER_AUTO, SEM_INNER_LOCAL, SEM_INNER_GLOBAL = 0, 1, 2
 SEM_SCHWARZ_LOCAL, SEM_SCHWARZ_COARSE, SEM_SCHWARZ_BOTH = 1, 2, 3
+SEM_CG_STANDARD, SEM_CG_PIPELINED = 0, 1
 (SEM_FIELD_X, SEM_FIELD_Y, SEM_FIELD_Z, SEM_FIELD_G, SEM_FIELD_B, SEM_FIELD_MULT,
  SEM_FIELD_MASK, SEM_FIELD_GID, SEM_FIELD_DINV) = range(9)
 
@@ -107,6 +108,7 @@ SIGNATURES = {
                                         ctypes.c_int, _P]),
     "sem_to_global": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "sem_set_inner_vectors": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sem_set_cg_variant": (ctypes.c_int, [_P, ctypes.c_int]),
     "sem_schwarz_create": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, _P, ctypes.POINTER(ctypes.c_void_p)]),
     "sem_schwarz_apply": (ctypes.c_int, [_P, _P, _P, _P]),

@@ -157,6 +157,11 @@ def sem_to_global(h, u, out_g, stream=None):
     return out_g
 
 
+def sem_set_cg_variant(h, kind):
+    """Recurrences of the FP64 CG solves: SEM_CG_STANDARD or SEM_CG_PIPELINED."""
+    check(_lib.load().sem_set_cg_variant(h.ptr, int(kind)))
+
+
 def sem_set_inner_vectors(h, kind):
     """Vectors of the FP32 inner solves: SEM_INNER_AUTO, SEM_INNER_LOCAL or SEM_INNER_GLOBAL."""
     check(_lib.load().sem_set_inner_vectors(h.ptr, int(kind)))

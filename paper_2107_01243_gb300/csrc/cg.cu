@@ -457,6 +457,130 @@ __global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict
     b[q] = (float)a[q];
 }
 
+// ---- pipelined PCG (Ghysels and Vanroose): one reduction per iteration, all
+// vectors updated by recurrences in one pass after the operator.
+// Start of a cycle (r holds the residual): u = dinv r, z = q = s = p = 0.
+__global__ void k_pipe_start(int64_t n, const double* __restrict__ r, const double* __restrict__ dinv,
+                             double* __restrict__ u, double* __restrict__ z, double* __restrict__ q,
+                             double* __restrict__ s, double* __restrict__ p) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    u[i] = dinv[i] * r[i];
+    z[i] = 0.0;
+    q[i] = 0.0;
+    s[i] = 0.0;
+    p[i] = 0.0;
+  }
+}
+
+// After w = H u: m = dinv w; gamma = <r, u>, delta = <w, u>, <r, r>;
+// alpha = gamma / delta, beta = 0.
+__global__ void __launch_bounds__(kRedThreads)
+k_pipe_first(int64_t n, const double* __restrict__ r, const double* __restrict__ u,
+             const double* __restrict__ w, const double* __restrict__ dinv,
+             const float* __restrict__ imult, double* __restrict__ m, CGState* __restrict__ st,
+             double* __restrict__ partials, double tol, int maxit, int iter0) {
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = r[i], ui = u[i], wi = w[i], im = (double)imult[i];
+    m[i] = dinv[i] * wi;
+    v[0] = fma(ri * ui, im, v[0]);
+    v[1] = fma(wi * ui, im, v[1]);
+    v[2] = fma(ri * ri, im, v[2]);
+  }
+  double tot[3];
+  if (grid_sum<3>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    st->rz = tot[0];
+    st->pw = tot[1];
+    st->rr = tot[2];
+    st->tol2 = tol * tol * st->bb;
+    st->iter = iter0;
+    st->maxit = maxit;
+    st->status = SEM_OK;
+    st->beta = 0.0;
+    st->done = 0;
+    if (!(tot[2] == tot[2])) {
+      st->status = SEM_ERR_BREAKDOWN;
+      st->done = 1;
+    } else if (tot[2] <= st->tol2 || st->bb == 0.0) {
+      st->done = 1;
+    } else if (iter0 >= maxit) {
+      st->status = SEM_ERR_NOCONV;
+      st->done = 1;
+    } else if (!(tot[1] > 0.0)) {
+      st->status = SEM_ERR_BREAKDOWN;
+      st->done = 1;
+    } else {
+      st->alpha = tot[0] / tot[1];
+    }
+  }
+}
+
+// One iteration after nv = H m (alpha, beta from the state); then the dots of
+// the new vectors and alpha, beta of the next iteration.
+__global__ void __launch_bounds__(kRedThreads)
+k_pipe_update(int64_t n, double* __restrict__ x, double* __restrict__ r, double* __restrict__ u,
+              double* __restrict__ w, double* __restrict__ z, double* __restrict__ q,
+              double* __restrict__ s, double* __restrict__ p, double* __restrict__ m,
+              const double* __restrict__ nv, const double* __restrict__ dinv,
+              const float* __restrict__ imult, CGState* __restrict__ st,
+              double* __restrict__ partials) {
+  if (st->done) return;
+  const double alpha = st->alpha, beta = st->beta;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = fma(beta, z[i], nv[i]);
+    const double qi = fma(beta, q[i], m[i]);
+    const double wi0 = w[i], ui0 = u[i];
+    const double si = fma(beta, s[i], wi0);
+    const double pi = fma(beta, p[i], ui0);
+    z[i] = zi;
+    q[i] = qi;
+    s[i] = si;
+    p[i] = pi;
+    x[i] = fma(alpha, pi, x[i]);
+    const double ri = fma(-alpha, si, r[i]);
+    const double ui = fma(-alpha, qi, ui0);
+    const double wi = fma(-alpha, zi, wi0);
+    r[i] = ri;
+    u[i] = ui;
+    w[i] = wi;
+    m[i] = dinv[i] * wi;
+    const double im = (double)imult[i];
+    v[0] = fma(ri * ui, im, v[0]);
+    v[1] = fma(wi * ui, im, v[1]);
+    v[2] = fma(ri * ri, im, v[2]);
+  }
+  double tot[3];
+  if (grid_sum<3>(v, partials, &st->counter, tot) && threadIdx.x == 0) {
+    st->iter += 1;
+    st->rr = tot[2];
+    if (!(tot[0] == tot[0]) || !(tot[1] == tot[1]) || !(tot[2] == tot[2])) {
+      st->status = SEM_ERR_BREAKDOWN;
+      st->done = 1;
+    } else if (tot[2] <= st->tol2) {
+      st->done = 1;
+    } else if (st->iter >= st->maxit) {
+      st->status = SEM_ERR_NOCONV;
+      st->done = 1;
+    } else {
+      const double b2 = tot[0] / st->rz;
+      const double den = tot[1] - b2 * tot[0] / st->alpha;
+      if (!(den > 0.0)) {
+        st->status = SEM_ERR_BREAKDOWN;
+        st->done = 1;
+      } else {
+        st->beta = b2;
+        st->alpha = tot[0] / den;
+        st->rz = tot[0];
+        st->pw = tot[1];
+      }
+    }
+  }
+}
+
 static int ew_grid(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * kNumSMs));
 }
@@ -703,6 +827,61 @@ static void solve_fp64(sem_handle* h, const double* b, double* x, const sem_solv
   info.status = fin.status;
 }
 
+// Pipelined PCG in FP64 (SEM_CG_PIPELINED): cycles of recurrences checked
+// against the true residual when the recurrence residual converges.
+static void solve_pipelined(sem_handle* h, const double* b, double* x, const sem_solve_opts& o,
+                            sem_solve_info& info, cudaStream_t s) {
+  const int64_t n = h->nL;
+  ensure(h->r, n); ensure(h->p, n); ensure(h->w, n);
+  for (DevBuf<double>* v : {&h->pipe_u, &h->pipe_z, &h->pipe_q, &h->pipe_s, &h->pipe_m,
+                            &h->pipe_n})
+    ensure(*v, n);
+  ensure_dinv(h, o.h1, o.h2, o.h1_field, false, s);
+  CGState* st = h->state.ptr;
+  k_norm_bb<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, h->imult.ptr, st, h->partials.ptr);
+  SEM_CHECK_LAUNCH();
+  if (o.x0_is_zero) SEM_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  const double* dinv = h->f64.dinv.ptr;
+  int iters = 0, cycles = 0, status = SEM_ERR_NOCONV;
+  double rel = 0.0;
+  constexpr int kMaxCycles = 6;
+  for (;;) {
+    residual64(h, b, x, o.h1, o.h2, o.h1_field, nullptr, st, s);   // r = b - H x
+    const CGState hs = read_state(st, s, h->dev_err.ptr);
+    rel = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+    if (!(rel == rel)) { status = SEM_ERR_BREAKDOWN; break; }
+    if (rel <= o.tol) { status = SEM_OK; break; }
+    if (iters >= o.maxit || cycles >= kMaxCycles) { status = SEM_ERR_NOCONV; break; }
+    ++cycles;
+    k_pipe_start<<<ew_grid(n), 256, 0, s>>>(n, h->r.ptr, dinv, h->pipe_u.ptr, h->pipe_z.ptr,
+                                           h->pipe_q.ptr, h->pipe_s.ptr, h->p.ptr);
+    SEM_CHECK_LAUNCH();
+    launch_apply<double>(h, h->f64, h->pipe_u.ptr, h->w.ptr, o.h1, o.h2, o.h1_field, nullptr,
+                         SEM_APPLY_FULL, s);
+    k_pipe_first<<<kRedBlocks, kRedThreads, 0, s>>>(n, h->r.ptr, h->pipe_u.ptr, h->w.ptr, dinv,
+                                                   h->imult.ptr, h->pipe_m.ptr, st,
+                                                   h->partials.ptr, o.tol, o.maxit, iters);
+    SEM_CHECK_LAUNCH();
+    const CGState fin = run_pcg_loop(h, st, o, s, [&](int count) {
+      for (int c = 0; c < count; ++c) {
+        launch_apply<double>(h, h->f64, h->pipe_m.ptr, h->pipe_n.ptr, o.h1, o.h2, o.h1_field, st,
+                             SEM_APPLY_FULL, s);
+        k_pipe_update<<<kRedBlocks, kRedThreads, 0, s>>>(
+            n, x, h->r.ptr, h->pipe_u.ptr, h->w.ptr, h->pipe_z.ptr, h->pipe_q.ptr,
+            h->pipe_s.ptr, h->p.ptr, h->pipe_m.ptr, h->pipe_n.ptr, dinv, h->imult.ptr, st,
+            h->partials.ptr);
+        SEM_CHECK_LAUNCH();
+      }
+    });
+    iters = fin.iter;
+    if (fin.status == SEM_ERR_BREAKDOWN) { status = SEM_ERR_BREAKDOWN; break; }
+  }
+  info.iters = iters;
+  info.outer_iters = cycles;
+  info.rel_res = rel;
+  info.status = status;
+}
+
 // Relative tolerance of the next inner FP32 solve when the outer relative
 // residual is rel: inner_tol (the reduction FP32 can be trusted with), or,
 // once less is needed, the reduction that reaches the outer tolerance with a
@@ -889,7 +1068,9 @@ extern "C" sem_status sem_cg_solve(sem_handle* h, const double* b_L, double* x_L
     SEM_REQUIRE(o.precision == SEM_SOLVE_F64 || (o.inner_tol > 0.0 && o.inner_tol < 1.0),
                 "sem_cg_solve: inner_tol must be in (0, 1)");
     StreamScope sc((cudaStream_t)o.stream);
-    if (o.precision == SEM_SOLVE_F64) solve_fp64(h, b_L, x_L, o, local, sc.own);
+    if (o.precision == SEM_SOLVE_F64 && h->cg_variant == SEM_CG_PIPELINED)
+      solve_pipelined(h, b_L, x_L, o, local, sc.own);
+    else if (o.precision == SEM_SOLVE_F64) solve_fp64(h, b_L, x_L, o, local, sc.own);
     else solve_mixed(h, b_L, x_L, o, local, sc.own);
   });
   if (info) *info = local;
@@ -903,6 +1084,15 @@ extern "C" sem_status sem_cg_solve(sem_handle* h, const double* b_L, double* x_L
     return (sem_status)local.status;
   }
   return SEM_OK;
+}
+
+extern "C" sem_status sem_set_cg_variant(sem_handle* h, int kind) {
+  return guarded([&] {
+    SEM_REQUIRE(h, "sem_set_cg_variant: null handle");
+    SEM_REQUIRE(kind == SEM_CG_STANDARD || kind == SEM_CG_PIPELINED,
+                "sem_set_cg_variant: unknown kind");
+    h->cg_variant = kind;
+  });
 }
 
 extern "C" sem_status sem_set_inner_vectors(sem_handle* h, int kind) {

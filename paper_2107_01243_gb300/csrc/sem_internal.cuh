@@ -177,6 +177,8 @@ struct sem_handle {
   // multiple of 4): residual, direction, H p, correction, Jacobi diagonal
   sem::DevBuf<float> rg, pg, wg, xg, dinvg;
   int inner_vectors = SEM_INNER_AUTO;       // sem_set_inner_vectors
+  int cg_variant = SEM_CG_STANDARD;         // sem_set_cg_variant
+  sem::DevBuf<double> pipe_u, pipe_z, pipe_q, pipe_s, pipe_m, pipe_n;   // pipelined CG
   sem::DevBuf<double> partials;             // reduction partials: [0,2B) solves, [2B,3B) sem_dot
   sem::DevBuf<sem::CGState> state;          // [3]: outer/FP64, inner/FP32, sem_dot ticket
   // host staging for sem_apply_host
