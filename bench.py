@@ -10,7 +10,8 @@ kernel, the end-to-end rate through the host-buffer C-ABI call and the
 oracle timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--no-solve]
+                  [--no-solve] [--no-batch] [--no-cpu] [--sections a,b,...]
+                  [--pressure-nel NEL] [--tiles SPEC] [--model-sweep]
 """
 import argparse
 import json
@@ -200,6 +201,12 @@ def main():
     ap.add_argument("--model-sweep", action="store_true",
                     help="print the Eq. 12-13 cost model against measured kernel times for "
                          "N = 2..9 instead of the benchmark line")
+    ap.add_argument("--sections", default="solve,batch,manufactured,projection,pressure,adjoint",
+                    help="comma list of the solver sections to run after the operator line "
+                         "(--no-solve and --no-batch remove theirs)")
+    ap.add_argument("--pressure-nel", type=int, default=48,
+                    help="elements per direction of the pressure-solver section (48: the "
+                         "solve mesh; smaller for profiling)")
     ap.add_argument("--tiles", default=None,
                     help="pin the Ax tiles instead of autotuning: "
                          "<bulk-copy|global-load>:<fp32 stages>:<fp32 elements per CTA>:<fp64 stages>")
@@ -375,14 +382,22 @@ def main():
     del w, w32, u32, ug32, wg32
     sem.sem_destroy(h)
 
-    if not args.no_solve:
+    sections = set(args.sections.split(","))
+    if args.no_solve:
+        sections -= {"solve", "manufactured", "projection", "pressure", "adjoint"}
+    if args.no_batch:
+        sections.discard("batch")
+    if "solve" in sections:
         line["solve"] = run_solves(sem, torch, dev)
-    if not args.no_batch:
+    if "batch" in sections:
         line["batch"] = run_batch(sem, torch, dev)
-    if not args.no_solve:
+    if "manufactured" in sections:
         line["manufactured"] = run_manufactured(sem, torch, dev)
+    if "projection" in sections:
         line["projection"] = run_projection(sem, torch, dev)
-        line["pressure"] = run_pressure(sem, torch, dev)
+    if "pressure" in sections:
+        line["pressure"] = run_pressure(sem, torch, dev, nel=args.pressure_nel)
+    if "adjoint" in sections:
         line["adjoint"] = run_adjoint(sem, torch, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -499,7 +514,7 @@ def _coords(sem, torch, h, dev):
     return [t.cpu().numpy() for t in xs]
 
 
-def run_pressure(sem, torch, dev, restart=10):
+def run_pressure(sem, torch, dev, restart=10, nel=48):
     """Neko's pressure-solver path (§4, Table 2) on the 48^3 solve mesh: flexible
     GMRES(10) preconditioned by the two-level Schwarz method (10 coarse CG
     iterations), FP64 to 1e-8 (Jacobi-PCG on the same problem is the "solve"
@@ -508,7 +523,7 @@ def run_pressure(sem, torch, dev, restart=10):
     on the restart length (38 at 10, 37 at 30), while the Gram-Schmidt work
     grows with it (0.31 s at 10, 0.43 s at 30)."""
     cfg = SOLVE
-    h = sem.sem_setup(cfg["nel"], cfg["N"], length=cfg["length"], deform=cfg["deform"])
+    h = sem.sem_setup((nel,) * 3, cfg["N"], length=cfg["length"], deform=cfg["deform"])
     X, Y, Z = _coords(sem, torch, h, dev)
     f = torch.from_numpy(si.eval_fourier(si.fourier_modes(cfg["seed"]), X, Y, Z)).to(dev)
     del X, Y, Z
@@ -520,7 +535,7 @@ def run_pressure(sem, torch, dev, restart=10):
     pre = sem.sem_schwarz_create(h, 1.0, 0.0, coarse_iters=10)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
-    out = {"workload": "Poisson, 48^3 deformed hex elements, N=7, 8 Fourier-mode RHS, "
+    out = {"workload": f"Poisson, {nel}^3 deformed hex elements, N=7, 8 Fourier-mode RHS, "
                        "FP64 to 1e-8", "restart": restart, "schwarz_setup_seconds": t_setup}
     for name, prec in (("gmres_schwarz", pre),):
         x = torch.empty_like(b)
