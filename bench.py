@@ -391,6 +391,8 @@ def main():
         line["solve"] = run_solves(sem, torch, dev)
     if "batch" in sections:
         line["batch"] = run_batch(sem, torch, dev)
+        # small problems, where one launch per stage for all problems pays most
+        line["batch"]["small_problems"] = run_batch(sem, torch, dev, n_problems=16, e_hi=4096)
     if "manufactured" in sections:
         line["manufactured"] = run_manufactured(sem, torch, dev)
     if "projection" in sections:
@@ -414,11 +416,11 @@ def main():
     return 0
 
 
-def run_batch(sem, torch, dev, n_problems=64):
+def run_batch(sem, torch, dev, n_problems=64, e_hi=32768):
     """64 independent deformed-box Helmholtz problems (E in [512, 32768], N in
     {5,7,9}, h2 = lambda in [0.1, 10]): one batched solve against the same
     problems solved one after another, FP32 inner / FP64 refinement to 1e-8."""
-    probs = si.batch_problems(n_problems)
+    probs = si.batch_problems(n_problems, e_hi=e_hi)
     hs, bs = [], []
     for q in probs:
         h = sem.sem_setup(q["nel"], q["N"], length=(si.TWO_PI,) * 3, deform=0.1,
@@ -450,7 +452,7 @@ def run_batch(sem, torch, dev, n_problems=64):
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
     work = sum(n * i["iters"] for n, i in zip(npts, infos))
-    out = {"workload": f"{len(hs)} Helmholtz problems, E in [512, 32768], N in {{5,7,9}}, "
+    out = {"workload": f"{len(hs)} Helmholtz problems, E in [512, {e_hi}], N in {{5,7,9}}, "
                        "h2 in [0.1, 10], deformed boxes, tol 1e-8, FP32 inner / FP64 refine",
            "local_points": int(sum(npts)),
            "batched_seconds": tb, "sequential_seconds": ts, "speedup": ts / tb,

@@ -34,6 +34,7 @@ namespace sem {
 
 constexpr int kMaxBatch = 256;
 constexpr int kChunk = 65536;          // points per vector work item
+constexpr int kGChunk = 16384;         // values per global-vector work item
 
 // batched Ax tile per order: K elements of P^2 threads each per work item
 template <int P>
@@ -83,6 +84,14 @@ struct BProb {
   unsigned nSX, nSY, nSZ, nmf;
   const int* mfree;
   FastDiv dN, dN1, dgy, dnx1, dny1, dnix, dniy;
+  // inner solve on global vectors (n_G padded to nGp, items of kChunk values)
+  float *xg, *rg, *pg, *wg;
+  const float* dinvg;
+  long long nGp;
+  int g_off, g_cnt;
+  FastDiv dnx, dny;
+  double* pwacc;         // <p, H p> accumulated by the element kernel (fused_pw)
+  int fused_pw;          // P = 8: the element kernel forms <p, H p>
 };
 
 __device__ __forceinline__ int find_prob(const long long* off, int n, long long g) {
@@ -535,6 +544,8 @@ bpupd_kernel(const BProb* __restrict__ probs, const int* __restrict__ item_prob,
 
 }  // namespace sem
 
+#include "batch_glob.cuh"
+
 using namespace sem;
 
 struct sem_batch {
@@ -561,6 +572,15 @@ struct sem_batch {
   DevBuf<long long> cls_soff[kMaxP + 1], cut_off[kMaxP + 1], sy_off[kMaxP + 1],
       sz_off[kMaxP + 1];
   int bapply_grid[kMaxP + 1] = {};
+  // inner solves on global vectors (every handle allows it): per class the
+  // element offsets of its problems, the global vector items
+  bool glob = false;
+  DevBuf<long long> cls_eoff[kMaxP + 1];
+  long long Ecls[kMaxP + 1] = {};
+  int bglob_grid[kMaxP + 1] = {};
+  DevBuf<int> gitem_prob;
+  DevBuf<double> pwacc;                  // per problem
+  int ngitems = 0;
   int nitems = 0, maxP = 0;
   cudaStream_t stream = nullptr;
 };
@@ -609,6 +629,27 @@ static int bapply_occupancy(int ncls) {
   return occ;
 }
 
+template <int P>
+static int bglob_occupancy(int ncls) {
+  using C = BGlobCfg<P>;
+  auto kern = bglob_kernel<P>;
+  SEM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)C::smem(kMaxBatch)));
+  int occ = 0;
+  SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::THREADS,
+                                                         C::smem(ncls)));
+  return occ;
+}
+
+template <int P>
+static void launch_bglob(sem_batch* bt, cudaStream_t s) {
+  using C = BGlobCfg<P>;
+  bglob_kernel<P><<<bt->bglob_grid[P], C::THREADS, C::smem(bt->ncls[P]), s>>>(
+      bt->probs.ptr, bt->cls_prob[P].ptr, bt->cls_eoff[P].ptr, bt->ncls[P], bt->Ecls[P],
+      bt->hs[0]->dev_err.ptr, kWaitTimeoutNs);
+  SEM_CHECK_LAUNCH();
+}
+
 static int pass_blocks(long long total) {
   return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 16LL * kNumSMs));
 }
@@ -645,6 +686,28 @@ static void launch_bfinish(sem_batch* bt, cudaStream_t s) {
 // one inner iteration over the batch (captured into a graph)
 static void batch_iteration(sem_batch* bt, cudaStream_t s) {
   const int n = (int)bt->hs.size();
+  if (bt->glob) {
+    for (int P = 2; P <= kMaxP; P += 2) {
+      if (!bt->ncls[P]) continue;
+      switch (P) {
+        case 2: launch_bglob<2>(bt, s); break;
+        case 4: launch_bglob<4>(bt, s); break;
+        case 6: launch_bglob<6>(bt, s); break;
+        case 8: launch_bglob<8>(bt, s); break;
+        default: launch_bglob<10>(bt, s); break;
+      }
+    }
+    const int gblocks = std::min(bt->ngitems, 8 * kNumSMs);
+    bgpw_kernel<<<gblocks, 256, 0, s>>>(bt->probs.ptr, bt->gitem_prob.ptr, n, bt->ngitems,
+                                        bt->partials.ptr, bt->tickets.ptr);
+    SEM_CHECK_LAUNCH();
+    bgupdate_kernel<<<gblocks, 256, 0, s>>>(bt->probs.ptr, bt->gitem_prob.ptr, n, bt->ngitems,
+                                            bt->partials.ptr, bt->tickets.ptr);
+    SEM_CHECK_LAUNCH();
+    bgpupd_kernel<<<gblocks, 256, 0, s>>>(bt->probs.ptr, bt->gitem_prob.ptr, n, bt->ngitems);
+    SEM_CHECK_LAUNCH();
+    return;
+  }
   if (bt->fused) {
     for (int P = 6; P <= kMaxP; P += 2) {
       if (!bt->ncls[P]) continue;
@@ -813,11 +876,55 @@ extern "C" sem_status sem_batch_create(sem_handle* const* handles, int n, sem_ba
                     : P == 8 ? bapply_occupancy<8>(ncl) : bapply_occupancy<10>(ncl);
       bt->bapply_grid[P] = (int)std::min<long long>(S, (long long)std::max(1, occ) * nsm);
     }
+    // global-vector inner solves when every handle allows them
+    bt->glob = true;
+    for (int p = 0; p < n; ++p)
+      bt->glob = bt->glob && handles[p]->inner_vectors != SEM_INNER_LOCAL &&
+                 glob_supported(handles[p]);
+    if (bt->glob) {
+      std::vector<int> gitem_prob;
+      int goff = 0;
+      for (int p = 0; p < n; ++p) {
+        BProb& b = bt->hp[p];
+        b.nGp = glob_padded(handles[p]);
+        b.g_off = goff;
+        b.g_cnt = (int)((b.nGp + kGChunk - 1) / kGChunk);
+        for (int q = 0; q < b.g_cnt; ++q) gitem_prob.push_back(p);
+        goff += b.g_cnt;
+        b.dnx = FastDiv((uint32_t)b.nelx);
+        b.dny = FastDiv((uint32_t)b.nely);
+        b.fused_pw = (b.P * b.P) % 32 == 0 ? 1 : 0;
+      }
+      bt->pwacc.alloc(n);
+      SEM_CUDA(cudaMemset(bt->pwacc.ptr, 0, n * sizeof(double)));
+      for (int p = 0; p < n; ++p) bt->hp[p].pwacc = bt->pwacc.ptr + p;
+      bt->ngitems = goff;
+      bt->gitem_prob.alloc(gitem_prob.size());
+      bt->gitem_prob.upload(gitem_prob.data(), gitem_prob.size(), nullptr);
+      for (int P = 2; P <= kMaxP; P += 2) {
+        if (!bt->ncls[P]) continue;
+        std::vector<long long> eoff;
+        long long Ec = 0;
+        for (int p = 0; p < n; ++p)
+          if (bt->hp[p].P == P) {
+            eoff.push_back(Ec);
+            Ec += bt->hp[p].E;
+          }
+        bt->Ecls[P] = Ec;
+        bt->cls_eoff[P].alloc(eoff.size());
+        bt->cls_eoff[P].upload(eoff.data(), eoff.size(), nullptr);
+        const int ncl = bt->ncls[P];
+        const int occ = P == 2 ? bglob_occupancy<2>(ncl) : P == 4 ? bglob_occupancy<4>(ncl)
+                      : P == 6 ? bglob_occupancy<6>(ncl) : P == 8 ? bglob_occupancy<8>(ncl)
+                      : bglob_occupancy<10>(ncl);
+        bt->bglob_grid[P] = (int)std::min<long long>(Ec, (long long)std::max(1, occ) * nsm);
+      }
+    }
     bt->d_off.alloc(n);
     bt->d_off.upload(d_off.data(), n, nullptr);
     bt->item_prob.alloc(item_prob.size());
     bt->item_prob.upload(item_prob.data(), item_prob.size(), nullptr);
-    bt->partials.alloc(2 * (size_t)bt->nitems);
+    bt->partials.alloc(2 * (size_t)std::max(bt->nitems, bt->ngitems));
     bt->tickets.alloc(n);
     SEM_CUDA(cudaMemset(bt->tickets.ptr, 0, n * sizeof(unsigned)));
     bt->states.alloc(n);
@@ -867,6 +974,7 @@ extern "C" sem_status sem_batch_solve(sem_batch* bt, const double* const* b_L,
       po[p].h2 = h2[p];
       po[p].h1_field = nullptr;
       mixed_prepare(h, po[p], own);
+      if (bt->glob) glob_prepare(h, own);
       BProb& b = bt->hp[p];
       b.dinv = h->f32.dinv.ptr;
       b.x = h->x32.ptr;
@@ -876,6 +984,11 @@ extern "C" sem_status sem_batch_solve(sem_batch* bt, const double* const* b_L,
       b.h1 = (float)h1[p];
       b.h2 = (float)h2[p];
       b.st = bt->states.ptr + p;
+      b.xg = h->xg.ptr;
+      b.rg = h->rg.ptr;
+      b.pg = h->pg.ptr;
+      b.wg = h->wg.ptr;
+      b.dinvg = h->dinvg.ptr;
       if (o.x0_is_zero) SEM_CUDA(cudaMemsetAsync(x_L[p], 0, h->nL * sizeof(double), own));
       outer_norm_b(h, b_L[p], own);
     }
@@ -908,7 +1021,8 @@ extern "C" sem_status sem_batch_solve(sem_batch* bt, const double* const* b_L,
     // FP64 residual of problem p; starts its next inner solve unless it is finished
     auto refine = [&](int p) {
       sem_handle* h = bt->hs[p];
-      outer_residual(h, b_L[p], x_L[p], po[p], own);
+      if (bt->glob) outer_residual_global(h, b_L[p], x_L[p], po[p], own);
+      else outer_residual(h, b_L[p], x_L[p], po[p], own);
       const CGState hs0 = state_to_host(h->state.ptr, own, h->dev_err.ptr);
       rel[p] = hs0.bb > 0 ? std::sqrt(hs0.rr / hs0.bb) : 0.0;
       if (!(rel[p] == rel[p])) { status[p] = SEM_ERR_BREAKDOWN; phase[p] = FINISHED; }
@@ -923,10 +1037,17 @@ extern "C" sem_status sem_batch_solve(sem_batch* bt, const double* const* b_L,
         return;
       }
       const BProb& b = bt->hp[p];
-      binit_kernel<<<std::min(b.v_cnt, 4 * kNumSMs), 256, 0, own>>>(
-          bt->probs.ptr, bt->item_prob.ptr, b.v_off, b.v_cnt, bt->nitems, bt->partials.ptr,
-          bt->tickets.ptr, inner_target(o.inner_tol, o.tol, rel[p]),
-          std::max(1, o.maxit - iters[p]));
+      if (bt->glob) {
+        bginit_kernel<<<std::min(b.g_cnt, 4 * kNumSMs), 256, 0, own>>>(
+            bt->probs.ptr, bt->gitem_prob.ptr, b.g_off, b.g_cnt, bt->ngitems, bt->partials.ptr,
+            bt->tickets.ptr, inner_target(o.inner_tol, o.tol, rel[p]),
+            std::max(1, o.maxit - iters[p]));
+      } else {
+        binit_kernel<<<std::min(b.v_cnt, 4 * kNumSMs), 256, 0, own>>>(
+            bt->probs.ptr, bt->item_prob.ptr, b.v_off, b.v_cnt, bt->nitems, bt->partials.ptr,
+            bt->tickets.ptr, inner_target(o.inner_tol, o.tol, rel[p]),
+            std::max(1, o.maxit - iters[p]));
+      }
       SEM_CHECK_LAUNCH();
     };
     for (int p = 0; p < n; ++p) refine(p);
@@ -959,7 +1080,8 @@ extern "C" sem_status sem_batch_solve(sem_batch* bt, const double* const* b_L,
           phase[p] = FINISHED;
           continue;
         }
-        outer_update(bt->hs[p], x_L[p], own);
+        if (bt->glob) add_from_global(bt->hs[p], x_L[p], bt->hs[p]->xg.ptr, own);
+        else outer_update(bt->hs[p], x_L[p], own);
         refine(p);
       }
     }

@@ -895,7 +895,7 @@ double inner_target(double inner_tol, double tol, double rel) {
 
 // global inner vectors (allocated zeroed, so that the padding stays zero) and
 // the Jacobi diagonal in global form
-static void glob_prepare(sem_handle* h, cudaStream_t s) {
+void glob_prepare(sem_handle* h, cudaStream_t s) {
   const int64_t n = glob_padded(h);
   for (DevBuf<float>* b : {&h->rg, &h->pg, &h->wg, &h->xg, &h->dinvg}) {
     if (b->n < (size_t)n) {
@@ -1011,6 +1011,12 @@ void outer_norm_b(sem_handle* h, const double* b, cudaStream_t s) {
 void outer_residual(sem_handle* h, const double* b, const double* x, const sem_solve_opts& o,
                     cudaStream_t s) {
   residual64(h, b, x, o.h1, o.h2, o.h1_field, h->r32.ptr, h->state.ptr, s);
+}
+
+void outer_residual_global(sem_handle* h, const double* b, const double* x,
+                           const sem_solve_opts& o, cudaStream_t s) {
+  residual64(h, b, x, o.h1, o.h2, o.h1_field, nullptr, h->state.ptr, s);
+  to_global<double>(h, h->r.ptr, h->rg.ptr, s);
 }
 
 void outer_update(sem_handle* h, double* x, cudaStream_t s) {

@@ -26,16 +26,13 @@
 
 #include "sem_internal.cuh"
 #include "reduce.cuh"
+#include "tma.cuh"
 
 namespace sem {
 namespace {
 
 constexpr int kSwThreads = 128;
 constexpr int kNbr = 0, kDir = 1, kFree = 2;
-
-__device__ __forceinline__ void red_add_f32(float* p, float v) {
-  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
-}
 
 // ------------------------------------------------------------------ host setup
 // Symmetric eigen-decomposition by cyclic Jacobi rotations (n <= 13):
@@ -242,7 +239,7 @@ schwarz_local_kernel(const float* __restrict__ rg, float* __restrict__ zg,
         const long long vi = (long long)(ex + (v & 1)) +
                              (long long)(prm.nelx + 1) *
                                  ((ey + ((v >> 1) & 1)) + (long long)(prm.nely + 1) * (ez + (v >> 2)));
-        red_add_f32(rc + vi, t);
+        red_add(rc + vi, t);
       }
     }
     if (prm.do_local) {
@@ -306,7 +303,7 @@ schwarz_local_kernel(const float* __restrict__ rg, float* __restrict__ zg,
         for (int c = 0; c < R; ++c) col[c] = c < PE ? box[(c * PE + cb) * R + ca] : 0.0f;
 #pragma unroll 2
         for (int c = 0; c < PE; ++c)
-          if ((kz >> c) & 1u) red_add_f32(zg + cbase + prm.sk * c, dot_row<R>(tz + PE * R + c * R, col, PE));
+          if ((kz >> c) & 1u) red_add(zg + cbase + prm.sk * c, dot_row<R>(tz + PE * R + c * R, col, PE));
       }
     }
     __syncthreads();                         // box and red are reused by the next element
@@ -338,7 +335,7 @@ __global__ void k_coarse_matvec(int E, const float* __restrict__ K, const float*
       float acc = 0.0f;
 #pragma unroll
       for (int c = 0; c < 8; ++c) acc = fmaf(Ke[r <= c ? pk(r, c) : pk(c, r)], pv[c], acc);
-      red_add_f32(w + vi[r], acc);
+      red_add(w + vi[r], acc);
     }
   }
 }

@@ -94,7 +94,7 @@ struct DevBuf {
 // multiply and shift (Granlund and Montgomery, 1994): q = (umulhi(n, m) + n) >> s
 struct FastDiv {
   uint32_t d, m, s;
-  FastDiv() : d(1), m(0), s(0) {}
+  __host__ __device__ FastDiv() : d(1), m(0), s(0) {}
   explicit FastDiv(uint32_t dd) : d(dd) {
     s = 0;
     while ((1ull << s) < dd) ++s;
@@ -242,6 +242,11 @@ void outer_norm_b(sem_handle* h, const double* b, cudaStream_t s);    // <b,b> -
 void outer_residual(sem_handle* h, const double* b, const double* x, const sem_solve_opts& o,
                     cudaStream_t s);                                   // r, r32, <r,r> -> state[0]
 void outer_update(sem_handle* h, double* x, cudaStream_t s);          // x += x32
+// global-vector inner solves: vectors and the global Jacobi diagonal; the
+// FP64 residual r (state[0].rr) and its global copy rg
+void glob_prepare(sem_handle* h, cudaStream_t s);
+void outer_residual_global(sem_handle* h, const double* b, const double* x,
+                           const sem_solve_opts& o, cudaStream_t s);
 CGState state_to_host(const CGState* d, cudaStream_t s, int* dev_err);
 
 // ---- global.cu: the FP32 operator on global vectors, w_g = mask Q^T H_L Q u_g

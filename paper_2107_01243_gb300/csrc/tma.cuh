@@ -1,5 +1,6 @@
 // Bulk asynchronous copies (TMA, cp.async.bulk) into shared memory with
-// mbarrier completion, and bounded waits.  Every wait gives up after a time
+// mbarrier completion, and bounded waits; 4-byte cp.async copies and L2
+// reductions without a returned value.  Every wait gives up after a time
 // limit, records SEM_ERR_TIMEOUT in a device error word and returns false, so
 // a stuck copy ends the kernel instead of hanging the GPU.
 #pragma once
@@ -70,6 +71,26 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
   if (err) atomicExch(err, (int)SEM_ERR_TIMEOUT);
   return false;
+}
+
+// 4-byte asynchronous global -> shared copies (cp.async), completed per thread
+// by wait_group and made visible to the CTA by a barrier
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
+}
+
+// w[0] += v in L2 with no value returned (atomicAdd may compile to an atomic
+// that returns the old value, whose register the warp then waits for)
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
 }  // namespace sem

@@ -1,6 +1,7 @@
 """Batched solves through the C ABI: problems of different element counts,
 orders and Helmholtz coefficients solved together, each judged by the
-oracle's FP64 residual and against its own single solve."""
+oracle's FP64 residual and against its own single solve; the inner solves
+run on global vectors (the default) or on L-vectors."""
 import numpy as np
 import pytest
 import torch
@@ -12,10 +13,11 @@ from tests.helpers import OracleProblem, rel_inf, TWO_PI
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
-# with orders N = 1, 3 the batch runs the element kernel and the gather-scatter
-# kernel; with N in {5, 7, 9} only, the fused operator (segments of four
-# elements, split gather-scatter): partial segments, single-element rows and
-# meshes one element thick are included
+# on L-vectors, with orders N = 1, 3 the batch runs the element kernel and the
+# gather-scatter kernel; with N in {5, 7, 9} only, the fused operator (segments
+# of four elements, split gather-scatter): partial segments, single-element
+# rows and meshes one element thick are included.  On global vectors every
+# order runs the gathering element kernel.
 PROBLEMS = [((3, 2, 2), 5, 0.7), ((2, 2, 2), 7, 3.1), ((4, 3, 2), 3, 0.1), ((1, 1, 2), 9, 9.5),
             ((3, 3, 3), 7, 1.7), ((3, 3, 2), 1, 2.0)]
 PROBLEMS_FUSED = [((3, 2, 2), 5, 0.7), ((2, 2, 2), 7, 3.1), ((1, 1, 2), 9, 9.5),
@@ -38,8 +40,12 @@ def _setup(problems):
 
 @pytest.mark.parametrize("use_graph", [True, False])
 @pytest.mark.parametrize("problems", [PROBLEMS, PROBLEMS_FUSED], ids=["unfused", "fused"])
-def test_batch_matches_oracle_and_single_solves(use_graph, problems):
+@pytest.mark.parametrize("inner", [sem.SEM_INNER_AUTO, sem.SEM_INNER_LOCAL],
+                         ids=["global-vectors", "local-vectors"])
+def test_batch_matches_oracle_and_single_solves(use_graph, problems, inner):
     hs, oracles, bs = _setup(problems)
+    for h in hs:
+        sem.sem_set_inner_vectors(h, inner)
     batch = sem.sem_batch_create(hs)
     xs = [torch.empty_like(b) for _, b in bs]
     lams = [lam for _, _, lam in problems]
