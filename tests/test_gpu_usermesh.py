@@ -70,3 +70,54 @@ def test_user_coordinates_solve():
         res = solve.residual(x.cpu().numpy().reshape(gid.shape), b_ref, G, D, gid, mask, mult,
                              1.0, 0.5, B)
         assert res <= 1.05e-9
+
+
+def _user_problem(nel, N):
+    X, Y, Z = twisted(nel, N)
+    xyz = np.concatenate([X.ravel(), Y.ravel(), Z.ravel()])
+    h = sem.sem_setup(nel, N, xyz=xyz)
+    G, B, _ = geometry.geom_factors(X, Y, Z, N)
+    gid = mesh.global_ids(*nel, N)
+    return h, (X, Y, Z), G, B, deriv_matrix(N), gid, mesh.dirichlet_mask(*nel, N), \
+        mesh.multiplicity(gid)
+
+
+def test_user_coordinates_global_operator():
+    nel, N = (3, 4, 2), 7
+    h, _, G, B, D, gid, mask, _ = _user_problem(nel, N)
+    ug = si.uniform((int(gid.max()) + 1,), 32).astype(np.float32).astype(np.float64)
+    ud = torch.from_numpy(ug).to(DEV, torch.float32)
+    w = torch.empty_like(ud)
+    sem.sem_apply_global(h, ud, w, 1.0, 0.6)
+    ref = operator.matvec(ug[gid], G, D, gid, mask, 1.0, 0.6, B)
+    assert rel_inf(w.double().cpu().numpy()[gid], ref) < 2e-5
+
+
+def test_user_coordinates_pressure_and_pipelined_solvers():
+    """GMRES with the Schwarz preconditioner (whose local solves use the box
+    spacing of the mesh description, here the unit box) and the pipelined
+    PCG on the twisted mesh, against the oracle."""
+    from oracle import gmres
+    from oracle.schwarz import Schwarz
+    nel, N, h2 = (4, 3, 3), 5, 0.5
+    h, (X, Y, Z), G, B, D, gid, mask, mult = _user_problem(nel, N)
+    f = si.eval_fourier(si.fourier_modes(42), X, Y, Z)
+    b_ref = solve.rhs(f, B, gid, mask)
+    b = torch.from_numpy(b_ref).to(DEV).view(-1)
+    H = lambda v: operator.matvec(v, G, D, gid, mask, 1.0, h2, B)
+    pre = sem.sem_schwarz_create(h, 1.0, h2)
+    x = torch.empty_like(b)
+    info = sem.sem_gmres_solve(h, b, x, h2=h2, tol=1e-9, restart=10, precond=pre)
+    assert info["status"] == "SEM_OK", info
+    res = solve.residual(x.cpu().numpy().reshape(gid.shape), b_ref, G, D, gid, mask, mult, 1.0,
+                         h2, B)
+    assert res <= 1.0001e-9
+    sw = Schwarz(nel, N, G, B, length=(1.0, 1.0, 1.0), h2=h2)
+    ref = gmres.fgmres(b_ref, H, sw.apply, mult, tol=1e-9, m=10, maxit=2000)
+    assert abs(info["iters"] - ref.iters) <= max(2, ref.iters // 10), (info, ref.iters)
+    sem.sem_set_cg_variant(h, sem.SEM_CG_PIPELINED)
+    xp = torch.empty_like(b)
+    info_p = sem.sem_cg_solve(h, b, xp, h2=h2, tol=1e-9)
+    assert info_p["status"] == "SEM_OK", info_p
+    assert solve.residual(xp.cpu().numpy().reshape(gid.shape), b_ref, G, D, gid, mask, mult, 1.0,
+                          h2, B) <= 1.0001e-9
