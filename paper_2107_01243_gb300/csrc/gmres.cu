@@ -22,7 +22,7 @@
 namespace sem {
 namespace {
 
-constexpr int kMaxRestart = 32;         // the fused Gram-Schmidt kernels take 32 vectors
+constexpr int kMaxRestart = 32;         // vectors the Gram-Schmidt kernels hold (kGsMax)
 
 // out = s v
 __global__ void k_scale(int64_t n, const double* __restrict__ v, double sc,
@@ -40,7 +40,7 @@ __global__ void k_hadamard(int64_t n, const double* __restrict__ d, const double
     z[q] = d[q] * v[q];
 }
 
-constexpr int kGsMax = 32;            // vectors a fused Gram-Schmidt kernel takes
+constexpr int kGsMax = 32;            // vector pointers and coefficients an update kernel keeps
 
 // Gram-Schmidt kernels.  Dots: blockIdx.y takes a chunk of kGsChunk vectors
 // (eight accumulators per thread, full occupancy), each chunk reduced on its
