@@ -31,6 +31,8 @@ bool launch_ax_tma_fused(const sem_handle* h, const float* u, float* w, float h1
                          const float* h1f, const CGState* st, CGState* pwst, cudaStream_t s);
 bool launch_ax_df_fused(const sem_handle* h, const double* u, double* w, double h1, double h2,
                         const CGState* st, CGState* pwst, cudaStream_t s);
+void launch_ax_df_fused_slab(const sem_handle* h, const double* u, double* w, double h1,
+                             double h2, int z0, int z1, cudaStream_t s);
 bool df_ax_supported(const sem_handle* h, const void* u, const void* w, const void* h1f);
 
 namespace {
@@ -125,26 +127,54 @@ int sweep_blocks(long long total) {
   return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 16LL * kNumSMs));
 }
 
+// the finishing passes on a box of nelx x nely x nelz elements starting at w
 template <int P, class T>
-void finish_p(const sem_handle* h, T* w, const CGState* st, cudaStream_t s) {
-  const long long nseg = (h->E + kFuseSeg - 1) / kFuseSeg;
-  if (nseg > 1 && h->nelx > 1) {
-    k_sx_cut<P, T><<<(unsigned)(nseg - 1), P * P, 0, s>>>(w, h->nelx, st);
+void finish_box(T* w, int nelx, int nely, int nelz, const CGState* st, cudaStream_t s) {
+  const long long E = (long long)nelx * nely * nelz;
+  const long long nseg = (E + kFuseSeg - 1) / kFuseSeg;
+  if (nseg > 1 && nelx > 1) {
+    k_sx_cut<P, T><<<(unsigned)(nseg - 1), P * P, 0, s>>>(w, nelx, st);
     SEM_CHECK_LAUNCH();
   }
-  if (h->nely > 1) {
-    const long long total = (long long)h->nelx * (h->nely - 1) * h->nelz * P * (P / 2);
+  if (nely > 1) {
+    const long long total = (long long)nelx * (nely - 1) * nelz * P * (P / 2);
     k_sy<P, T><<<sweep_blocks(total), 256, 0, s>>>(
-        w, h->nelx, h->nely, (uint32_t)total, FastDiv((uint32_t)h->nelx),
-        FastDiv((uint32_t)(h->nely - 1)), st);
+        w, nelx, nely, (uint32_t)total, FastDiv((uint32_t)nelx), FastDiv((uint32_t)(nely - 1)),
+        st);
     SEM_CHECK_LAUNCH();
   }
-  if (h->nelz > 1) {
-    const long long layer = (long long)h->nelx * h->nely;
-    const long long total = layer * (h->nelz - 1) * P * P / (16 / (int)sizeof(T));
+  if (nelz > 1) {
+    const long long layer = (long long)nelx * nely;
+    const long long total = layer * (nelz - 1) * P * P / (16 / (int)sizeof(T));
     k_sz<P, T><<<sweep_blocks(total), 256, 0, s>>>(w, (uint32_t)layer, (uint32_t)total, st);
     SEM_CHECK_LAUNCH();
   }
+}
+
+template <int P, class T>
+void finish_p(const sem_handle* h, T* w, const CGState* st, cudaStream_t s) {
+  finish_box<P, T>(w, h->nelx, h->nely, h->nelz, st, s);
+}
+
+// z-pairs between element planes z - 1 and z of the box (one plane of pairs)
+template <int P, class T>
+void zpairs_between(const sem_handle* h, T* w, int z, cudaStream_t s) {
+  constexpr long long P3 = (long long)P * P * P;
+  const long long layer = (long long)h->nelx * h->nely;
+  const long long total = layer * P * P / (16 / (int)sizeof(T));
+  k_sz<P, T><<<sweep_blocks(total), 256, 0, s>>>(w + (z - 1) * layer * P3, (uint32_t)layer,
+                                                  (uint32_t)total, nullptr);
+  SEM_CHECK_LAUNCH();
+}
+
+// the finishing passes of the slab of element planes [z0, z1), then (z0 > 0)
+// the z-pairs between it and the slab below
+template <int P>
+void finish_slab(const sem_handle* h, double* w, int z0, int z1, cudaStream_t s) {
+  constexpr long long P3 = (long long)P * P * P;
+  finish_box<P, double>(w + (long long)z0 * h->nelx * h->nely * P3, h->nelx, h->nely, z1 - z0,
+                        nullptr, s);
+  if (z0 > 0) zpairs_between<P, double>(h, w, z0, s);
 }
 
 template <class T>
@@ -192,6 +222,82 @@ bool launch_apply(sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T 
   }
   if (phase & SEM_APPLY_FINISH) finish<T>(h, w, st, s);
   return pw;
+}
+
+// Streams and events of the pipelined host-buffer operator, kept per handle.
+struct HostPipe {
+  static constexpr int kSlabs = 16;
+  cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
+  cudaEvent_t start = nullptr, arrived[kSlabs] = {}, final_[kSlabs] = {};
+  HostPipe() {
+    SEM_CUDA(cudaStreamCreateWithFlags(&in, cudaStreamNonBlocking));
+    SEM_CUDA(cudaStreamCreateWithFlags(&comp, cudaStreamNonBlocking));
+    SEM_CUDA(cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking));
+    SEM_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    for (int q = 0; q < kSlabs; ++q) {
+      SEM_CUDA(cudaEventCreateWithFlags(&arrived[q], cudaEventDisableTiming));
+      SEM_CUDA(cudaEventCreateWithFlags(&final_[q], cudaEventDisableTiming));
+    }
+  }
+  ~HostPipe() {
+    for (int q = 0; q < kSlabs; ++q) {
+      if (arrived[q]) cudaEventDestroy(arrived[q]);
+      if (final_[q]) cudaEventDestroy(final_[q]);
+    }
+    if (start) cudaEventDestroy(start);
+    for (cudaStream_t t : {in, comp, out})
+      if (t) cudaStreamDestroy(t);
+  }
+};
+
+bool host_pipeline_supported(const sem_handle* h, const void* din, const void* dout) {
+  return h->nelz >= 2 && apply_fused_supported<double>(h, din, dout, nullptr);
+}
+
+// w_host = mask o QQ^T A_L u_host (FP64) with the copies overlapped with the
+// work: the box is cut into slabs of element planes; slab q is copied in on
+// one stream, its element kernel and finishing passes (and the z-pairs with
+// slab q - 1) run on a second, and slab q - 1, then final, is copied out on a
+// third while later slabs are still arriving or being computed.  Every pair
+// sum is the one the unsplit operator forms, so the result is the same.
+void apply_host_pipelined(sem_handle* h, const double* u_host, double* w_host, double* din,
+                          double* dout, cudaStream_t user) {
+  if (!h->host_pipe) h->host_pipe = std::make_shared<HostPipe>();
+  HostPipe& hp = *h->host_pipe;
+  const int S = std::min(HostPipe::kSlabs, h->nelz);
+  const long long P3 = h->P3, layer = (long long)h->nelx * h->nely;
+  std::vector<int> z(S + 1);
+  for (int q = 0; q <= S; ++q) z[q] = (int)((long long)q * h->nelz / S);
+  SEM_CUDA(cudaEventRecord(hp.start, user));
+  SEM_CUDA(cudaStreamWaitEvent(hp.in, hp.start, 0));
+  SEM_CUDA(cudaStreamWaitEvent(hp.comp, hp.start, 0));
+  SEM_CUDA(cudaStreamWaitEvent(hp.out, hp.start, 0));
+  for (int q = 0; q < S; ++q) {
+    const long long o = z[q] * layer * P3, n = (long long)(z[q + 1] - z[q]) * layer * P3;
+    SEM_CUDA(cudaMemcpyAsync(din + o, u_host + o, n * sizeof(double), cudaMemcpyHostToDevice,
+                             hp.in));
+    SEM_CUDA(cudaEventRecord(hp.arrived[q], hp.in));
+  }
+  for (int q = 0; q < S; ++q) {
+    SEM_CUDA(cudaStreamWaitEvent(hp.comp, hp.arrived[q], 0));
+    launch_ax_df_fused_slab(h, din, dout, 1.0, 0.0, z[q], z[q + 1], hp.comp);
+    switch (h->P) {
+      case 6: finish_slab<6>(h, dout, z[q], z[q + 1], hp.comp); break;
+      case 8: finish_slab<8>(h, dout, z[q], z[q + 1], hp.comp); break;
+      case 10: finish_slab<10>(h, dout, z[q], z[q + 1], hp.comp); break;
+      default: throw Error(SEM_ERR_ARG, "apply_host_pipelined: unsupported order");
+    }
+    if (q > 0) SEM_CUDA(cudaEventRecord(hp.final_[q - 1], hp.comp));
+  }
+  SEM_CUDA(cudaEventRecord(hp.final_[S - 1], hp.comp));
+  for (int q = 0; q < S; ++q) {
+    const long long o = z[q] * layer * P3, n = (long long)(z[q + 1] - z[q]) * layer * P3;
+    SEM_CUDA(cudaStreamWaitEvent(hp.out, hp.final_[q], 0));
+    SEM_CUDA(cudaMemcpyAsync(w_host + o, dout + o, n * sizeof(double), cudaMemcpyDeviceToHost,
+                             hp.out));
+  }
+  SEM_CUDA(cudaStreamSynchronize(hp.out));
+  SEM_CUDA(cudaStreamSynchronize(hp.comp));
 }
 
 template bool launch_apply<float>(sem_handle*, const OpData<float>&, const float*, float*, float,

@@ -361,10 +361,19 @@ static void df_upload_d(const sem_handle* h) {
   done[P] = true;
 }
 
+// A slab of whole element planes: elements [e0, e0 + E) of the handle, the
+// box fb (its nelz the slab's planes, its faces those the slab touches).
+struct DFSlab {
+  int64_t e0;
+  int E;
+  FuseBox fb;
+};
+
 // returns the grid it launched (the fused operator's later passes need it)
 template <int P, int STAGES, bool FUSE = false>
 static int launch_df_p(const sem_handle* h, const double* u, double* w, double h1, double h2,
-                       const CGState* st, cudaStream_t s, CGState* pwst = nullptr) {
+                       const CGState* st, cudaStream_t s, CGState* pwst = nullptr,
+                       const DFSlab* slab = nullptr) {
   const bool helm = (float)h2 != 0.0f;
   const size_t smem = df_smem_bytes<P, STAGES>(helm);
   auto kern = ax_df_kernel<P, STAGES, FUSE>;
@@ -388,13 +397,17 @@ static int launch_df_p(const sem_handle* h, const double* u, double* w, double h
   c.h1l = (float)(h1 - (double)c.h1h);
   c.h2h = (float)h2;
   c.h2l = (float)(h2 - (double)c.h2h);
-  const int E = (int)h->E;
+  const int E = slab ? slab->E : (int)h->E;
+  const int64_t e0 = slab ? slab->e0 : 0;
+  constexpr int64_t P3 = (int64_t)P * P * P;
   int grid = (int)std::min<int64_t>(E, (int64_t)o * df_num_sms());
   if (grid < 1) grid = 1;
   if (pwst) grid = std::min(grid, kFusedPartials);
-  const FuseBox fb{h->nelx, h->nely, h->nelz, h->faces};
-  kern<<<grid, 3 * P * P, smem, s>>>(u, w, h->gdf.ptr, h->bdf.ptr, c, E, st, h->dev_err.ptr,
-                                     kWaitTimeoutNs, fb, pwst, h->partials.ptr + 4 * kRedBlocks);
+  const FuseBox fb = slab ? slab->fb : FuseBox{h->nelx, h->nely, h->nelz, h->faces};
+  kern<<<grid, 3 * P * P, smem, s>>>(u + e0 * P3, w + e0 * P3, h->gdf.ptr + e0 * 6 * P3,
+                                     h->bdf.ptr ? h->bdf.ptr + e0 * P3 : nullptr, c, E, st,
+                                     h->dev_err.ptr, kWaitTimeoutNs, fb, pwst,
+                                     h->partials.ptr + 4 * kRedBlocks);
   SEM_CHECK_LAUNCH();
   return grid;
 }
@@ -444,6 +457,33 @@ bool launch_ax_df_fused(const sem_handle* h, const double* u, double* w, double 
       else launch_df_p<10, 1, true>(h, u, w, h1, h2, st, s);
       return false;
     default: throw Error(SEM_ERR_ARG, "launch_ax_df_fused: unsupported order");
+  }
+}
+
+// The fused element kernel on the slab of element planes [z0, z1): faces of
+// the box that the slab does not touch are not Dirichlet faces of the slab.
+void launch_ax_df_fused_slab(const sem_handle* h, const double* u, double* w, double h1,
+                             double h2, int z0, int z1, cudaStream_t s) {
+  const int64_t layer = (int64_t)h->nelx * h->nely;
+  int faces = h->faces;
+  if (z0 > 0) faces &= ~SEM_FACE_ZMIN;
+  if (z1 < h->nelz) faces &= ~SEM_FACE_ZMAX;
+  const DFSlab sl{z0 * layer, (int)((z1 - z0) * layer), FuseBox{h->nelx, h->nely, z1 - z0, faces}};
+  const bool two = h->tune.df_variant != 0;
+  switch (h->P) {
+    case 6:
+      if (two) launch_df_p<6, 2, true>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
+      else launch_df_p<6, 1, true>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
+      break;
+    case 8:
+      if (two) launch_df_p<8, 2, true>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
+      else launch_df_p<8, 1, true>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
+      break;
+    case 10:
+      if (two) launch_df_p<10, 2, true>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
+      else launch_df_p<10, 1, true>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
+      break;
+    default: throw Error(SEM_ERR_ARG, "launch_ax_df_fused_slab: unsupported order");
   }
 }
 

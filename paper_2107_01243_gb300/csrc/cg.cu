@@ -1143,6 +1143,17 @@ extern "C" sem_status sem_apply_host(sem_handle* h, const void* u_host, void* w_
     ensure(h->stage_in, n);
     ensure(h->stage_out, n);
     const size_t bytes = n * (dtype == SEM_F64 ? sizeof(double) : sizeof(float));
+    if (dtype == SEM_F64 && host_pipeline_supported(h, h->stage_in.ptr, h->stage_out.ptr)) {
+      apply_host_pipelined(h, (const double*)u_host, (double*)w_host, h->stage_in.ptr,
+                           h->stage_out.ptr, s);
+      int herr = 0;
+      SEM_CUDA(cudaMemcpy(&herr, h->dev_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+      if (herr) {
+        SEM_CUDA(cudaMemset(h->dev_err.ptr, 0, sizeof(int)));
+        throw Error(SEM_ERR_TIMEOUT, "sem_apply_host: a bounded device wait timed out");
+      }
+      return;
+    }
     SEM_CUDA(cudaMemcpyAsync(h->stage_in.ptr, u_host, bytes, cudaMemcpyHostToDevice, s));
     if (dtype == SEM_F64) {
       launch_apply<double>(h, h->f64, h->stage_in.ptr, h->stage_out.ptr, 1.0, 0.0, nullptr,

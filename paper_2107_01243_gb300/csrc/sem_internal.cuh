@@ -16,6 +16,7 @@
 namespace sem {
 
 struct GmresWork;                    // gmres.cu
+struct HostPipe;                     // apply.cu
 
 constexpr int kMaxN = 10;            // highest supported polynomial order
 constexpr int kMaxP = kMaxN + 1;
@@ -184,6 +185,7 @@ struct sem_handle {
   // host staging for sem_apply_host
   sem::DevBuf<double> stage_in, stage_out;
   std::shared_ptr<sem::GmresWork> gmres;    // GMRES workspace, kept between solves
+  std::shared_ptr<sem::HostPipe> host_pipe; // streams of the pipelined sem_apply_host
   double dinv_h1 = NAN, dinv_h2 = NAN;
   const void* dinv_h1f = nullptr;
   int dinv_valid = 0;
@@ -258,6 +260,11 @@ bool launch_apply_global(const sem_handle* h, const float* u, float* w, float h1
 template <class Tin>
 void to_global(const sem_handle* h, const Tin* in, float* out, cudaStream_t s);  // owner copies
 void add_from_global(const sem_handle* h, double* x, const float* d, cudaStream_t s);
+
+// ---- apply.cu: FP64 operator with host buffers, copies overlapped by slabs
+bool host_pipeline_supported(const sem_handle* h, const void* din, const void* dout);
+void apply_host_pipelined(sem_handle* h, const double* u_host, double* w_host, double* din,
+                          double* dout, cudaStream_t user);
 
 // ---- cg.cu: FP32 CG steps on vectors padded to a multiple of 4 with zeros
 // (nv4 = padded length / 4), plain dots (each entry counted once); w must
