@@ -35,6 +35,14 @@ METRIC = "Ax+dssum GDOF/s (FP64, N=7, E=32^3 deformed); CG solve to 1e-8 mixed v
 UNIT = "GDOF/s"
 
 
+def arm_config(world, n=32 ** 3 * 8 ** 3):
+    """The workload of the operator line, shared by both arms."""
+    return {"workload": "Ax+dssum (mask), 32x32x32 deformed hex elements on [0,2pi]^3, "
+                        "N=7, u~U(-1,1) seed 42",
+            "local_points": n, "l2": "inputs larger than L2 (u 134 MB, G 805 MB)",
+            "parallelism": f"replicas x{world}"}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -178,8 +186,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "Ax+dssum, 32x32x32 deformed hex elements on [0,2pi]^3, N=7 "
-                               "(oracle sample: 32x32x2 slab)", "sample_points": int(u.size)},
+        "config": arm_config(args.gpus),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -344,10 +351,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "Ax+dssum (mask), 32x32x32 deformed hex elements on [0,2pi]^3, "
-                               "N=7, u~U(-1,1) seed 42",
-                   "local_points": n, "l2": "inputs larger than L2 (u 134 MB, G 805 MB)",
-                   "parallelism": f"replicas x{world}"},
+        "config": arm_config(world, n),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": ax_traffic(tiles),
                      "kernel": ax_kernel_name(tiles),
