@@ -484,7 +484,7 @@ sem_status sem_dot_noalloc(sem_handle* h, const double* a, const double* b, doub
  * sem_apply does, copies the result to w_host and synchronises the stream.
  * Pinned host memory gives full copy bandwidth.  In FP64 on the fused path
  * (N in {5, 7, 9}, at least two element planes in z) the box is cut into up
- * to 16 slabs of element planes and the copies overlap the work: slab q is
+ * to 8 slabs of element planes and the copies overlap the work: slab q is
  * copied in while earlier slabs are computed and copied out, on streams of
  * the handle ordered after the caller's stream; the result is the same, bit
  * for bit, as sem_apply's.

@@ -226,7 +226,7 @@ bool launch_apply(sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T 
 
 // Streams and events of the pipelined host-buffer operator, kept per handle.
 struct HostPipe {
-  static constexpr int kSlabs = 16;
+  static constexpr int kSlabs = 8;
   cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
   cudaEvent_t start = nullptr, arrived[kSlabs] = {}, final_[kSlabs] = {};
   HostPipe() {
