@@ -257,9 +257,10 @@ bool host_pipeline_supported(const sem_handle* h, const void* din, const void* d
 // w_host = mask o QQ^T A_L u_host (FP64) with the copies overlapped with the
 // work: the box is cut into slabs of element planes; slab q is copied in on
 // one stream, its element kernel and finishing passes (and the z-pairs with
-// slab q - 1) run on a second, and slab q - 1, then final, is copied out on a
-// third while later slabs are still arriving or being computed.  Every pair
-// sum is the one the unsplit operator forms, so the result is the same.
+// slab q - 1) run on a second, and the planes those passes made final are
+// copied out on a third while later slabs are still arriving or being
+// computed.  Every pair sum is the one the unsplit operator forms, so the
+// result is the same.
 void apply_host_pipelined(sem_handle* h, const double* u_host, double* w_host, double* din,
                           double* dout, cudaStream_t user) {
   if (!h->host_pipe) h->host_pipe = std::make_shared<HostPipe>();
@@ -287,11 +288,15 @@ void apply_host_pipelined(sem_handle* h, const double* u_host, double* w_host, d
       case 10: finish_slab<10>(h, dout, z[q], z[q + 1], hp.comp); break;
       default: throw Error(SEM_ERR_ARG, "apply_host_pipelined: unsupported order");
     }
-    if (q > 0) SEM_CUDA(cudaEventRecord(hp.final_[q - 1], hp.comp));
+    SEM_CUDA(cudaEventRecord(hp.final_[q], hp.comp));
   }
-  SEM_CUDA(cudaEventRecord(hp.final_[S - 1], hp.comp));
+  // after slab q's passes the planes from the last plane of slab q - 1 up to
+  // (not including) slab q's last plane are final; the last slab's last
+  // plane too
   for (int q = 0; q < S; ++q) {
-    const long long o = z[q] * layer * P3, n = (long long)(z[q + 1] - z[q]) * layer * P3;
+    const long long p0 = q == 0 ? z[0] : z[q] - 1, p1 = q == S - 1 ? z[S] : z[q + 1] - 1;
+    if (p1 <= p0) continue;
+    const long long o = p0 * layer * P3, n = (p1 - p0) * layer * P3;
     SEM_CUDA(cudaStreamWaitEvent(hp.out, hp.final_[q], 0));
     SEM_CUDA(cudaMemcpyAsync(w_host + o, dout + o, n * sizeof(double), cudaMemcpyDeviceToHost,
                              hp.out));
