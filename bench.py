@@ -543,12 +543,14 @@ def run_pressure(sem, torch, dev, restart=10, nel=48):
     t_setup = time.perf_counter() - t0
     out = {"workload": f"Poisson, {nel}^3 deformed hex elements, N=7, 8 Fourier-mode RHS, "
                        "FP64 to 1e-8", "restart": restart, "schwarz_setup_seconds": t_setup}
-    for name, prec in (("gmres_schwarz", pre),):
+    # gmres_schwarz_mixed: FP32 inner FGMRES on global vectors, FP64 refinement
+    for name, prec in (("gmres_schwarz", sem.SEM_SOLVE_F64),
+                       ("gmres_schwarz_mixed", sem.SEM_SOLVE_MIXED)):
         x = torch.empty_like(b)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        info = sem.sem_gmres_solve(h, b, x, tol=cfg["tol"], restart=restart, precond=prec,
-                                   maxit=20000, raise_on_fail=False)
+        info = sem.sem_gmres_solve(h, b, x, tol=cfg["tol"], restart=restart, precond=pre,
+                                   maxit=20000, precision=prec, raise_on_fail=False)
         torch.cuda.synchronize()
         out[name] = {"seconds": time.perf_counter() - t0, "iters": info["iters"],
                      "restarts": info["outer_iters"], "rel_res": info["rel_res"],

@@ -388,7 +388,14 @@ sem_status sem_schwarz_destroy(sem_schwarz* s);
  * directions; restarts from the true residual.  precond: a Schwarz object
  * made for the same handle (and coefficients), or NULL for point Jacobi.
  * opts: h1, h2, tol (relative residual), maxit (iterations), x0_is_zero,
- * stream as for sem_cg_solve (h1_field must be NULL, precision is ignored).
+ * stream as for sem_cg_solve (h1_field must be NULL).  With precision
+ * SEM_SOLVE_MIXED, a Schwarz preconditioner and a handle that allows global
+ * vectors (FP32 geometry, odd N), the solve is FP64 iterative refinement on
+ * L-vectors around an FP32 flexible GMRES on global vectors (operator as
+ * sem_apply_global, preconditioner on global vectors), each inner solve to
+ * the relative tolerance of sem_cg_solve's mixed solves (inner_tol,
+ * max_outer); info.outer_iters then counts refinement steps.  Otherwise the
+ * FP64 solve runs.
  * The workspace (2 restart + 2 FP64 L-vectors) is allocated on the first
  * solve and kept on the handle until it is destroyed.  Synchronises once per
  * iteration.  info: iterations, restart cycles in outer_iters, final

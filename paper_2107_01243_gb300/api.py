@@ -453,15 +453,20 @@ def sem_schwarz_apply(sw, r, z, stream=None):
 
 
 def sem_gmres_solve(h, b, x, h1=1.0, h2=0.0, tol=1e-8, maxit=5000, restart=30, precond=None,
-                    x0=None, stream=None, raise_on_fail=True):
+                    precision=SEM_SOLVE_F64, inner_tol=1e-4, max_outer=30, x0=None, stream=None,
+                    raise_on_fail=True):
     """Flexible GMRES(restart) for mask o QQ^T H x = b, right-preconditioned by a
     Schwarz object (or point Jacobi when precond is None); returns the info dict
-    (outer_iters = restart cycles)."""
+    (outer_iters = restart cycles in FP64, refinement steps in mixed precision).
+    precision=SEM_SOLVE_MIXED with a Schwarz object runs FP32 inner GMRES on
+    global vectors inside FP64 refinement."""
     lib = _lib.load()
     o = SolveOpts()
     lib.sem_solve_opts_default(ctypes.byref(o))
     o.h1, o.h2 = float(h1), float(h2)
     o.tol, o.maxit = float(tol), int(maxit)
+    o.precision = int(precision)
+    o.inner_tol, o.max_outer = float(inner_tol), int(max_outer)
     pb = h._vec(b, "b", torch.float64)
     px = h._vec(x, "x", torch.float64)
     if x0 is not None:

@@ -489,7 +489,7 @@ namespace sem {
 namespace {
 
 template <int PE>
-void launch_local(sem_schwarz* sw, cudaStream_t s) {
+void launch_local(sem_schwarz* sw, const float* rg, float* zg, cudaStream_t s) {
   const sem_handle* h = sw->h;
   auto kern = schwarz_local_kernel<PE>;
   static int occ = 0;
@@ -498,23 +498,22 @@ void launch_local(sem_schwarz* sw, cudaStream_t s) {
     if (occ < 1) occ = 1;
   }
   const int grid = (int)std::min<int64_t>(h->E, (int64_t)occ * kNumSMs);
-  kern<<<grid, kSwThreads, 0, s>>>(sw->rg.ptr, sw->zg.ptr, sw->rc.ptr, sw->tab.ptr, sw->prm,
-                                   (int)h->E);
+  kern<<<grid, kSwThreads, 0, s>>>(rg, zg, sw->rc.ptr, sw->tab.ptr, sw->prm, (int)h->E);
   SEM_CHECK_LAUNCH();
 }
 
-void launch_local_any(sem_schwarz* sw, cudaStream_t s) {
+void launch_local_any(sem_schwarz* sw, const float* rg, float* zg, cudaStream_t s) {
   switch (sw->Pe) {
-    case 4: launch_local<4>(sw, s); break;
-    case 5: launch_local<5>(sw, s); break;
-    case 6: launch_local<6>(sw, s); break;
-    case 7: launch_local<7>(sw, s); break;
-    case 8: launch_local<8>(sw, s); break;
-    case 9: launch_local<9>(sw, s); break;
-    case 10: launch_local<10>(sw, s); break;
-    case 11: launch_local<11>(sw, s); break;
-    case 12: launch_local<12>(sw, s); break;
-    case 13: launch_local<13>(sw, s); break;
+    case 4: launch_local<4>(sw, rg, zg, s); break;
+    case 5: launch_local<5>(sw, rg, zg, s); break;
+    case 6: launch_local<6>(sw, rg, zg, s); break;
+    case 7: launch_local<7>(sw, rg, zg, s); break;
+    case 8: launch_local<8>(sw, rg, zg, s); break;
+    case 9: launch_local<9>(sw, rg, zg, s); break;
+    case 10: launch_local<10>(sw, rg, zg, s); break;
+    case 11: launch_local<11>(sw, rg, zg, s); break;
+    case 12: launch_local<12>(sw, rg, zg, s); break;
+    case 13: launch_local<13>(sw, rg, zg, s); break;
     default: throw Error(SEM_ERR_ARG, "schwarz: unsupported order");
   }
 }
@@ -595,13 +594,16 @@ void build_coarse(sem_schwarz* sw, cudaStream_t s) {
 
 sem_handle* schwarz_handle(const sem_schwarz* sw) { return sw->h; }
 
-void schwarz_apply(sem_schwarz* sw, const double* r, double* z, cudaStream_t s) {
+namespace {
+
+// the local solves of rg added into zg (zeroed here), the coarse restriction
+// and the coarse CG; returns the coarse solution or NULL (no coarse level)
+const float* schwarz_levels(sem_schwarz* sw, const float* rg, float* zg, cudaStream_t s) {
   sem_handle* h = sw->h;
-  to_global<double>(h, r, sw->rg.ptr, s);
-  SEM_CUDA(cudaMemsetAsync(sw->zg.ptr, 0, h->nG * sizeof(float), s));
+  SEM_CUDA(cudaMemsetAsync(zg, 0, h->nG * sizeof(float), s));
   const bool coarse = (sw->levels & SEM_SCHWARZ_COARSE) != 0;
   if (coarse) SEM_CUDA(cudaMemsetAsync(sw->rc.ptr, 0, sw->nv4 * 4 * sizeof(float), s));
-  launch_local_any(sw, s);
+  launch_local_any(sw, rg, zg, s);
   if (coarse) {
     CGState* st = sw->st.ptr;
     vcg_init(sw->nv4, sw->rc.ptr, sw->cdinv.ptr, sw->pc.ptr, sw->xc.ptr, sw->wc.ptr, st,
@@ -617,7 +619,64 @@ void schwarz_apply(sem_schwarz* sw, const double* r, double* z, cudaStream_t s) 
       vcg_pupd(sw->nv4, sw->pc.ptr, sw->rc.ptr, sw->cdinv.ptr, st, s);
     }
   }
-  const float* xcp = coarse ? sw->xc.ptr : nullptr;
+  return coarse ? sw->xc.ptr : nullptr;
+}
+
+// z_g = mask o (z_g + R_0^T c) at every global point, c read in the element
+// that holds the point at (i, j, k) with i, j, k < N where possible
+__global__ void k_sw_combine_global(int64_t nG, float* __restrict__ z, const float* __restrict__ xc,
+                                    SwParams prm, int faces, FastDiv dgx, FastDiv dgy,
+                                    FastDiv dN) {
+  const int N = prm.N;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nG;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t r = dgx.div((uint32_t)g);
+    const int ix = (int)((uint32_t)g - r * dgx.d);
+    const uint32_t izu = dgy.div(r);
+    const int iy = (int)(r - izu * dgy.d), iz = (int)izu;
+    const bool masked = ((faces & SEM_FACE_XMIN) && ix == 0) ||
+                        ((faces & SEM_FACE_XMAX) && ix == prm.gx - 1) ||
+                        ((faces & SEM_FACE_YMIN) && iy == 0) ||
+                        ((faces & SEM_FACE_YMAX) && iy == prm.gy - 1) ||
+                        ((faces & SEM_FACE_ZMIN) && iz == 0) ||
+                        ((faces & SEM_FACE_ZMAX) && iz == N * prm.nelz);
+    if (masked) {
+      z[g] = 0.0f;
+      continue;
+    }
+    if (!xc) continue;
+    const int ex = min((int)dN.div((uint32_t)ix), prm.nelx - 1);
+    const int ey = min((int)dN.div((uint32_t)iy), prm.nely - 1);
+    const int ez = min((int)dN.div((uint32_t)iz), prm.nelz - 1);
+    const int i = ix - ex * N, j = iy - ey * N, k = iz - ez * N;
+    const int v0 = ex + (prm.nelx + 1) * (ey + (prm.nely + 1) * ez);
+    const int sy = prm.nelx + 1, sz = (prm.nelx + 1) * (prm.nely + 1);
+    const float fx0 = prm.phi[0][i], fx1 = prm.phi[1][i];
+    const float fy0 = prm.phi[0][j], fy1 = prm.phi[1][j];
+    const float fz0 = prm.phi[0][k], fz1 = prm.phi[1][k];
+    const float c00 = fmaf(fx1, xc[v0 + 1], fx0 * xc[v0]);
+    const float c10 = fmaf(fx1, xc[v0 + sy + 1], fx0 * xc[v0 + sy]);
+    const float c01 = fmaf(fx1, xc[v0 + sz + 1], fx0 * xc[v0 + sz]);
+    const float c11 = fmaf(fx1, xc[v0 + sz + sy + 1], fx0 * xc[v0 + sz + sy]);
+    z[g] += fmaf(fz1, fmaf(fy1, c11, fy0 * c01), fz0 * fmaf(fy1, c10, fy0 * c00));
+  }
+}
+
+}  // namespace
+
+void schwarz_apply_global(sem_schwarz* sw, const float* r_g, float* z_g, cudaStream_t s) {
+  sem_handle* h = sw->h;
+  const float* xcp = schwarz_levels(sw, r_g, z_g, s);
+  k_sw_combine_global<<<ew_blocks(h->nG), 256, 0, s>>>(
+      h->nG, z_g, xcp, sw->prm, h->faces, FastDiv((uint32_t)(h->N * h->nelx + 1)),
+      FastDiv((uint32_t)(h->N * h->nely + 1)), FastDiv((uint32_t)h->N));
+  SEM_CHECK_LAUNCH();
+}
+
+void schwarz_apply(sem_schwarz* sw, const double* r, double* z, cudaStream_t s) {
+  sem_handle* h = sw->h;
+  to_global<double>(h, r, sw->rg.ptr, s);
+  const float* xcp = schwarz_levels(sw, sw->rg.ptr, sw->zg.ptr, s);
   const int cg = ew_blocks(h->nL);
   switch (h->P) {
     case 3: k_sw_combine<3><<<cg, 256, 0, s>>>(h->nL, sw->zg.ptr, xcp, z, sw->prm, h->faces); break;

@@ -16,6 +16,7 @@
 namespace sem {
 
 struct GmresWork;                    // gmres.cu
+struct GmresWorkF;                   // gmres.cu
 struct HostPipe;                     // apply.cu
 
 constexpr int kMaxN = 10;            // highest supported polynomial order
@@ -185,6 +186,7 @@ struct sem_handle {
   // host staging for sem_apply_host
   sem::DevBuf<double> stage_in, stage_out;
   std::shared_ptr<sem::GmresWork> gmres;    // GMRES workspace, kept between solves
+  std::shared_ptr<sem::GmresWorkF> gmres32; // mixed-precision GMRES workspace
   std::shared_ptr<sem::HostPipe> host_pipe; // streams of the pipelined sem_apply_host
   double dinv_h1 = NAN, dinv_h2 = NAN;
   const void* dinv_h1f = nullptr;
@@ -286,6 +288,8 @@ void residual_f64(sem_handle* h, const double* b, const double* x, double h1, do
 
 // ---- schwarz.cu: z = M^-1 r (FP64 L-vectors)
 void schwarz_apply(sem_schwarz* sw, const double* r, double* z, cudaStream_t s);
+// z_g = M^-1 r_g on FP32 global vectors (z_g padded like r_g; padding stays zero)
+void schwarz_apply_global(sem_schwarz* sw, const float* r_g, float* z_g, cudaStream_t s);
 sem_handle* schwarz_handle(const sem_schwarz* sw);
 
 // ---- grad.cu

@@ -156,3 +156,28 @@ def test_gmres_zero_rhs_and_errors():
     other = sem.sem_schwarz_create(h2)
     with pytest.raises(sem.SemError):
         sem.sem_gmres_solve(h, b, x, precond=other)
+
+
+@pytest.mark.parametrize("nel,N,h2,faces", [((3, 3, 2), 5, 0.0, mesh.ALL_FACES),
+                                            ((4, 3, 3), 7, 1.0, mesh.ALL_FACES),
+                                            ((5, 2, 3), 9, 0.2, mesh.FACE_XMIN | mesh.FACE_ZMAX),
+                                            ((4, 4, 4), 3, 0.0, mesh.ALL_FACES)])
+def test_gmres_mixed_precision(nel, N, h2, faces):
+    """FP32 inner FGMRES on global vectors with the Schwarz preconditioner inside
+    FP64 refinement: the oracle's FP64 residual reaches the tolerance and the
+    solution matches the FP64 GMRES solution."""
+    h, o, _ = make(nel, N, faces, h2=h2)
+    b = o.rhs(si.eval_fourier(si.fourier_modes(4200 + N), o.x, o.y, o.z))
+    bd = torch.from_numpy(b).to(DEV).view(-1)
+    pre = sem.sem_schwarz_create(h, 1.0, h2)
+    x = torch.empty_like(bd)
+    info = sem.sem_gmres_solve(h, bd, x, h2=h2, tol=1e-9, restart=10, precond=pre,
+                               precision=sem.SEM_SOLVE_MIXED)
+    assert info["status"] == "SEM_OK", info
+    assert info["outer_iters"] >= 1
+    res = o.residual(x.cpu().numpy().reshape(o.shape), b, 1.0, h2)
+    assert res <= 1.0001e-9
+    assert abs(res - info["rel_res"]) < 1e-12
+    x64 = torch.empty_like(bd)
+    sem.sem_gmres_solve(h, bd, x64, h2=h2, tol=1e-9, restart=10, precond=pre)
+    assert rel_inf(x.cpu().numpy(), x64.cpu().numpy()) < 1e-6
