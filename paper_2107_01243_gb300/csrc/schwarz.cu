@@ -31,7 +31,12 @@
 namespace sem {
 namespace {
 
-constexpr int kSwThreads = 128;
+// threads of the local-solve CTA: one per z-column of the grown box, whole warps
+template <int PE>
+struct SwCfg {
+  static constexpr int THREADS = PE * PE <= 128 ? 128 : (PE * PE + 31) / 32 * 32;
+  static constexpr int MINB = PE * PE <= 128 ? 4 : 2;
+};
 constexpr int kNbr = 0, kDir = 1, kFree = 2;
 
 // ------------------------------------------------------------------ host setup
@@ -169,7 +174,7 @@ __device__ __forceinline__ float dot_row(const float* __restrict__ row, const fl
 // The coarse restriction is taken from the gathered columns of the element's
 // own points (a, b, c in 1 .. P).
 template <int PE>
-__global__ void __launch_bounds__(kSwThreads, 4)
+__global__ void __launch_bounds__(SwCfg<PE>::THREADS, SwCfg<PE>::MINB)
 schwarz_local_kernel(const float* __restrict__ rg, float* __restrict__ zg,
                      float* __restrict__ rc, const float* __restrict__ tab_g, SwParams prm,
                      int E) {
@@ -177,7 +182,8 @@ schwarz_local_kernel(const float* __restrict__ rg, float* __restrict__ zg,
   constexpr int R = L::R, P = PE - 2, N = PE - 3;
   __shared__ __align__(16) float tab[L::ALL];
   __shared__ __align__(16) float box[PE * PE * R];
-  __shared__ float red[8][kSwThreads / 32];
+  constexpr int NW = SwCfg<PE>::THREADS / 32;
+  __shared__ float red[8][NW];
   for (int q = threadIdx.x; q < L::ALL; q += blockDim.x) tab[q] = tab_g[q];
   __syncthreads();
   const int tid = threadIdx.x;
@@ -234,7 +240,7 @@ schwarz_local_kernel(const float* __restrict__ rg, float* __restrict__ zg,
       __syncthreads();
       if (tid < 8) {
         float t = 0.0f;
-        for (int w = 0; w < kSwThreads / 32; ++w) t += red[tid][w];
+        for (int w = 0; w < NW; ++w) t += red[tid][w];
         const int v = tid;
         const long long vi = (long long)(ex + (v & 1)) +
                              (long long)(prm.nelx + 1) *
@@ -492,13 +498,14 @@ template <int PE>
 void launch_local(sem_schwarz* sw, const float* rg, float* zg, cudaStream_t s) {
   const sem_handle* h = sw->h;
   auto kern = schwarz_local_kernel<PE>;
+  constexpr int T = SwCfg<PE>::THREADS;
   static int occ = 0;
   if (!occ) {
-    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kSwThreads, 0));
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, 0));
     if (occ < 1) occ = 1;
   }
   const int grid = (int)std::min<int64_t>(h->E, (int64_t)occ * kNumSMs);
-  kern<<<grid, kSwThreads, 0, s>>>(rg, zg, sw->rc.ptr, sw->tab.ptr, sw->prm, (int)h->E);
+  kern<<<grid, T, 0, s>>>(rg, zg, sw->rc.ptr, sw->tab.ptr, sw->prm, (int)h->E);
   SEM_CHECK_LAUNCH();
 }
 

@@ -24,7 +24,8 @@ L = (TWO_PI,) * 3
 CASES = [((3, 2, 2), 3, mesh.ALL_FACES), ((2, 3, 2), 5, mesh.ALL_FACES),
          ((3, 3, 2), 7, mesh.FACE_XMIN | mesh.FACE_YMAX | mesh.FACE_ZMIN), ((1, 1, 1), 7, 63),
          ((4, 1, 2), 9, mesh.ALL_FACES), ((2, 2, 3), 4, 0), ((5, 4, 3), 7, mesh.ALL_FACES),
-         ((2, 1, 1), 2, mesh.FACE_XMIN)]
+         ((2, 1, 1), 2, mesh.FACE_XMIN), ((3, 2, 2), 9, mesh.ALL_FACES),
+         ((2, 2, 2), 10, mesh.FACE_YMIN | mesh.FACE_ZMAX)]
 
 
 def make(nel, N, faces, h1=1.0, h2=0.0, coarse_iters=10):
@@ -103,8 +104,10 @@ def test_schwarz_rejects_bad_arguments():
         sem.sem_schwarz_apply(pre, v, v)
 
 
+# N = 9, 10: grown boxes of 12^2, 13^2 columns (more than 128 threads per CTA)
 SOLVES = [((3, 3, 2), 5, 0.0, mesh.ALL_FACES), ((4, 3, 3), 7, 1.0, mesh.ALL_FACES),
-          ((2, 2, 4), 3, 0.0, mesh.FACE_XMIN | mesh.FACE_ZMAX)]
+          ((2, 2, 4), 3, 0.0, mesh.FACE_XMIN | mesh.FACE_ZMAX),
+          ((5, 2, 3), 9, 0.2, mesh.FACE_XMIN | mesh.FACE_ZMAX)]
 
 
 @pytest.mark.parametrize("nel,N,h2,faces", SOLVES)
