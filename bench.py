@@ -43,6 +43,25 @@ def arm_config(world, n=32 ** 3 * 8 ** 3):
             "parallelism": f"replicas x{world}"}
 
 
+def max_over_ranks(values, device):
+    """Each timing in `values` (ms) replaced by its maximum over the ranks of
+    the default process group (unchanged without one): the slowest replica
+    sets the whole-job rate.  `device` holds the reduction tensor (a CUDA
+    device under NCCL, the CPU under gloo)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(points_per_rank, steps, world, ms):
+    """G points per second over all replicas: every rank processes
+    points_per_rank per step, and the job ends with its slowest rank (ms)."""
+    return world * points_per_rank * steps / (ms / 1e3) / 1e9
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -291,11 +310,8 @@ def main():
     ms = t0.elapsed_time(t1)
     ax_ms = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
     ds_ms = statistics.mean(b.elapsed_time(c) for _, b, c in ev)
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t)
-    value = world * n * K / (ms / 1e3) / 1e9
+    (ms,) = max_over_ranks([ms], dev)
+    value = whole_job_rate(n, K, world, ms)
 
     def split_times(local, finish, warm=3):
         for _ in range(warm):
@@ -339,8 +355,8 @@ def main():
         sem.sem_apply_host(h, u_host, w_host)
     b.record(stream)
     barrier()
-    e2e_ms = a.elapsed_time(b) / Ke
-    e2e = world * n / (e2e_ms / 1e3) / 1e9
+    (e2e_ms,) = max_over_ranks([a.elapsed_time(b)], dev)
+    e2e = whole_job_rate(n, Ke, world, e2e_ms)
 
     hbm, peak_kind = peaks()
     ax_bytes = 64 * n                       # u 8 + w 8 + 6 G x 8 per point
