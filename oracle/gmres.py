@@ -39,8 +39,9 @@ def givens(a, b):
     return a / r, b / r
 
 
-def fgmres(b, matvec, precond, mult, tol=1e-8, m=30, maxit=1000, x0=None):
-    """Solve H x = b; matvec(v) = H v, precond(v) = M^-1 v (L-vectors)."""
+def fgmres(b, matvec, precond, mult, tol=1e-8, m=30, maxit=1000, x0=None, basis=None):
+    """Solve H x = b; matvec(v) = H v, precond(v) = M^-1 v (L-vectors).
+    basis: optional list that receives the Arnoldi vectors V of every cycle."""
     dot = lambda a, c: weighted_dot(a, c, mult)
     x = np.zeros_like(b) if x0 is None else x0.copy()
     bnorm = np.sqrt(dot(b, b))
@@ -88,6 +89,8 @@ def fgmres(b, matvec, precond, mult, tol=1e-8, m=30, maxit=1000, x0=None):
             if abs(g[j + 1]) <= tol * bnorm or total >= maxit or hn == 0.0:
                 break
             V.append(w / hn)
+        if basis is not None:
+            basis.append(list(V))
         y = np.zeros(k)
         for i in range(k - 1, -1, -1):
             y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]

@@ -39,6 +39,40 @@ def test_undeformed_geometric_factors(N):
     assert abs(m["B"].sum() - 12 * h ** 3) < 1e-13
 
 
+def test_deformation_structure():
+    """Structure of the deformed-box reading: the displacement of each
+    coordinate depends only on the other two, and the map commutes with the
+    cyclic permutation of the axes (x, y, z) -> (y, z, x), so on a cube mesh
+    the point with lattice index (ix, iy, iz) lands, permuted, where the point
+    (iy, iz, ix) does."""
+    nel, N, a = 3, 4, 0.1
+    x0, y0, z0 = mesh.box_coords(nel, nel, nel, N, (0, 0, 0), (TWO_PI,) * 3, 0.0)
+    x, y, z = mesh.box_coords(nel, nel, nel, N, (0, 0, 0), (TWO_PI,) * 3, a)
+    dx, dy, dz = x - x0, y - y0, z - z0
+    ix, iy, iz = mesh.lattice_indices(nel, nel, nel, N)
+    n = N * nel + 1
+
+    def on_lattice(f):
+        out = np.full((n, n, n), np.nan)
+        out[iz.ravel(), iy.ravel(), ix.ravel()] = f.ravel()
+        return out                                   # out[iz, iy, ix]
+
+    DX, DY, DZ = on_lattice(dx), on_lattice(dy), on_lattice(dz)
+    assert not np.isnan(DX).any()
+    # dx is constant along x, dy along y, dz along z
+    assert np.abs(DX - DX[:, :, :1]).max() < 1e-15
+    assert np.abs(DY - DY[:, :1, :]).max() < 1e-15
+    assert np.abs(DZ - DZ[:1, :, :]).max() < 1e-15
+    assert np.abs(DX).max() > 0.05 and np.abs(DY).max() > 0.05 and np.abs(DZ).max() > 0.05
+    # cyclic symmetry: dy at lattice (ix, iy, iz) equals dx at (iy, iz, ix), and
+    # so on round the cycle; with arrays indexed [iz, iy, ix] the value at
+    # (iy, iz, ix) is F[ix, iz, iy]
+    cyc = lambda F: np.einsum('abc->bca', F)
+    assert np.abs(DY - cyc(DX)).max() < 1e-15
+    assert np.abs(DZ - cyc(DY)).max() < 1e-15
+    assert np.abs(DX - cyc(DZ)).max() < 1e-15
+
+
 def test_deformed_volume():
     # the sine deformation's det(grad) perturbation terms integrate to zero
     # over a period, so the deformed box keeps the volume (2 pi)^3

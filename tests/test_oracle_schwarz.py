@@ -186,6 +186,24 @@ def test_gmres_minimises_the_residual_over_the_krylov_space():
         assert abs(got - best) <= 1e-7 * best + 1e-14, (k, got, best)
 
 
+@pytest.mark.parametrize("nel,N", [((2, 2, 1), 3), ((2, 2, 2), 4)])
+def test_arnoldi_basis_stays_orthonormal(nel, N):
+    """Classical Gram-Schmidt applied twice keeps the Arnoldi vectors
+    orthonormal in the unique-dof inner product to rounding over a long cycle
+    (32 and 61 vectors, run to 1e-14); a single pass loses orthogonality to
+    about 3e-3 on these problems."""
+    o = OracleProblem(nel, N, length=(TWO_PI,) * 3, deform=0.1)
+    b = o.rhs(si.eval_fourier(si.fourier_modes(99), o.x, o.y, o.z))
+    cycles = []
+    res = gmres.fgmres(b, lambda v: o.matvec(v, 1.0, 0.0), lambda v: v, o.mult, tol=1e-14,
+                       m=1000, maxit=1000, basis=cycles)
+    assert res.status == "ok" and len(cycles) == 1
+    V = cycles[0]
+    assert len(V) >= 30
+    M = np.array([[operator.weighted_dot(a, c, o.mult) for c in V] for a in V])
+    assert np.abs(M - np.eye(len(V))).max() < 1e-13
+
+
 @pytest.mark.parametrize("m", [40, 4])
 def test_fgmres_with_schwarz_reaches_the_solution(m):
     nel, N, h2 = (3, 3, 2), 4, 0.7
