@@ -23,6 +23,10 @@
  *  - Errors: every call returns a sem_status; no exception crosses the ABI.
  *    sem_last_error() gives a thread-local message for the last failure.
  *  - A handle is not thread-safe: one host thread at a time per handle.
+ *  - One CUDA device per process: the first sem_setup binds the device that
+ *    is current then (per-order constant tables and kernel attributes are set
+ *    up once per process); every later call must run with that device
+ *    current.  Run one process per GPU to use several.
  */
 #ifndef SEM_GB300_H
 #define SEM_GB300_H
@@ -130,10 +134,15 @@ typedef struct {
  * Host: GLL nodes/weights, derivative matrix D (§2, Eq. 7-9), global
  * numbering, multiplicity, Dirichlet mask and the gather-scatter segment
  * lists (§3.2).  Device: GLL coordinates, geometric factors G (6 per point)
- * and mass B (§2, Eq. 9) in the precisions named by precision_flags.
- * Synchronises the stream before returning.  *out receives the handle;
- * release it with sem_destroy.  Errors: SEM_ERR_ARG (bad sizes or N, a
- * non-positive Jacobian), SEM_ERR_OOM, SEM_ERR_CUDA.
+ * and mass B (§2, Eq. 9) in the precisions named by precision_flags.  Also
+ * does the once-per-process setup of the kernels the handle's order uses
+ * (constant tables, kernel attributes), so that later calls can be captured
+ * into CUDA graphs from the first one.  Synchronises the stream before
+ * returning (the first handle of an order in a process synchronises the
+ * device).  *out receives the handle; release it with sem_destroy.
+ * Errors: SEM_ERR_ARG (bad sizes or N, a non-positive Jacobian),
+ * SEM_ERR_STATE (the current device is not the one an earlier sem_setup of
+ * this process bound), SEM_ERR_OOM, SEM_ERR_CUDA.
  */
 sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_flags,
                      void* stream, sem_handle** out);
@@ -479,8 +488,8 @@ sem_status sem_dot(sem_handle* h, const double* a, const double* b, double* out,
  * library (128 KiB, held by every GPU that loads the library until exit), so
  * n_L may be at most 67,108,864 local points (SEM_ERR_ARG beyond that).  All
  * calls share the array; calls whose kernels overlap on the GPU race, so
- * order them on one stream.  The first call on each device looks up the
- * array's address; make it before any stream capture.
+ * order them on one stream.  sem_setup looks up the array's address, so a
+ * first call inside a stream capture makes no synchronous call.
  */
 sem_status sem_dot_noalloc(sem_handle* h, const double* a, const double* b, double* out,
                            void* stream);

@@ -329,7 +329,8 @@ static int df_num_sms() {
   return n;
 }
 
-// copies D and its even-odd halves for this order into constant memory (once)
+// copies D and its even-odd halves for this order into constant memory (once
+// per process: the library drives one device, see sem_setup)
 static void df_upload_d(const sem_handle* h) {
   static bool done[kMaxP + 1] = {};
   const int P = h->P, N = P - 1, H = P / 2;
@@ -358,6 +359,10 @@ static void df_upload_d(const sem_handle* h) {
       }
   }
   SEM_CUDA(cudaMemcpyToSymbol(c_df_eo, eo, sizeof(eo), (size_t)P * sizeof(eo)));
+  // a copy from pageable memory may still be in flight when the call returns,
+  // and only the legacy stream is ordered after it: wait once, so that kernels
+  // on non-blocking streams see the tables
+  SEM_CUDA(cudaDeviceSynchronize());
   done[P] = true;
 }
 
@@ -369,13 +374,10 @@ struct DFSlab {
   FuseBox fb;
 };
 
-// returns the grid it launched (the fused operator's later passes need it)
-template <int P, int STAGES, bool FUSE = false>
-static int launch_df_p(const sem_handle* h, const double* u, double* w, double h1, double h2,
-                       const CGState* st, cudaStream_t s, CGState* pwst = nullptr,
-                       const DFSlab* slab = nullptr) {
-  const bool helm = (float)h2 != 0.0f;
-  const size_t smem = df_smem_bytes<P, STAGES>(helm);
+// CTAs per SM of one kernel variant (Poisson or Helmholtz stage size); the
+// first call also sets the variant's shared-memory attributes
+template <int P, int STAGES, bool FUSE>
+static int df_occupancy(bool helm) {
   auto kern = ax_df_kernel<P, STAGES, FUSE>;
   static bool configured = false;
   static int occ[2] = {0, 0};
@@ -388,9 +390,47 @@ static int launch_df_p(const sem_handle* h, const double* u, double* w, double h
   }
   int& o = occ[helm ? 1 : 0];
   if (!o) {
-    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 3 * P * P, smem));
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 3 * P * P,
+                                                           df_smem_bytes<P, STAGES>(helm)));
     if (o < 1) o = 1;
   }
+  return o;
+}
+
+template <int P>
+static void df_prepare_p(const sem_handle* h) {
+  for (int helm = 0; helm < 2; ++helm) {
+    df_occupancy<P, 1, false>(helm != 0);
+    df_occupancy<P, 2, false>(helm != 0);
+    df_occupancy<P, 1, true>(helm != 0);
+    df_occupancy<P, 2, true>(helm != 0);
+  }
+  df_num_sms();
+  df_upload_d(h);
+}
+
+// The once-per-process setup of the double-float kernels (constant tables,
+// kernel attributes, occupancies), run by sem_setup: outside any stream
+// capture, so that a solve captured into a CUDA graph as the first call of a
+// process makes no synchronous copy inside the capture.
+void df_prepare(const sem_handle* h) {
+  switch (h->P) {
+    case 6: df_prepare_p<6>(h); break;
+    case 8: df_prepare_p<8>(h); break;
+    case 10: df_prepare_p<10>(h); break;
+    default: break;
+  }
+}
+
+// returns the grid it launched (the fused operator's later passes need it)
+template <int P, int STAGES, bool FUSE = false>
+static int launch_df_p(const sem_handle* h, const double* u, double* w, double h1, double h2,
+                       const CGState* st, cudaStream_t s, CGState* pwst = nullptr,
+                       const DFSlab* slab = nullptr) {
+  const bool helm = (float)h2 != 0.0f;
+  const size_t smem = df_smem_bytes<P, STAGES>(helm);
+  auto kern = ax_df_kernel<P, STAGES, FUSE>;
+  const int o = df_occupancy<P, STAGES, FUSE>(helm);
   df_upload_d(h);
   DFScal c;
   c.h1h = (float)h1;

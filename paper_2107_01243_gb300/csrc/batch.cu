@@ -593,6 +593,7 @@ static void batch_upload_d(const sem_handle* h) {
   float d[kMaxP * kMaxP] = {};
   for (int q = 0; q < h->P * h->P; ++q) d[q] = (float)h->Dh[q];
   SEM_CUDA(cudaMemcpyToSymbol(c_b32_D, d, sizeof(d), (size_t)h->P * sizeof(d)));
+  SEM_CUDA(cudaDeviceSynchronize());   // the pageable copy is complete for every stream
   done[h->P] = true;
 }
 

@@ -73,6 +73,10 @@ static double* noalloc_scratch() {
   return g_noalloc_addr[dev];
 }
 
+// run by sem_setup, so that a first sem_dot_noalloc inside a stream capture
+// finds the address already resolved
+void noalloc_prepare() { noalloc_scratch(); }
+
 }  // namespace sem
 
 using namespace sem;

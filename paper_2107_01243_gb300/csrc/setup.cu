@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <numeric>
 #include <memory>
 
@@ -348,11 +349,23 @@ using namespace sem;
 
 extern "C" const char* sem_last_error(void) { return g_last_error.c_str(); }
 
+// The library drives one CUDA device per process: per-order constant tables
+// and kernel attributes are set up once.  The first sem_setup binds the
+// device current at that call; a later one on another device is refused.
+static std::atomic<int> g_bound_device{-1};
+
 extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_flags,
                                 void* stream, sem_handle** out) {
   return guarded([&] {
     SEM_REQUIRE(mesh && out, "sem_setup: null mesh or out");
     *out = nullptr;
+    int dev = -1;
+    SEM_CUDA(cudaGetDevice(&dev));
+    int bound = -1;
+    if (!g_bound_device.compare_exchange_strong(bound, dev) && bound != dev)
+      throw Error(SEM_ERR_STATE, "sem_setup: the library drives one CUDA device per process "
+                                 "(bound to device " + std::to_string(bound) + ", current " +
+                                 std::to_string(dev) + ")");
     SEM_REQUIRE(N >= 1 && N <= kMaxN, "sem_setup: N must be in [1, 10]");
     SEM_REQUIRE(mesh->nelx >= 1 && mesh->nely >= 1 && mesh->nelz >= 1,
                 "sem_setup: element counts must be >= 1");
@@ -430,7 +443,9 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
       SEM_CHECK_LAUNCH();
       split_kernel<<<grid_for(nL), 256, 0, s>>>(h->f64.B.ptr, h->bdf.ptr, nL);
       SEM_CHECK_LAUNCH();
+      df_prepare(h.get());
     }
+    noalloc_prepare();
     h->dev_err.alloc(1);
     SEM_CUDA(cudaMemsetAsync(h->dev_err.ptr, 0, sizeof(int), s));
     h->state.alloc(3);
