@@ -23,6 +23,17 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream))
 
 
+def _copy_x0(x, x0, stream):
+    """x <- x0 on torch's current stream, ordered before work on `stream`."""
+    x.copy_(x0)
+    if stream is None:
+        return
+    if isinstance(stream, torch.cuda.Stream):
+        stream.wait_stream(torch.cuda.current_stream())
+    else:                                 # a raw cudaStream_t: wait on the host
+        torch.cuda.current_stream().synchronize()
+
+
 def _dtype_code(t):
     if t.dtype == torch.float64:
         return SEM_F64
@@ -91,6 +102,10 @@ def sem_setup(nel, N, x0=(0.0, 0.0, 0.0), length=(1.0, 1.0, 1.0), deform=0.0,
     if xyz is not None:
         import numpy as np
         keep = np.ascontiguousarray(xyz, dtype=np.float64)
+        n_l = m.nelx * m.nely * m.nelz * (int(N) + 1) ** 3
+        if keep.size != 3 * n_l:       # the library reads exactly 3 n_L host values
+            raise SemError(1, f"xyz must hold 3 x n_L = {3 * n_l} coordinates "
+                              f"(x, y, z L-vectors), got {keep.size}")
         m.xyz_gll = keep.ctypes.data
     out = ctypes.c_void_p()
     check(lib.sem_setup(ctypes.byref(m), int(N), int(precision), _stream(stream),
@@ -199,7 +214,7 @@ def sem_cg_solve(h, b, x, h1=1.0, h2=0.0, h1_field=None, tol=1e-8, maxit=20000,
     pb = h._vec(b, "b", torch.float64)
     px = h._vec(x, "x", torch.float64)
     if x0 is not None:
-        x.copy_(x0)
+        _copy_x0(x, x0, stream)
         o.x0_is_zero = 0
     o.stream = _stream(stream).value
     info = SolveInfo()
@@ -470,7 +485,7 @@ def sem_gmres_solve(h, b, x, h1=1.0, h2=0.0, tol=1e-8, maxit=5000, restart=30, p
     pb = h._vec(b, "b", torch.float64)
     px = h._vec(x, "x", torch.float64)
     if x0 is not None:
-        x.copy_(x0)
+        _copy_x0(x, x0, stream)
         o.x0_is_zero = 0
     o.stream = _stream(stream).value
     info = SolveInfo()

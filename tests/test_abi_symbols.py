@@ -57,3 +57,12 @@ def test_binding_loads_without_gpu(lib_path):
     from paper_2107_01243_gb300 import _lib
     lib = _lib.load()
     assert lib.sem_last_error() == b""
+
+
+def test_user_coordinates_of_the_wrong_size_are_refused_before_the_call(lib_path):
+    """sem_setup reads exactly 3 n_L host coordinates from xyz_gll; the binding
+    refuses any other size before the library could read past the array."""
+    import numpy as np
+    import paper_2107_01243_gb300 as sem
+    with pytest.raises(sem.SemError, match="3 x n_L = 192"):
+        sem.sem_setup((2, 2, 2), 1, xyz=np.zeros(10))

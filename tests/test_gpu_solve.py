@@ -87,6 +87,33 @@ def test_mixed_precision_refinement(nel, N):
     assert rel_inf(xg, ref.x) < 1e-6
 
 
+@pytest.mark.parametrize("precision", [sem.SEM_SOLVE_F64, sem.SEM_SOLVE_MIXED])
+@pytest.mark.parametrize("side_stream", [False, True])
+def test_initial_guess(precision, side_stream):
+    """A solve started from a given x0 (continuous, zero on Dirichlet points):
+    the FP64 iterates follow the oracle's PCG started from the same x0, both
+    precisions reach the tolerance by the oracle's residual, and on a side
+    stream the copy of x0 into x is ordered before the solve (x starts as NaN)."""
+    nel, N, tol = (3, 2, 2), 7, 1e-9
+    h = sem.sem_setup(nel, N, length=(TWO_PI,) * 3, deform=0.1)
+    o = OracleProblem(nel, N, length=(TWO_PI,) * 3, deform=0.1)
+    b_ref = o.rhs(si.eval_fourier(si.fourier_modes(1240), o.x, o.y, o.z))
+    x0 = si.uniform((int(o.gid.max()) + 1,), 1241)[o.gid] * o.mask
+    b, x0d = to_dev(b_ref), to_dev(x0)
+    x = torch.full_like(b, float("nan"))
+    stream = torch.cuda.Stream() if side_stream else None
+    info = sem.sem_cg_solve(h, b, x, tol=tol, precision=precision, x0=x0d, stream=stream)
+    torch.cuda.synchronize()
+    xg = to_np(x, o.shape)
+    assert info["status"] == "SEM_OK", info
+    res = o.residual(xg, b_ref)
+    assert res <= 1.05 * tol and abs(res - info["rel_res"]) < 1e-12
+    if precision == sem.SEM_SOLVE_F64:
+        ref = o.pcg(b_ref, tol=tol, x0=x0)
+        assert abs(info["iters"] - ref.iters) <= 1, (info, ref.iters)
+        assert rel_inf(xg, ref.x) < 1e-7
+
+
 def test_helmholtz_mass_only_converges_in_one_iteration():
     nel, N = (3, 2, 2), 5
     h = sem.sem_setup(nel, N, length=(TWO_PI,) * 3, deform=0.1)
