@@ -14,6 +14,7 @@ oracle timed on the host cores.
                   [--pressure-nel NEL] [--tiles SPEC] [--model-sweep]
 """
 import argparse
+import datetime
 import json
 import math
 import os
@@ -108,24 +109,35 @@ def alu_roof(tiles, ax_ms):
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples (every 50 ms) around the timed region; the summary
+    keeps the samples whose timestamps fall between mark_start() and
+    mark_end() (host times taken after the synchronisations that bracket the
+    region), or all samples if none does."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.t_start = self.t_end = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         time.sleep(0.3)
         return self
+
+    def mark_start(self):
+        self.t_start = time.time()
+
+    def mark_end(self):
+        self.t_end = time.time()
 
     def __exit__(self, *a):
         self.out = ""
@@ -140,24 +152,31 @@ class ClockSampler:
     def summary(self):
         if not getattr(self, "out", ""):
             return None
-        sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []                              # (host time or None, sm, max, reasons)
         for line in self.out.strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax = float(parts[2])
+                sm, smax = float(parts[2]), float(parts[3])
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            rows.append((ts, sm, smax, {n for n, v in zip(names, parts[6:10])
+                                        if v.lower().startswith("active")}))
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        inside = []
+        if self.t_start is not None and self.t_end is not None:
+            inside = [r for r in rows if r[0] is not None and self.t_start <= r[0] <= self.t_end]
+        use = inside or rows
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": use[-1][2],
+                "reasons": sorted(set().union(*(r[3] for r in use))), "samples": len(rows),
+                "samples_in_timed_region": len(inside)}
 
 
 # ---------------------------------------------------------------- oracle timing
@@ -218,7 +237,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
@@ -298,6 +317,7 @@ def main():
     t1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         barrier()
+        clk.mark_start()
         t0.record(stream)
         for s in range(K):
             ev[s][0].record(stream)
@@ -307,6 +327,7 @@ def main():
             ev[s][2].record(stream)
         t1.record(stream)
         barrier()
+        clk.mark_end()
     ms = t0.elapsed_time(t1)
     ax_ms = statistics.mean(a.elapsed_time(b) for a, b, _ in ev)
     ds_ms = statistics.mean(b.elapsed_time(c) for _, b, c in ev)

@@ -25,3 +25,29 @@ def test_reference_arm_line():
     assert line["value"] > 0.0 and line["e2e"]["value"] == line["value"]
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_clock_summary_keeps_the_samples_of_the_timed_region():
+    """nvidia-smi lines (timestamp first) outside [mark_start, mark_end] are
+    dropped; the throttle reasons are those seen inside; without samples in
+    the region every sample counts."""
+    import datetime
+
+    def line(t, sm, thermal="Not Active", cap="Not Active"):
+        ts = datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, 0, {sm}, 2070, 900.0, 0x0, Not Active, {thermal}, Not Active, {cap}"
+
+    t0 = 1_800_000_000.0
+    c = bench.ClockSampler(0)
+    c.out = "\n".join([line(t0 - 0.2, 1100, thermal="Active"), line(t0 + 0.05, 2070),
+                       line(t0 + 0.10, 2040, cap="Active"), line(t0 + 0.15, 2070),
+                       line(t0 + 0.5, 900)])
+    c.t_start, c.t_end = t0, t0 + 0.2
+    s = c.summary()
+    assert s["samples"] == 5 and s["samples_in_timed_region"] == 3
+    assert s["sm_mhz"] == 2070 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"]
+    c.t_start, c.t_end = t0 + 1.0, t0 + 1.01          # no sample inside: all count
+    s = c.summary()
+    assert s["samples_in_timed_region"] == 0 and s["sm_mhz"] == 2040
+    assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
