@@ -418,10 +418,11 @@ sem_status sem_gmres_solve(sem_handle* h, const double* b_L, double* x_L,
  * Batched solves.  sem_batch_create groups n (<= 256) handles, each built with
  * SEM_PREC_F32 and an odd N (even points per direction), into a batch that
  * advances all their solves together: every stage of an FP32 inner CG
- * iteration (Ax, gather-scatter, the vector updates with per-problem dot
- * products) is one kernel launch over all problems, elements of different
- * orders dispatched inside the same persistent Ax kernel, and batches of
- * iterations are captured in a CUDA graph.  Each problem refines in FP64 as
+ * iteration (the operator, the vector updates with per-problem dot products)
+ * is one kernel launch over all problems (the element kernels one persistent
+ * launch per order present), and batches of iterations are captured in a
+ * CUDA graph.  The inner PCG runs on global vectors (as sem_apply_global)
+ * unless a handle asks for L-vectors (sem_set_inner_vectors).  Each problem refines in FP64 as
  * in sem_cg_solve with SEM_SOLVE_MIXED (constant h1, h2 per problem).
  * sem_batch_solve: b_L[p] and x_L[p] are device pointers (host array of n
  * pointers) as for sem_cg_solve on handle p; h1[p], h2[p] the coefficients;

@@ -2,7 +2,13 @@
 // and order N advance together, FP32-inner PCG inside FP64 refinement per
 // problem (the solver of cg.cu, arXiv 2107.01243 §2 end and §4, applied to a
 // batch).  Every stage of an inner CG iteration is one launch over all
-// problems:
+// problems (per order class for the element kernels).  By default (every
+// handle allows global vectors) the inner PCG runs on global vectors:
+//   bglob   per order class, a persistent element kernel that gathers u from
+//           each problem's lattice and adds face values to its w by L2
+//           reductions (batch_glob.cuh), forming <p, H p> at P = 8
+//   bginit, bgpw, bgupdate, bgpupd  per-problem-chunk vector kernels
+// On L-vectors (SEM_INNER_LOCAL on a handle) the stages are:
 //   bax     persistent bulk-copy (TMA) Ax over all elements of the problems of
 //           one order (one launch per order present, each with the tile and
 //           shared-memory stages of its own order)
