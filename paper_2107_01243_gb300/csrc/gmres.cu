@@ -11,6 +11,13 @@
 // The (m+1) x m Hessenberg matrix, its Givens rotations and the residual
 // estimate live on the host (one synchronisation per iteration); x += Z y at
 // the end of a cycle, and each cycle starts from the true residual.
+//
+// Mixed precision (gmres_solve_mixed): FP64 iterative refinement on
+// L-vectors (residual r = b - Hx and update x += d in FP64, as the mixed CG
+// does) around the same flexible GMRES in FP32 on global vectors: the
+// operator of global.cu, the Schwarz preconditioner applied on global
+// vectors, Gram-Schmidt dots accumulated per thread with Kahan compensation
+// in FP32 and across threads in FP64.
 #include <cmath>
 #include <memory>
 #include <vector>
