@@ -8,6 +8,13 @@
 // alpha, beta and the stop flag live on the device (CGState); every kernel
 // returns at once when the flag is set, so a batch of iterations can be
 // captured in a CUDA graph and the host reads the state once per batch.
+//
+// The mixed solve's FP32 inner PCG runs on global (unique-dof) vectors when
+// the handle allows it (glob_iterations: the operator of global.cu and
+// padded float4 vector kernels), else on L-vectors.  The FP64 solve can also
+// run the pipelined recurrences of Ghysels and Vanroose (solve_pipelined,
+// §10 outlook): one fused vector kernel with a single three-value reduction
+// per iteration, and a check of the true residual at the end of each cycle.
 #include <cmath>
 #include <algorithm>
 #include <cstdint>

@@ -1,5 +1,7 @@
 // Handle setup: GLL basis, box topology, gather-scatter lists, coordinates and
-// geometric factors (arXiv 2107.01243 §2, Eq. 7-10; §3.2).
+// geometric factors (arXiv 2107.01243 §2, Eq. 7-10; §3.2).  sem_setup also
+// binds the process to its device and runs the once-per-process kernel setup
+// of the handle's order, outside any stream capture.
 #include <cmath>
 #include <cstring>
 #include <algorithm>
