@@ -46,8 +46,14 @@ void load_file_locked() {
   FILE* f = std::fopen(path, "r");
   if (!f) return;
   int P, b, l, v, d;
-  while (std::fscanf(f, "%d %d %d %d %d", &P, &b, &l, &v, &d) == 5)
+  while (std::fscanf(f, "%d %d %d %d %d", &P, &b, &l, &v, &d) == 5) {
+    // entries outside the tuner's own choices (a damaged or foreign file) are
+    // skipped: the variant indexes the stage tables
+    if (P < 2 || P > kMaxP || b < 0 || b > 62 || (l != 0 && l != 1) || v < 0 || v >= 5 ||
+        (d != 0 && d != 1))
+      continue;
     g_cache[std::make_tuple(P, b)] = Choice{l, v, d};
+  }
   std::fclose(f);
 }
 
