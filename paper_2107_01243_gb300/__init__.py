@@ -16,8 +16,12 @@ from ._lib import (SemError, SEM_F64, SEM_F32, SEM_PREC_F64, SEM_PREC_F32, SEM_S
                    SEM_DSSUM_SEGMENTS, SEM_APPLY_LOCAL, SEM_APPLY_FINISH, SEM_APPLY_FULL,
                    SEM_INNER_AUTO, SEM_INNER_LOCAL, SEM_INNER_GLOBAL, SEM_SCHWARZ_LOCAL,
                    SEM_SCHWARZ_COARSE, SEM_SCHWARZ_BOTH, SEM_CG_STANDARD, SEM_CG_PIPELINED)
+from ._lib import (SEM_FACE_XMIN, SEM_FACE_XMAX, SEM_FACE_YMIN, SEM_FACE_YMAX, SEM_FACE_ZMIN,
+                   SEM_FACE_ZMAX)
 from .api import (Handle, sem_setup, sem_destroy, sem_get_sizes, sem_get_field, sem_ax,
-                  sem_apply, sem_apply_global, sem_to_global, sem_set_inner_vectors, sem_set_cg_variant, sem_dssum, sem_rhs, sem_cg_solve, sem_helmholtz_grad, sem_apply_host, sem_dot, sem_sync,
+                  sem_apply, sem_apply_global, sem_to_global, sem_set_inner_vectors,
+                  sem_set_cg_variant, sem_dssum, sem_rhs, sem_cg_solve, sem_helmholtz_grad,
+                  sem_apply_host, sem_dot, sem_sync,
                   sem_selftest_timeout, sem_set_f64_kernel, sem_set_dssum_kernel,
                   sem_autotune, sem_set_tuning,
                   sem_dot_noalloc, Batch, sem_batch_create, sem_batch_solve,

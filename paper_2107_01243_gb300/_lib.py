@@ -20,6 +20,8 @@ STATUS_NAMES = {0: "SEM_OK", 1: "SEM_ERR_ARG", 2: "SEM_ERR_CUDA", 3: "SEM_ERR_NO
 SEM_F64, SEM_F32 = 0, 1
 SEM_PREC_F64, SEM_PREC_F32 = 1, 2
 SEM_SOLVE_F64, SEM_SOLVE_MIXED = 0, 1
+SEM_FACE_XMIN, SEM_FACE_XMAX, SEM_FACE_YMIN, SEM_FACE_YMAX, SEM_FACE_ZMIN, SEM_FACE_ZMAX = (
+    1, 2, 4, 8, 16, 32)
 SEM_FACE_ALL = 63
 SEM_F64_KERNEL_AUTO, SEM_F64_KERNEL_NATIVE, SEM_F64_KERNEL_DOUBLEFLOAT = 0, 1, 2
 SEM_DSSUM_BOX, SEM_DSSUM_SEGMENTS = 0, 1

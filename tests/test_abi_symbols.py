@@ -66,3 +66,75 @@ def test_user_coordinates_of_the_wrong_size_are_refused_before_the_call(lib_path
     import paper_2107_01243_gb300 as sem
     with pytest.raises(sem.SemError, match="3 x n_L = 192"):
         sem.sem_setup((2, 2, 2), 1, xyz=np.zeros(10))
+
+
+def _header_text():
+    text = open(os.path.join(HEADER_DIR, "sem.h")).read()
+    return re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+
+
+def test_binding_constants_equal_the_header_enums():
+    from paper_2107_01243_gb300 import _lib
+    names = re.findall(r"\b(SEM_[A-Z0-9_]+)\s*=\s*(\d+)", _header_text())
+    assert len(names) > 40
+    for name, value in names:
+        assert getattr(_lib, name) == int(value), name
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    """Offsets and sizes of every struct of the boundary, as gcc lays them
+    out from include/sem.h, equal those of the ctypes mirrors."""
+    import shutil
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_2107_01243_gb300 import _lib
+    structs = {"sem_mesh_desc": _lib.MeshDesc, "sem_solve_opts": _lib.SolveOpts,
+               "sem_solve_info": _lib.SolveInfo, "sem_tuning": _lib.Tuning}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sem.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", HEADER_DIR, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    seen = 0
+    for line in out.splitlines():
+        cname, field, value = line.split()
+        cls = structs[cname]
+        got = ctypes.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
+        assert got == int(value), (cname, field, got, value)
+        seen += 1
+    assert seen == sum(len(c._fields_) + 1 for c in structs.values())
+
+
+def test_binding_signatures_have_the_header_arity():
+    """Every function the binding declares takes as many arguments as its
+    prototype in include/sem.h, with the same pointer / integer / floating
+    kind at each position."""
+    from paper_2107_01243_gb300 import _lib
+    protos = {}
+    for m in re.finditer(r"\b(?:sem_status|void|const char\*)\s+(sem_[a-z0-9_]+)\s*\(([^)]*)\)\s*;",
+                         _header_text()):
+        params = [p.strip() for p in m.group(2).split(",")]
+        protos[m.group(1)] = [] if params == ["void"] else params
+    assert set(_lib.SIGNATURES) == set(protos)          # the binding covers the whole ABI
+
+    def kind_c(p):
+        if "*" in p:
+            return "ptr"
+        return "float" if p.split()[0] in ("double", "float") else "int"
+
+    def kind_ct(t):
+        if t in (ctypes.c_double, ctypes.c_float):
+            return "float"
+        if t in (ctypes.c_int, ctypes.c_int64, ctypes.c_uint32):
+            return "int"
+        return "ptr"
+
+    for name, (_, args) in _lib.SIGNATURES.items():
+        assert len(args) == len(protos[name]), name
+        assert [kind_ct(t) for t in args] == [kind_c(p) for p in protos[name]], name
