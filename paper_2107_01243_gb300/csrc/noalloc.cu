@@ -18,9 +18,9 @@
 //    contents; each call clears the ticket before its kernel runs.  Calls
 //    whose kernels overlap on the GPU (different streams, no ordering) race
 //    on the array and give wrong results: order them on one stream.
-//  * The first call on each device looks up the array's device address with
-//    cudaGetSymbolAddress (with that device current) and caches it; make that
-//    first call before any stream capture.
+//  * sem_setup looks up the array's device address with cudaGetSymbolAddress
+//    (noalloc_prepare) and caches it, so every call, the first included, may
+//    run inside a stream capture.
 #include <mutex>
 
 #include "sem_internal.cuh"
