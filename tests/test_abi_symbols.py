@@ -138,3 +138,13 @@ def test_binding_signatures_have_the_header_arity():
     for name, (_, args) in _lib.SIGNATURES.items():
         assert len(args) == len(protos[name]), name
         assert [kind_ct(t) for t in args] == [kind_c(p) for p in protos[name]], name
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No CPU fallback: without the built library the first call raises."""
+    from paper_2107_01243_gb300 import _lib
+    import paper_2107_01243_gb300 as sem
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "libsem_gb300.so"))
+    with pytest.raises(sem.SemError, match="CUDA library not built"):
+        sem.sem_setup((1, 1, 1), 2)
