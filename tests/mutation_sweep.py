@@ -96,6 +96,13 @@ MUTATIONS = [
     ("oracle.pipecg", "z_recurrence", "z = n + beta * z", "z = m + beta * z"),
     ("oracle.pipecg", "alpha_sign", "alpha = gamma / (delta - beta * gamma / alpha_old)",
      "alpha = gamma / (delta + beta * gamma / alpha_old)"),
+    ("oracle.dense", "barycentric_ratio_inverted", "D[i, j] = (lam[j] / lam[i]) / (xi[i] - xi[j])",
+     "D[i, j] = (lam[i] / lam[j]) / (xi[i] - xi[j])"),
+    ("oracle.dense", "kronecker_axes_swapped", "Dr = np.kron(I, np.kron(I, D1))",
+     "Dr = np.kron(I, np.kron(D1, I))"),
+    ("oracle.dense", "inverse_jacobian_not_transposed", "JinvT = np.linalg.inv(J).T",
+     "JinvT = np.linalg.inv(J)"),
+    ("oracle.dense", "mass_without_detJ", "M[e, q] = W[q] * detJ", "M[e, q] = W[q]"),
     ("oracle.schwarz", "grown_points_reversed", "    idx = np.arange(N - 1, 2 * N + 2)",
      "    idx = np.arange(N - 1, 2 * N + 2)[::-1]"),
     ("oracle.schwarz", "dirichlet_point_kept", "            keep[1] = False", "            pass"),
