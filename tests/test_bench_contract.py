@@ -51,3 +51,19 @@ def test_clock_summary_keeps_the_samples_of_the_timed_region():
     s = c.summary()
     assert s["samples_in_timed_region"] == 0 and s["sm_mhz"] == 2040
     assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_issue_roof_arithmetic():
+    """The alu object of the bench line: ncu's warp instructions per launch of
+    the fused FP64 element kernel over its CUDA-event time, against 152 SMs x
+    4 schedulers x 2.07 GHz (a GB300 run: 0.35244 ms -> 0.680 of the roof)."""
+    tiles = {"f64_stages": 1}
+    assert bench.ax_kernel_name(tiles) == "ax_df_kernel<8, 1, 1>"
+    assert bench.ax_traffic(tiles) == 1_064_131_328
+    roof = bench.alu_roof(tiles, 0.3524431988596916)
+    assert roof["peak"] == 152 * 4 * 2.07e9
+    assert abs(roof["frac"] - 301_503_392 / 0.3524431988596916e-3 / roof["peak"]) < 1e-12
+    assert abs(roof["frac"] - 0.6797) < 1e-3
+    # a kernel variant no ncu capture covers reports no traffic and no roof
+    assert bench.ax_traffic({"f64_stages": 2}) is None
+    assert bench.alu_roof({"f64_stages": 2}, 0.3) is None
