@@ -318,7 +318,7 @@ using namespace sem;
 
 extern "C" sem_status sem_apply(sem_handle* h, const void* u_L, void* w_L, double h1, double h2,
                                 const void* h1_field, int dtype, int phase, void* stream) {
-  return guarded([&] {
+  return guarded("sem_apply", [&] {
     SEM_REQUIRE(h && u_L && w_L, "sem_apply: null argument");
     SEM_REQUIRE(phase == SEM_APPLY_FULL || phase == SEM_APPLY_LOCAL || phase == SEM_APPLY_FINISH,
                 "sem_apply: phase must be SEM_APPLY_FULL, _LOCAL or _FINISH");

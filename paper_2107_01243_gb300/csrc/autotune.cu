@@ -91,7 +91,7 @@ float time_calls(F fn, cudaStream_t s, int reps) {
 using namespace sem;
 
 extern "C" sem_status sem_autotune(sem_handle* h, void* stream, sem_tuning* out) {
-  return guarded([&] {
+  return guarded("sem_autotune", [&] {
     SEM_REQUIRE(h, "sem_autotune: null handle");
     cudaStream_t s = (cudaStream_t)stream;
     const int b = ebucket(h->E);
@@ -166,7 +166,7 @@ extern "C" sem_status sem_autotune(sem_handle* h, void* stream, sem_tuning* out)
 }
 
 extern "C" sem_status sem_set_tuning(sem_handle* h, const sem_tuning* t) {
-  return guarded([&] {
+  return guarded("sem_set_tuning", [&] {
     SEM_REQUIRE(h && t, "sem_set_tuning: null argument");
     SEM_REQUIRE(t->ax32_kernel == 0 || t->ax32_kernel == 1, "sem_set_tuning: bad ax32_kernel");
     SEM_REQUIRE(t->f64_stages == 1 || t->f64_stages == 2, "sem_set_tuning: bad f64_stages");

@@ -200,7 +200,7 @@ using namespace sem;
 
 extern "C" sem_status sem_ax(sem_handle* h, const void* u_L, void* w_L, double h1, double h2,
                              const void* h1_field, int dtype, void* stream) {
-  return guarded([&] {
+  return guarded("sem_ax", [&] {
     SEM_REQUIRE(h && u_L && w_L, "sem_ax: null handle or vector");
     SEM_REQUIRE(u_L != w_L, "sem_ax: u_L and w_L must be distinct");
     cudaStream_t s = (cudaStream_t)stream;

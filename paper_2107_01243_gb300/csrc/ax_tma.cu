@@ -291,7 +291,7 @@ using namespace sem;
 
 extern "C" sem_status sem_selftest_timeout(sem_handle* h, double timeout_ms, void* stream) {
   sem_status result = SEM_OK;
-  sem_status st = guarded([&] {
+  sem_status st = guarded("sem_selftest_timeout", [&] {
     SEM_REQUIRE(h, "sem_selftest_timeout: null handle");
     SEM_REQUIRE(timeout_ms > 0 && timeout_ms <= 2000, "sem_selftest_timeout: timeout in (0, 2000] ms");
     SEM_REQUIRE(h->f32.G.ptr, "sem_selftest_timeout: needs FP32 geometry");

@@ -758,7 +758,7 @@ static void batch_iteration(sem_batch* bt, cudaStream_t s) {
 }  // namespace sem
 
 extern "C" sem_status sem_batch_create(sem_handle* const* handles, int n, sem_batch** out) {
-  return guarded([&] {
+  return guarded("sem_batch_create", [&] {
     SEM_REQUIRE(handles && out && n >= 1 && n <= kMaxBatch, "sem_batch_create: bad arguments");
     *out = nullptr;
     std::unique_ptr<sem_batch> bt(new sem_batch());
@@ -943,7 +943,7 @@ extern "C" sem_status sem_batch_create(sem_handle* const* handles, int n, sem_ba
 }
 
 extern "C" sem_status sem_batch_destroy(sem_batch* bt) {
-  return guarded([&] {
+  return guarded("sem_batch_destroy", [&] {
     if (!bt) return;
     cudaDeviceSynchronize();
     delete bt;
@@ -953,7 +953,7 @@ extern "C" sem_status sem_batch_destroy(sem_batch* bt) {
 extern "C" sem_status sem_batch_solve(sem_batch* bt, const double* const* b_L,
                                       double* const* x_L, const double* h1, const double* h2,
                                       const sem_solve_opts* opts, sem_solve_info* infos) {
-  return guarded([&] {
+  return guarded("sem_batch_solve", [&] {
     SEM_REQUIRE(bt && b_L && x_L && h1 && h2, "sem_batch_solve: null argument");
     sem_solve_opts o;
     if (opts) o = *opts; else sem_solve_opts_default(&o);

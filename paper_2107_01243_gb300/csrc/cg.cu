@@ -1071,7 +1071,7 @@ extern "C" void sem_solve_opts_default(sem_solve_opts* o) {
 extern "C" sem_status sem_cg_solve(sem_handle* h, const double* b_L, double* x_L,
                                    const sem_solve_opts* opts, sem_solve_info* info) {
   sem_solve_info local{};
-  sem_status st = guarded([&] {
+  sem_status st = guarded("sem_cg_solve", [&] {
     SEM_REQUIRE(h && b_L && x_L, "sem_cg_solve: null handle or vector");
     sem_solve_opts o;
     if (opts) o = *opts; else sem_solve_opts_default(&o);
@@ -1100,7 +1100,7 @@ extern "C" sem_status sem_cg_solve(sem_handle* h, const double* b_L, double* x_L
 }
 
 extern "C" sem_status sem_set_cg_variant(sem_handle* h, int kind) {
-  return guarded([&] {
+  return guarded("sem_set_cg_variant", [&] {
     SEM_REQUIRE(h, "sem_set_cg_variant: null handle");
     SEM_REQUIRE(kind == SEM_CG_STANDARD || kind == SEM_CG_PIPELINED,
                 "sem_set_cg_variant: unknown kind");
@@ -1109,7 +1109,7 @@ extern "C" sem_status sem_set_cg_variant(sem_handle* h, int kind) {
 }
 
 extern "C" sem_status sem_set_inner_vectors(sem_handle* h, int kind) {
-  return guarded([&] {
+  return guarded("sem_set_inner_vectors", [&] {
     SEM_REQUIRE(h, "sem_set_inner_vectors: null handle");
     SEM_REQUIRE(kind == SEM_INNER_AUTO || kind == SEM_INNER_LOCAL || kind == SEM_INNER_GLOBAL,
                 "sem_set_inner_vectors: unknown kind");
@@ -1118,7 +1118,7 @@ extern "C" sem_status sem_set_inner_vectors(sem_handle* h, int kind) {
 }
 
 extern "C" sem_status sem_rhs(sem_handle* h, const double* f_L, double* b_L, void* stream) {
-  return guarded([&] {
+  return guarded("sem_rhs", [&] {
     SEM_REQUIRE(h && f_L && b_L, "sem_rhs: null argument");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = h->nL;
@@ -1130,7 +1130,7 @@ extern "C" sem_status sem_rhs(sem_handle* h, const double* f_L, double* b_L, voi
 
 extern "C" sem_status sem_dot(sem_handle* h, const double* a, const double* b, double* out,
                               void* stream) {
-  return guarded([&] {
+  return guarded("sem_dot", [&] {
     SEM_REQUIRE(h && a && b && out, "sem_dot: null argument");
     cudaStream_t s = (cudaStream_t)stream;
     k_wdot<<<kRedBlocks, kRedThreads, 0, s>>>(h->nL, a, b, h->imult.ptr, out,
@@ -1142,7 +1142,7 @@ extern "C" sem_status sem_dot(sem_handle* h, const double* a, const double* b, d
 
 extern "C" sem_status sem_apply_host(sem_handle* h, const void* u_host, void* w_host, int dtype,
                                      void* stream) {
-  return guarded([&] {
+  return guarded("sem_apply_host", [&] {
     SEM_REQUIRE(h && u_host && w_host, "sem_apply_host: null argument");
     SEM_REQUIRE(dtype == SEM_F64 || dtype == SEM_F32, "sem_apply_host: bad dtype");
     cudaStream_t s = (cudaStream_t)stream;

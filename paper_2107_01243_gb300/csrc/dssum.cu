@@ -53,7 +53,7 @@ using namespace sem;
 
 extern "C" sem_status sem_dssum(sem_handle* h, void* w_L, int apply_mask, int dtype,
                                 void* stream) {
-  return guarded([&] {
+  return guarded("sem_dssum", [&] {
     SEM_REQUIRE(h && w_L, "sem_dssum: null handle or vector");
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == SEM_F64) launch_dssum<double>(h, (double*)w_L, apply_mask != 0, nullptr, s);
@@ -63,7 +63,7 @@ extern "C" sem_status sem_dssum(sem_handle* h, void* w_L, int apply_mask, int dt
 }
 
 extern "C" sem_status sem_set_dssum_kernel(sem_handle* h, int kind) {
-  return guarded([&] {
+  return guarded("sem_set_dssum_kernel", [&] {
     SEM_REQUIRE(h, "sem_set_dssum_kernel: null handle");
     SEM_REQUIRE(kind == SEM_DSSUM_BOX || kind == SEM_DSSUM_SEGMENTS,
                 "sem_set_dssum_kernel: unknown kind");

@@ -338,7 +338,7 @@ using namespace sem;
 
 extern "C" sem_status sem_apply_global(sem_handle* h, const void* u_g, void* w_g, double h1,
                                        double h2, int dtype, void* stream) {
-  return guarded([&] {
+  return guarded("sem_apply_global", [&] {
     SEM_REQUIRE(h && u_g && w_g, "sem_apply_global: null argument");
     SEM_REQUIRE(u_g != w_g, "sem_apply_global: u and w must not alias");
     SEM_REQUIRE(dtype == SEM_F32, "sem_apply_global: FP32 only");
@@ -353,7 +353,7 @@ extern "C" sem_status sem_apply_global(sem_handle* h, const void* u_g, void* w_g
 
 extern "C" sem_status sem_to_global(sem_handle* h, const void* in_L, void* out_g, int dtype,
                                     void* stream) {
-  return guarded([&] {
+  return guarded("sem_to_global", [&] {
     SEM_REQUIRE(h && in_L && out_g, "sem_to_global: null argument");
     SEM_REQUIRE(dtype == SEM_F32 || dtype == SEM_F64, "sem_to_global: dtype");
     SEM_REQUIRE(h->nL < (1LL << 31), "sem_to_global: needs fewer than 2^31 local points");

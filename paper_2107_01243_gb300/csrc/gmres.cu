@@ -612,7 +612,7 @@ extern "C" sem_status sem_gmres_solve(sem_handle* h, const double* b_L, double* 
                                       const sem_solve_opts* opts, int restart,
                                       sem_schwarz* precond, sem_solve_info* info) {
   sem_solve_info local{};
-  sem_status st = guarded([&] {
+  sem_status st = guarded("sem_gmres_solve", [&] {
     SEM_REQUIRE(h && b_L && x_L, "sem_gmres_solve: null handle or vector");
     sem_solve_opts o;
     if (opts) o = *opts; else sem_solve_opts_default(&o);

@@ -88,7 +88,7 @@ using namespace sem;
 
 extern "C" sem_status sem_helmholtz_grad(sem_handle* h, const double* u_L,
                                          const double* lambda_L, double* g_L, void* stream) {
-  return guarded([&] {
+  return guarded("sem_helmholtz_grad", [&] {
     SEM_REQUIRE(h && u_L && lambda_L && g_L, "sem_helmholtz_grad: null argument");
     launch_grad(h, u_L, lambda_L, g_L, (cudaStream_t)stream);
   });

@@ -83,7 +83,7 @@ using namespace sem;
 
 extern "C" sem_status sem_dot_noalloc(sem_handle* h, const double* a, const double* b,
                                       double* out, void* stream) {
-  return guarded([&] {
+  return guarded("sem_dot_noalloc", [&] {
     SEM_REQUIRE(h && a && b && out, "sem_dot_noalloc: null argument");
     if (h->nL > kNoAllocMaxPoints)
       throw Error(SEM_ERR_ARG, "sem_dot_noalloc: n_L = " + std::to_string(h->nL) +

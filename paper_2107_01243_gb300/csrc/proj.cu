@@ -88,7 +88,7 @@ void orthonormal_add(sem_proj* pr, double* v, double* hv, cudaStream_t s) {
 }  // namespace
 
 extern "C" sem_status sem_proj_create(sem_handle* h, int m, sem_proj** out) {
-  return guarded([&] {
+  return guarded("sem_proj_create", [&] {
     SEM_REQUIRE(h && out, "sem_proj_create: null argument");
     SEM_REQUIRE(m >= 0 && m <= kMaxProj, "sem_proj_create: space size must be in [0, 64]");
     SEM_REQUIRE(h->f64.G.ptr, "sem_proj_create: handle has no FP64 geometry");
@@ -128,21 +128,21 @@ extern "C" sem_status sem_proj_create(sem_handle* h, int m, sem_proj** out) {
 }
 
 extern "C" sem_status sem_proj_size(const sem_proj* pr, int* l) {
-  return guarded([&] {
+  return guarded("sem_proj_size", [&] {
     SEM_REQUIRE(pr && l, "sem_proj_size: null argument");
     *l = pr->l;
   });
 }
 
 extern "C" sem_status sem_proj_reset(sem_proj* pr) {
-  return guarded([&] {
+  return guarded("sem_proj_reset", [&] {
     SEM_REQUIRE(pr, "sem_proj_reset: null argument");
     pr->l = 0;
   });
 }
 
 extern "C" sem_status sem_proj_destroy(sem_proj* pr) {
-  return guarded([&] {
+  return guarded("sem_proj_destroy", [&] {
     if (!pr) return;
     cudaDeviceSynchronize();
     delete pr;
@@ -152,7 +152,7 @@ extern "C" sem_status sem_proj_destroy(sem_proj* pr) {
 extern "C" sem_status sem_proj_solve(sem_proj* pr, const double* b_L, double* x_L,
                                      const sem_solve_opts* opts, sem_solve_info* info) {
   sem_status inner_status = SEM_OK;
-  sem_status st = guarded([&] {
+  sem_status st = guarded("sem_proj_solve", [&] {
     SEM_REQUIRE(pr && b_L && x_L, "sem_proj_solve: null argument");
     sem_solve_opts o;
     if (opts) o = *opts; else sem_solve_opts_default(&o);

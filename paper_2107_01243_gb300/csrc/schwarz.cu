@@ -704,7 +704,7 @@ void schwarz_apply(sem_schwarz* sw, const double* r, double* z, cudaStream_t s) 
 
 extern "C" sem_status sem_schwarz_create(sem_handle* h, double h1, double h2, int levels,
                                          int coarse_iters, void* stream, sem_schwarz** out) {
-  return guarded([&] {
+  return guarded("sem_schwarz_create", [&] {
     SEM_REQUIRE(h && out, "sem_schwarz_create: null argument");
     *out = nullptr;
     SEM_REQUIRE(levels >= 1 && levels <= 3, "sem_schwarz_create: levels must be 1, 2 or 3");
@@ -760,7 +760,7 @@ extern "C" sem_status sem_schwarz_create(sem_handle* h, double h1, double h2, in
 
 extern "C" sem_status sem_schwarz_apply(sem_schwarz* sw, const double* r_L, double* z_L,
                                         void* stream) {
-  return guarded([&] {
+  return guarded("sem_schwarz_apply", [&] {
     SEM_REQUIRE(sw && r_L && z_L, "sem_schwarz_apply: null argument");
     SEM_REQUIRE(r_L != z_L, "sem_schwarz_apply: r and z must not alias");
     schwarz_apply(sw, r_L, z_L, (cudaStream_t)stream);
@@ -768,7 +768,7 @@ extern "C" sem_status sem_schwarz_apply(sem_schwarz* sw, const double* r_L, doub
 }
 
 extern "C" sem_status sem_schwarz_destroy(sem_schwarz* sw) {
-  return guarded([&] {
+  return guarded("sem_schwarz_destroy", [&] {
     if (sw) cudaDeviceSynchronize();
     delete sw;
   });

@@ -3,6 +3,7 @@
 #include <type_traits>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <string>
 #include <vector>
@@ -65,6 +66,23 @@ sem_status guarded(F&& f) {
     set_last_error(e.what());
     return SEM_ERR_CUDA;
   }
+}
+
+// NVTX range around a scope: profilers (Nsight Systems, ncu --nvtx) show
+// which API call issued which kernels.  NVTX 3 is header-only; with no tool
+// attached a range costs a few nanoseconds.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+
+// guarded() inside an NVTX range named after the API call
+template <class F>
+sem_status guarded(const char* name, F&& f) {
+  TraceRange range(name);
+  return guarded(std::forward<F>(f));
 }
 
 // ------------------------------------------------------------------ device buffers

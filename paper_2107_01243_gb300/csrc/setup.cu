@@ -358,7 +358,7 @@ static std::atomic<int> g_bound_device{-1};
 
 extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_flags,
                                 void* stream, sem_handle** out) {
-  return guarded([&] {
+  return guarded("sem_setup", [&] {
     SEM_REQUIRE(mesh && out, "sem_setup: null mesh or out");
     *out = nullptr;
     int dev = -1;
@@ -459,7 +459,7 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
 }
 
 extern "C" sem_status sem_destroy(sem_handle* h) {
-  return guarded([&] {
+  return guarded("sem_destroy", [&] {
     if (!h) return;
     cudaDeviceSynchronize();
     delete h;
@@ -468,7 +468,7 @@ extern "C" sem_status sem_destroy(sem_handle* h) {
 
 extern "C" sem_status sem_get_sizes(const sem_handle* h, int64_t* n_local, int64_t* n_global,
                                     int* N, int64_t* E) {
-  return guarded([&] {
+  return guarded("sem_get_sizes", [&] {
     SEM_REQUIRE(h, "sem_get_sizes: null handle");
     if (n_local) *n_local = h->nL;
     if (n_global) *n_global = h->nG;
@@ -479,7 +479,7 @@ extern "C" sem_status sem_get_sizes(const sem_handle* h, int64_t* n_local, int64
 
 extern "C" sem_status sem_get_field(sem_handle* h, int which, void* dst, int dtype,
                                     void* stream) {
-  return guarded([&] {
+  return guarded("sem_get_field", [&] {
     SEM_REQUIRE(h && dst, "sem_get_field: null handle or dst");
     SEM_REQUIRE(dtype == SEM_F64 || dtype == SEM_F32, "sem_get_field: bad dtype");
     cudaStream_t s = (cudaStream_t)stream;
@@ -538,7 +538,7 @@ extern "C" sem_status sem_get_field(sem_handle* h, int which, void* dst, int dty
 }
 
 extern "C" sem_status sem_sync(sem_handle* h, void* stream) {
-  return guarded([&] {
+  return guarded("sem_sync", [&] {
     SEM_REQUIRE(h, "sem_sync: null handle");
     cudaStream_t s = (cudaStream_t)stream;
     int herr = 0;
@@ -553,7 +553,7 @@ extern "C" sem_status sem_sync(sem_handle* h, void* stream) {
 }
 
 extern "C" sem_status sem_set_f64_kernel(sem_handle* h, int kind) {
-  return guarded([&] {
+  return guarded("sem_set_f64_kernel", [&] {
     SEM_REQUIRE(h, "sem_set_f64_kernel: null handle");
     SEM_REQUIRE(kind == SEM_F64_KERNEL_AUTO || kind == SEM_F64_KERNEL_NATIVE ||
                     kind == SEM_F64_KERNEL_DOUBLEFLOAT,
