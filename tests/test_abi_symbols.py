@@ -148,3 +148,38 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(_lib, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "libsem_gb300.so"))
     with pytest.raises(sem.SemError, match="CUDA library not built"):
         sem.sem_setup((1, 1, 1), 2)
+
+
+def test_plain_c_client_links_and_calls_host_entry_points(tmp_path, lib_path):
+    """The library is usable from C alone (no Python, no torch): a C program
+    compiled against include/sem.h links libsem_gb300.so, reads the solver
+    defaults and gets SEM_ERR_ARG with a message for a null mesh (both host
+    paths: no GPU needed)."""
+    import shutil
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "client.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "sem.h"
+int main(void) {
+  sem_solve_opts o;
+  sem_solve_opts_default(&o);
+  printf("%g %d %d %d %d %g %d\n", o.tol, o.maxit, o.check_every, o.use_graph, o.x0_is_zero,
+         o.inner_tol, o.max_outer);
+  sem_handle* h = (sem_handle*)1;
+  sem_status st = sem_setup(NULL, 7, SEM_PREC_F64, NULL, &h);
+  printf("%d %d [%s]\n", (int)st, h == (sem_handle*)1, sem_last_error());
+  return 0;
+}
+''')
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(lib_path)
+    subprocess.run(["gcc", "-std=c11", "-I", HEADER_DIR, str(src), "-L", libdir, "-lsem_gb300",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    tol, maxit, every, graph, x0z, itol, mouter = out[0].split()
+    assert (float(tol), int(maxit), int(every), int(graph), int(x0z)) == (1e-8, 20000, 16, 1, 1)
+    assert (float(itol), int(mouter)) == (1e-4, 30)
+    st, untouched, msg = out[1].split(" ", 2)
+    assert int(st) == 1 and "null mesh" in msg          # SEM_ERR_ARG, out not written
