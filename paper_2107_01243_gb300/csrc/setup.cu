@@ -361,13 +361,6 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
   return guarded("sem_setup", [&] {
     SEM_REQUIRE(mesh && out, "sem_setup: null mesh or out");
     *out = nullptr;
-    int dev = -1;
-    SEM_CUDA(cudaGetDevice(&dev));
-    int bound = -1;
-    if (!g_bound_device.compare_exchange_strong(bound, dev) && bound != dev)
-      throw Error(SEM_ERR_STATE, "sem_setup: the library drives one CUDA device per process "
-                                 "(bound to device " + std::to_string(bound) + ", current " +
-                                 std::to_string(dev) + ")");
     SEM_REQUIRE(N >= 1 && N <= kMaxN, "sem_setup: N must be in [1, 10]");
     SEM_REQUIRE(mesh->nelx >= 1 && mesh->nely >= 1 && mesh->nelz >= 1,
                 "sem_setup: element counts must be >= 1");
@@ -375,6 +368,17 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
                 "sem_setup: precision_flags selects no precision");
     SEM_REQUIRE(mesh->len[0] > 0 && mesh->len[1] > 0 && mesh->len[2] > 0,
                 "sem_setup: box lengths must be positive");
+    SEM_REQUIRE((double)mesh->nelx * mesh->nely * mesh->nelz * (N + 1) * (N + 1) * (N + 1) <
+                    (double)INT32_MAX,
+                "sem_setup: more than 2^31 local points");
+    // arguments first (no CUDA call above this line), then the device
+    int dev = -1;
+    SEM_CUDA(cudaGetDevice(&dev));
+    int bound = -1;
+    if (!g_bound_device.compare_exchange_strong(bound, dev) && bound != dev)
+      throw Error(SEM_ERR_STATE, "sem_setup: the library drives one CUDA device per process "
+                                 "(bound to device " + std::to_string(bound) + ", current " +
+                                 std::to_string(dev) + ")");
     cudaStream_t s = (cudaStream_t)stream;
     std::unique_ptr<sem_handle> h(new sem_handle());
     h->N = N;

@@ -183,3 +183,23 @@ int main(void) {
     assert (float(itol), int(mouter)) == (1e-4, 30)
     st, untouched, msg = out[1].split(" ", 2)
     assert int(st) == 1 and "null mesh" in msg          # SEM_ERR_ARG, out not written
+
+
+def test_setup_arguments_are_checked_before_any_cuda_call(lib_path):
+    """sem_setup validates its arguments before it touches the device, so the
+    error codes of the boundary are checked here without a GPU; a valid call
+    on a machine without one fails loudly (no CPU fallback)."""
+    import torch
+    import paper_2107_01243_gb300 as sem
+    bad = [dict(nel=(2, 2, 2), N=11), dict(nel=(2, 2, 2), N=0), dict(nel=(0, 1, 1), N=3),
+           dict(nel=(1, 1, 1), N=3, length=(1.0, 0.0, 1.0)),
+           dict(nel=(1, 1, 1), N=3, precision=0), dict(nel=(1000, 1000, 1000), N=7)]
+    for kw in bad:
+        nel, N = kw.pop("nel"), kw.pop("N")
+        with pytest.raises(sem.SemError) as e:
+            sem.sem_setup(nel, N, stream=0, **kw)       # stream 0: no torch.cuda call
+        assert e.value.status == 1, (nel, N, kw, str(e.value))
+    if not torch.cuda.is_available():
+        with pytest.raises(sem.SemError) as e:
+            sem.sem_setup((1, 1, 1), 3, stream=0)
+        assert e.value.status == 2                   # SEM_ERR_CUDA: no device, no fallback
