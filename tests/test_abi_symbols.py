@@ -203,3 +203,40 @@ def test_setup_arguments_are_checked_before_any_cuda_call(lib_path):
         with pytest.raises(sem.SemError) as e:
             sem.sem_setup((1, 1, 1), 3, stream=0)
         assert e.value.status == 2                   # SEM_ERR_CUDA: no device, no fallback
+
+
+NULL_PROBE = r"""
+import ctypes, sys
+sys.path.insert(0, sys.argv[1])
+from paper_2107_01243_gb300 import _lib
+lib = _lib.load()
+for name, (res, args) in _lib.SIGNATURES.items():
+    if name == "sem_last_error":
+        continue
+    vals = [1.0 if t in (ctypes.c_double, ctypes.c_float) else
+            1 if t in (ctypes.c_int, ctypes.c_int64, ctypes.c_uint32) else None for t in args]
+    print(name, getattr(lib, name)(*vals), flush=True)
+"""
+
+
+def test_every_entry_point_rejects_null_pointers(lib_path):
+    """Every call, given null pointers (and unit scalars), returns an error
+    status without touching the device or crashing; the destroy calls accept
+    NULL as a no-op."""
+    import sys
+    out = subprocess.run([sys.executable, "-c", NULL_PROBE, ROOT], capture_output=True,
+                         text=True, timeout=120)
+    assert out.returncode == 0, out.stderr[-2000:]
+    seen = {}
+    for line in out.stdout.splitlines():
+        name, st = line.split()
+        seen[name] = st
+    from paper_2107_01243_gb300 import _lib
+    assert set(seen) == set(_lib.SIGNATURES) - {"sem_last_error"}
+    for name, st in seen.items():
+        if name.endswith("_destroy"):
+            assert st == "0", name
+        elif name == "sem_solve_opts_default":
+            assert st == "None"
+        else:
+            assert st == "1", (name, st)                 # SEM_ERR_ARG
