@@ -200,8 +200,18 @@ sem_status sem_ax(sem_handle* h, const void* u_L, void* w_L, double h1, double h
  * aligned vectors) keeps FP64 inputs and outputs, stores G and B as float
  * pairs (8 bytes per value) and evaluates every sum with error-free float
  * transformations; its error against FP64 is about 1e-14 relative to the
- * largest |w|.  SEM_F64_KERNEL_NATIVE forces IEEE FP64 arithmetic.  Returns
- * SEM_ERR_ARG for an unknown kind.
+ * largest |w| of an element.  Range: the operator is linear, so the kernel
+ * scales by exact powers of two to keep every intermediate inside FP32's
+ * exponent range, and undoes the scaling on the FP64 result.  G and B of an
+ * element whose largest magnitude lies outside [2^-16, 2^16), and h1 or h2
+ * outside that range, are normalised at setup or per call; an element whose
+ * largest |u| lies outside [2^-60, 2^76) (including subnormal-only elements)
+ * is rescaled by its own maximum in the kernel.  So every finite FP64 input
+ * keeps the stated accuracy, up to FP64's own overflow and underflow of the
+ * result.  An element whose u holds an Inf or a NaN gives NaN at all of its
+ * points (the native kernel propagates them point by point instead).
+ * SEM_F64_KERNEL_NATIVE forces IEEE FP64 arithmetic.  Returns SEM_ERR_ARG
+ * for an unknown kind.
  */
 sem_status sem_set_f64_kernel(sem_handle* h, int kind);
 

@@ -36,8 +36,11 @@ __constant__ float c_df_dl[kMaxP + 1][kMaxP * kMaxP];
 constexpr int kMaxH = kMaxP / 2 + 1;
 __constant__ float c_df_eo[kMaxP + 1][2][2][2][kMaxH * kMaxH];
 
+// h1 = m1 2^t1, h2 = m2 2^t2 with the mantissas as pairs (t = 0 while
+// |h| lies in [2^-16, 2^16), see df.cuh)
 struct DFScal {
   float h1h, h1l, h2h, h2l;
+  int t1, t2;
 };
 
 // Shared-memory layout of one element's pairs.  P = 8: unpadded planes of 64
@@ -121,21 +124,33 @@ __device__ __forceinline__ void dot3_df(float2 g0, float2 g1, float2 g2, float2 
 // FUSE: the CTA walks segments of kFuseSeg consecutive elements and writes
 // the fused output (FusedStore: mask, x-neighbour pairs of the segment summed
 // in the CTA) for the assembled operator of apply.cu.
+//
+// Range (df.cuh): esc[e] holds the element's power-of-two exponents of G and
+// B (bits 0-15 and 16-31, signed; the float pairs hold G 2^-sG and B 2^-sB).
+// Each warp takes the largest magnitude key of its u values; the CTA barrier
+// after the conversion also tells whether some warp saw a key outside
+// [2^-60, 2^76).  Then (rarely) the whole CTA reads the element maximum and
+// either rescales u by 2^-kU, kU = floor(log2 max |u_e|), or, for an Inf or
+// NaN in u_e, marks the element, whose outputs are then all NaN.  Thread 0
+// combines the exponents into the element's coefficients c1, c2 (both
+// <= 2 in magnitude after scaling, or h1, h2 themselves in the common case)
+// and the output exponent, by which the FP64 result is multiplied.
 template <int P, int STAGES, bool FUSE>
 __global__ void __launch_bounds__(3 * P * P, P == 8 ? 5 : 1)     // P = 8: five CTAs per SM
 ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2* __restrict__ G,
-             const float2* __restrict__ B, DFScal C, int E, const CGState* __restrict__ st,
-             int* __restrict__ err, uint64_t timeout_ns, FuseBox fb, CGState* __restrict__ pwst,
-             double* __restrict__ partials) {
+             const float2* __restrict__ B, const int* __restrict__ esc, DFScal C, int E,
+             const CGState* __restrict__ st, int* __restrict__ err, uint64_t timeout_ns,
+             FuseBox fb, CGState* __restrict__ pwst, double* __restrict__ partials) {
   using L = DFLayout<P>;
   constexpr int P2 = P * P, P3 = P2 * P, NT = 3 * P2;
+  constexpr int NW = (NT + 31) / 32;
+  constexpr unsigned LASTMASK = (NT % 32) ? ((1u << (NT % 32)) - 1u) : 0xffffffffu;
   constexpr uint32_t UB = P3 * sizeof(double), GB = 6 * P3 * sizeof(float2),
                      BB = P3 * sizeof(float2);
   if (st && st->done) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   const bool helm = (C.h2h != 0.0f);
-  const bool scale1 = !(C.h1h == 1.0f && C.h1l == 0.0f);
   const uint32_t SB = UB + GB + (helm ? BB : 0);          // stage bytes
   unsigned char* stage0 = smem_raw + 128;
   float2* U = reinterpret_cast<float2*>(stage0 + STAGES * SB);
@@ -143,6 +158,8 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
   const int tid = threadIdx.x;
   const int g = tid / P2, lam = tid % P2;
   const int c1 = lam % P, c2 = lam / P;
+  const int warp = tid >> 5;
+  const unsigned wmask = (warp == NW - 1) ? LASTMASK : 0xffffffffu;
   // line of direction g: r: (j=c1, k=c2); s: (i=c1, k=c2); t: (i=c1, j=c2);
   // its element positions and this thread's point positions, fixed for the kernel
   int loff[P];
@@ -186,9 +203,14 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
 
   BoxWalk bw;                          // thread 0 (FUSE)
   __shared__ unsigned s_fl;            // FusedStore flags of the current element
+  __shared__ unsigned s_key[NW];       // per-warp magnitude keys of u_e
+  __shared__ float4 s_cf;              // the element's c1 (x, y) and c2 (z, w) pairs
+  __shared__ int2 s_ci;                // output exponent; <p, H p> rescaling exponent
   // FUSE with pwst: <p, H p> = sum over local points of p (H_L p) (p continuous
-  // and zero on Dirichlet points), accumulated per thread in pair arithmetic
+  // and zero on Dirichlet points), accumulated per thread in pair arithmetic;
+  // elements with a nonzero scaling exponent are added in FP64 (pw_d)
   float pw_s = 0.0f, pw_e = 0.0f;
+  double pw_d = 0.0;
   int n = 0;
   for (int e = seq.first(); e < E; e = seq.next(e), ++n) {
     const int s = n % STAGES;
@@ -196,31 +218,83 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     const double* su = reinterpret_cast<const double*>(stage0 + s * SB);
     const float2* sg = reinterpret_cast<const float2*>(stage0 + s * SB + UB);
     const float2* sb = reinterpret_cast<const float2*>(stage0 + s * SB + UB + GB);
-    // phase 0: u -> pairs
+    // phase 0: u -> pairs, and the warp's largest magnitude key
+    unsigned key = 0u, lor = 0u;
 #pragma unroll
     for (int m = 0; m < NQ; ++m) {
       const int q = tid + m * NT;
       if (q < P3) {
+        const double x = su[q];
+        const unsigned long long xb = (unsigned long long)__double_as_longlong(x);
+        key = max(key, (unsigned)(xb >> 32) & 0x7FFFFFFFu);
+        lor |= (unsigned)xb;
         float hi, lo;
-        d2df(su[q], hi, lo);
+        d2df(x, hi, lo);
         U[qoff[m]] = make_float2(hi, lo);
       }
     }
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        for (int nn = n; nn < issued; ++nn)
-          mbar_wait_bounded(&bar[nn % STAGES], (uint32_t)(nn / STAGES) & 1u, err, timeout_ns);
+    key |= (lor != 0u) ? 1u : 0u;
+    const unsigned wkey = __reduce_max_sync(wmask, key);
+    if ((tid & 31) == 0) s_key[warp] = wkey;
+    const bool wbad = wkey != 0u && (wkey - kDfKeyLo) >= (kDfKeyHi - kDfKeyLo);
+    int kU = 0;                        // u_e was scaled by 2^-kU
+    bool nanel = false;                // u_e holds an Inf or NaN
+    if (__syncthreads_or(!ok || wbad)) {
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          for (int nn = n; nn < issued; ++nn)
+            mbar_wait_bounded(&bar[nn % STAGES], (uint32_t)(nn / STAGES) & 1u, err, timeout_ns);
+        }
+        break;                         // the reduction below still counts this CTA
       }
-      break;                           // the reduction below still counts this CTA
+      unsigned km = 0u;
+#pragma unroll
+      for (int w2 = 0; w2 < NW; ++w2) km = max(km, s_key[w2]);
+      if (km >= kDfKeyNonFinite) {
+        nanel = true;
+      } else if (km < kDfKeyLo || km >= kDfKeyHi) {
+        kU = df_key_exp(km);           // the same value in every thread
+        const int ka = -kU / 2;
+        const double sa = df_pow2d(ka), sbb = df_pow2d(-kU - ka);
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) {
+          const int q = tid + m * NT;
+          if (q < P3) {
+            float hi, lo;
+            d2df(su[q] * sa * sbb, hi, lo);
+            U[qoff[m]] = make_float2(hi, lo);
+          }
+        }
+        __syncthreads();
+      }
     }
-    if (FUSE && tid == 0) {            // box position of e, read back in the output phase
-      if (e % kFuseSeg == 0) bw.start(e, fb); else bw.step(fb);
-      s_fl = fused_flags(e, bw, fb);
+    if (tid == 0) {
+      if (FUSE) {                      // box position of e, read back in the output phase
+        if (e % kFuseSeg == 0) bw.start(e, fb); else bw.step(fb);
+        s_fl = fused_flags(e, bw, fb);
+      }
+      // the element's coefficients and exponents
+      const int sw = esc[e];
+      const int a1 = (int)(short)(sw & 0xFFFF) + C.t1;
+      const int a2 = helm ? (sw >> 16) + C.t2 : a1;
+      const int unit = max(a1, a2);
+      s_cf = make_float4(df_scale_down(C.h1h, a1 - unit), df_scale_down(C.h1l, a1 - unit),
+                         df_scale_down(C.h2h, a2 - unit), df_scale_down(C.h2l, a2 - unit));
+      int kE = 0;
+      if (FUSE && pwst && kU == 0 && !nanel) {
+        unsigned km = 0u;
+#pragma unroll
+        for (int w2 = 0; w2 < NW; ++w2) km = max(km, s_key[w2]);
+        if (km != 0u && (km < kDfPwLo || km >= kDfPwHi)) kE = df_key_exp(km);
+      }
+      s_ci = make_int2(unit + kU, kE);
     }
     // forward derivatives: group g differentiates along direction g
     line_task<P, false>(U, myR, loff);
     __syncthreads();
-    // geometric factors at every point: (WR, WS, WT) = h1 G (UR, US, UT), in place
+    // geometric factors at every point: (WR, WS, WT) = c1 G (UR, US, UT), in place
+    const float4 cf = s_cf;
+    const bool scale1 = !(cf.x == 1.0f && cf.y == 0.0f);
 #pragma unroll
     for (int m = 0; m < NQ; ++m) {
       const int q = tid + m * NT;
@@ -234,9 +308,9 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       dot3_df(g12, g22, g23, ur, us, ut, sh, sl);
       dot3_df(g13, g23, g33, ur, us, ut, th, tl);
       if (scale1) {
-        dfmul(C.h1h, C.h1l, rh, rl, rh, rl);
-        dfmul(C.h1h, C.h1l, sh, sl, sh, sl);
-        dfmul(C.h1h, C.h1l, th, tl, th, tl);
+        dfmul(cf.x, cf.y, rh, rl, rh, rl);
+        dfmul(cf.x, cf.y, sh, sl, sh, sl);
+        dfmul(cf.x, cf.y, th, tl, th, tl);
       }
       R[0][at] = make_float2(rh, rl);
       R[1][at] = make_float2(sh, sl);
@@ -254,7 +328,16 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     // transposed derivatives, in place: group g along direction g
     line_task<P, true>(myR, myR, loff);
     __syncthreads();
-    // w = CR + CS + CT (+ h2 B u) -> double
+    // w = CR + CS + CT (+ c2 B u), times 2^oexp -> double
+    const int2 ci = s_ci;
+    // <p, H p> of an element with a nonzero exponent: the running pair is
+    // moved to FP64 first, the element's own sum is scaled and added after
+    const int pwexp = 2 * (ci.y + kU) + ci.x - kU;
+    if (FUSE && pwst && (pwexp != 0 || nanel)) {
+      pw_d += (double)pw_s + (double)pw_e;
+      pw_s = 0.0f;
+      pw_e = 0.0f;
+    }
     double* we = w + (size_t)e * P3;
     FusedStore<P, double> fs;
     if constexpr (FUSE) {
@@ -273,18 +356,34 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       if (helm) {
         const float2 bv = sb[q], uv = U[at];
         float bh, bl;
-        dfmul(C.h2h, C.h2l, bv.x, bv.y, bh, bl);
+        dfmul(cf.z, cf.w, bv.x, bv.y, bh, bl);
         tmac(bh, bl, uv.x, uv.y, S, er);
       }
       if (FUSE && pwst) {
-        const float2 pv = U[at];
-        tmac(pv.x, pv.y, S, er, pw_s, pw_e);
+        float2 pv = U[at];
+        float ws = S, wl = er;
+        if (ci.y != 0) {               // p and H p times 2^-kE, into [1, 2^49)
+          const float f = __int_as_float((127 - ci.y) << 23);
+          pv.x = __fmul_rn(pv.x, f);
+          pv.y = __fmul_rn(pv.y, f);
+          ws = __fmul_rn(ws, f);
+          wl = __fmul_rn(wl, f);
+        }
+        tmac(pv.x, pv.y, ws, wl, pw_s, pw_e);
       }
-      const double val = (double)S + (double)er;   // exact widenings, one rounding
+      double val = (double)S + (double)er;   // exact widenings, one rounding
+      if (ci.x != 0) val = df_ldexp(val, ci.x);
+      if (nanel) val = __longlong_as_double(0x7FF8000000000000ll);
       if constexpr (FUSE)
         fs.store(q % P, (q / P) % P, q / P2, val);
       else
         we[q] = val;
+    }
+    if (FUSE && pwst && (pwexp != 0 || nanel)) {
+      pw_d += nanel ? __longlong_as_double(0x7FF8000000000000ll)
+                    : df_ldexp((double)pw_s + (double)pw_e, pwexp);
+      pw_s = 0.0f;
+      pw_e = 0.0f;
     }
     if (helm) {
       __syncthreads();                         // U and the stage are free
@@ -300,7 +399,7 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
   }
   if constexpr (FUSE && (3 * P * P) % 32 == 0) {
     if (pwst) {
-      double v[1] = {(double)pw_s + (double)pw_e};
+      double v[1] = {((double)pw_s + (double)pw_e) + pw_d};
       double tot[1];
       if (grid_sum<1>(v, partials, &pwst->counter, tot) && threadIdx.x == 0) {
         st_after_pw(pwst, tot[0]);
@@ -310,6 +409,15 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
 }
 
 // ---------------------------------------------------------------- launch
+// h = m 2^t with t = df_pick_exp(|h|) and m as a pair (exact: m is h times a
+// power of two, split into its leading 24 bits and the next 24)
+static void df_split_scalar(double h, float& hi, float& lo, int& t) {
+  t = df_pick_exp(std::fabs(h));
+  const double m = std::ldexp(h, -t);
+  hi = (float)m;
+  lo = (float)(m - (double)hi);
+}
+
 template <int P, int STAGES>
 static size_t df_smem_bytes(bool helm) {
   using L = DFLayout<P>;
@@ -427,16 +535,14 @@ template <int P, int STAGES, bool FUSE = false>
 static int launch_df_p(const sem_handle* h, const double* u, double* w, double h1, double h2,
                        const CGState* st, cudaStream_t s, CGState* pwst = nullptr,
                        const DFSlab* slab = nullptr) {
-  const bool helm = (float)h2 != 0.0f;
+  const bool helm = h2 != 0.0;
   const size_t smem = df_smem_bytes<P, STAGES>(helm);
   auto kern = ax_df_kernel<P, STAGES, FUSE>;
   const int o = df_occupancy<P, STAGES, FUSE>(helm);
   df_upload_d(h);
   DFScal c;
-  c.h1h = (float)h1;
-  c.h1l = (float)(h1 - (double)c.h1h);
-  c.h2h = (float)h2;
-  c.h2l = (float)(h2 - (double)c.h2h);
+  df_split_scalar(h1, c.h1h, c.h1l, c.t1);
+  df_split_scalar(h2, c.h2h, c.h2l, c.t2);
   const int E = slab ? slab->E : (int)h->E;
   const int64_t e0 = slab ? slab->e0 : 0;
   constexpr int64_t P3 = (int64_t)P * P * P;
@@ -445,9 +551,9 @@ static int launch_df_p(const sem_handle* h, const double* u, double* w, double h
   if (pwst) grid = std::min(grid, kFusedPartials);
   const FuseBox fb = slab ? slab->fb : FuseBox{h->nelx, h->nely, h->nelz, h->faces};
   kern<<<grid, 3 * P * P, smem, s>>>(u + e0 * P3, w + e0 * P3, h->gdf.ptr + e0 * 6 * P3,
-                                     h->bdf.ptr ? h->bdf.ptr + e0 * P3 : nullptr, c, E, st,
-                                     h->dev_err.ptr, kWaitTimeoutNs, fb, pwst,
-                                     h->partials.ptr + 4 * kRedBlocks);
+                                     h->bdf.ptr ? h->bdf.ptr + e0 * P3 : nullptr,
+                                     h->escale.ptr + e0, c, E, st, h->dev_err.ptr,
+                                     kWaitTimeoutNs, fb, pwst, h->partials.ptr + 4 * kRedBlocks);
   SEM_CHECK_LAUNCH();
   return grid;
 }

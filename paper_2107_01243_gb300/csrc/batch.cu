@@ -998,6 +998,7 @@ extern "C" sem_status sem_batch_solve(sem_batch* bt, const double* const* b_L,
       b.dinvg = h->dinvg.ptr;
       if (o.x0_is_zero) SEM_CUDA(cudaMemsetAsync(x_L[p], 0, h->nL * sizeof(double), own));
       outer_norm_b(h, b_L[p], own);
+      inner_scale_from_b(h, own);
     }
     bt->probs.upload(bt->hp.data(), n, own);
     // Each problem moves on its own: FP64 residual -> (converged | FP32 inner
@@ -1087,7 +1088,8 @@ extern "C" sem_status sem_batch_solve(sem_batch* bt, const double* const* b_L,
           phase[p] = FINISHED;
           continue;
         }
-        if (bt->glob) add_from_global(bt->hs[p], x_L[p], bt->hs[p]->xg.ptr, own);
+        if (bt->glob) add_from_global(bt->hs[p], x_L[p], bt->hs[p]->xg.ptr, own,
+                                      1.0 / bt->hs[p]->rscale);
         else outer_update(bt->hs[p], x_L[p], own);
         refine(p);
       }

@@ -24,6 +24,7 @@
 #include "sem_internal.cuh"
 #include "reduce.cuh"
 #include "cg_state.cuh"
+#include "df.cuh"
 
 namespace sem {
 
@@ -391,17 +392,17 @@ k_pupd(int64_t n, T* __restrict__ p, const T* __restrict__ r, const T* __restric
     p[q] = dinv[q] * r[q] + beta * p[q];
 }
 
-// r64 = b - w64 (FP64 residual), optional FP32 copy, <r,r> into st->rr
+// r64 = b - w64 (FP64 residual), optional FP32 copy of rscale r64, <r,r> into st->rr
 __global__ void __launch_bounds__(kRedThreads)
 k_resid(int64_t n, const double* __restrict__ b, const double* __restrict__ w,
         double* __restrict__ r, float* __restrict__ r32, const float* __restrict__ imult,
-        CGState* __restrict__ st, double* __restrict__ partials) {
+        CGState* __restrict__ st, double* __restrict__ partials, double rscale) {
   double v[1] = {0.0};
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
     double rq = b[q] - w[q];
     r[q] = rq;
-    if (r32) r32[q] = (float)rq;
+    if (r32) r32[q] = (float)(rq * rscale);
     v[0] += rq * rq * (double)imult[q];
   }
   double tot[1];
@@ -433,10 +434,12 @@ k_wdot(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
   if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) *out = tot[0];
 }
 
-__global__ void k_addx(int64_t n, double* __restrict__ x, const float* __restrict__ d) {
+// x += d scale (the FP32 correction of a refinement step, scale = 1 / rscale)
+__global__ void k_addx(int64_t n, double* __restrict__ x, const float* __restrict__ d,
+                       double scale) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x)
-    x[q] += (double)d[q];
+    x[q] += (double)d[q] * scale;
 }
 
 __global__ void k_dinv(int64_t n, const double* __restrict__ dg, const uint8_t* __restrict__ mask,
@@ -799,7 +802,7 @@ static void residual64(sem_handle* h, const double* b, const double* x, double h
   const int64_t n = h->nL;
   launch_apply<double>(h, h->f64, x, h->w.ptr, h1, h2, h1f, nullptr, SEM_APPLY_FULL, s);
   k_resid<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, h->w.ptr, h->r.ptr, r32, h->imult.ptr, st,
-                                             h->partials.ptr);
+                                             h->partials.ptr, h->rscale);
   SEM_CHECK_LAUNCH();
 }
 
@@ -935,6 +938,7 @@ static void solve_mixed(sem_handle* h, const double* b, double* x, const sem_sol
   CGState* st1 = h->state.ptr + 1;
   k_norm_bb<<<kRedBlocks, kRedThreads, 0, s>>>(n, b, h->imult.ptr, st0, h->partials.ptr);
   SEM_CHECK_LAUNCH();
+  inner_scale_from_b(h, s);
   if (o.x0_is_zero) SEM_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
   int total = 0, outer = 0;
   int status = SEM_ERR_NOCONV;
@@ -950,7 +954,7 @@ static void solve_mixed(sem_handle* h, const double* b, double* x, const sem_sol
     const double itol = inner_target(o.inner_tol, o.tol, rel);
     CGState in;
     if (glob) {
-      to_global<double>(h, h->r.ptr, h->rg.ptr, s);
+      to_global<double>(h, h->r.ptr, h->rg.ptr, s, h->rscale);
       vcg_init(glob_padded(h) / 4, h->rg.ptr, h->dinvg.ptr, h->pg.ptr, h->xg.ptr, h->wg.ptr,
                st1, h->partials.ptr, itol, o.maxit - total, s);
       in = run_pcg_loop(h, st1, o, s, [&](int count) {
@@ -969,9 +973,9 @@ static void solve_mixed(sem_handle* h, const double* b, double* x, const sem_sol
     ++outer;
     if (in.status == SEM_ERR_BREAKDOWN && in.iter == 0) { status = SEM_ERR_BREAKDOWN; break; }
     if (glob) {
-      add_from_global(h, x, h->xg.ptr, s);
+      add_from_global(h, x, h->xg.ptr, s, 1.0 / h->rscale);
     } else {
-      k_addx<<<ew_grid(n), 256, 0, s>>>(n, x, h->x32.ptr);
+      k_addx<<<ew_grid(n), 256, 0, s>>>(n, x, h->x32.ptr, 1.0 / h->rscale);
       SEM_CHECK_LAUNCH();
     }
   }
@@ -1023,11 +1027,17 @@ void outer_residual(sem_handle* h, const double* b, const double* x, const sem_s
 void outer_residual_global(sem_handle* h, const double* b, const double* x,
                            const sem_solve_opts& o, cudaStream_t s) {
   residual64(h, b, x, o.h1, o.h2, o.h1_field, nullptr, h->state.ptr, s);
-  to_global<double>(h, h->r.ptr, h->rg.ptr, s);
+  to_global<double>(h, h->r.ptr, h->rg.ptr, s, h->rscale);
+}
+
+void inner_scale_from_b(sem_handle* h, cudaStream_t s) {
+  const CGState hs = read_state(h->state.ptr, s);
+  const double rms = std::sqrt(hs.bb / (double)std::max<int64_t>(1, h->nG));
+  h->rscale = std::ldexp(1.0, -df_pick_exp(rms));
 }
 
 void outer_update(sem_handle* h, double* x, cudaStream_t s) {
-  k_addx<<<ew_grid(h->nL), 256, 0, s>>>(h->nL, x, h->x32.ptr);
+  k_addx<<<ew_grid(h->nL), 256, 0, s>>>(h->nL, x, h->x32.ptr, 1.0 / h->rscale);
   SEM_CHECK_LAUNCH();
 }
 
@@ -1040,7 +1050,7 @@ void residual_f64(sem_handle* h, const double* b, const double* x, double h1, do
                   double* w, double* r, CGState* st, cudaStream_t s) {
   launch_apply<double>(h, h->f64, x, w, h1, h2, nullptr, nullptr, SEM_APPLY_FULL, s);
   k_resid<<<kRedBlocks, kRedThreads, 0, s>>>(h->nL, b, w, r, nullptr, h->imult.ptr, st,
-                                             h->partials.ptr);
+                                             h->partials.ptr, 1.0);
   SEM_CHECK_LAUNCH();
 }
 

@@ -120,4 +120,70 @@ __device__ __forceinline__ void dfmul(float ah, float al, float bh, float bl, fl
   pl = e;
 }
 
+// ------------------------------------------------------------------ range
+// Pair arithmetic keeps its 48 bits only while every intermediate stays in
+// FP32's exponent range (normal floats from 2^-126 to 2^128).  The element
+// operator is linear, so a kernel may scale u, the geometric factors and the
+// coefficients by powers of two (exact in binary arithmetic) and undo the
+// scaling on the FP64 result.  Quantities whose magnitude lies in
+// [2^-16, 2^16) are used unscaled (exponent 0); the others are normalised to
+// [1, 2).  With coefficients so bounded (|c G| < 2^32) an element whose
+// largest |u| lies in [2^-60, 2^76) keeps every intermediate between about
+// 2^-140 and 2^123: products and sums stay finite, and the FP32 error terms
+// (2^-48 of the partial sums, subnormal at worst) stay far below the 1e-12
+// relative accuracy.  Other elements are rescaled by their own maximum.
+
+// exponent of a nonnegative magnitude a: 0 inside [2^-16, 2^16) (and for 0
+// or a non-finite a), else floor(log2 a)
+__host__ __device__ inline int df_pick_exp(double a) {
+  if (!(a > 0.0) || !(a <= 1.7976931348623157e308)) return 0;
+  if (a >= 0x1p-16 && a < 0x1p16) return 0;
+  int e = 0;
+  (void)frexp(a, &e);
+  return e - 1;
+}
+
+// Magnitude key of a double: its high word without the sign, with bit 0 set
+// when the low word is nonzero (so that only +-0 has key 0).  Keys order
+// like magnitudes up to that bit; a key >= kDfKeyNonFinite is an Inf or NaN.
+constexpr unsigned kDfKeyLo = (1023u - 60u) << 20;     // |u| >= 2^-60
+constexpr unsigned kDfKeyHi = (1023u + 76u) << 20;     // |u| <  2^76
+constexpr unsigned kDfKeyNonFinite = 0x7FF00000u;
+// <p, H p> of the fused kernel: p is rescaled only outside [2^-20, 2^20)
+constexpr unsigned kDfPwLo = (1023u - 20u) << 20;
+constexpr unsigned kDfPwHi = (1023u + 20u) << 20;
+
+// floor(log2) of the magnitude a finite key stands for; elements whose
+// largest value is subnormal (key below 2^20) are scaled by 2^1060, which
+// maps every subnormal into [2^-14, 2^38)
+__device__ __forceinline__ int df_key_exp(unsigned key) {
+  const int f = (int)(key >> 20);
+  return f ? f - 1023 : -1060;
+}
+
+// 2^e as a double, e in [-1022, 1023]
+__device__ __forceinline__ double df_pow2d(int e) {
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// v 2^e for |e| up to about 3000, in steps that are exact powers of two
+__device__ __forceinline__ double df_ldexp(double v, int e) {
+  while (e > 1000) {
+    v *= df_pow2d(1000);
+    e -= 1000;
+  }
+  while (e < -1000) {
+    v *= df_pow2d(-1000);
+    e += 1000;
+  }
+  return v * df_pow2d(e);
+}
+
+// x 2^d for d <= 0 (two steps below FP32's normal range, 0 far below it)
+__device__ __forceinline__ float df_scale_down(float x, int d) {
+  if (d >= -126) return __fmul_rn(x, __int_as_float((127 + d) << 23));
+  if (d >= -252) return __fmul_rn(__fmul_rn(x, 0x1p-126f), __int_as_float((253 + d) << 23));
+  return __fmul_rn(x, 0.0f);
+}
+
 }  // namespace sem

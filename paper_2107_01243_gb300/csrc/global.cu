@@ -269,7 +269,7 @@ bool launch_apply_global(const sem_handle* h, const float* u, float* w, float h1
 template <class Tin>
 __global__ void k_to_global(int64_t nG, const Tin* __restrict__ in, float* __restrict__ out,
                             int N, int P, int nelx, int nely, int nelz, FastDiv dgx, FastDiv dgy,
-                            FastDiv dN) {
+                            FastDiv dN, double scale) {
   const long long P3 = (long long)P * P * P;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nG;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -282,14 +282,14 @@ __global__ void k_to_global(int64_t nG, const Tin* __restrict__ in, float* __res
     const int ez = min((int)dN.div((uint32_t)iz), nelz - 1);
     const int i = ix - ex * N, j = iy - ey * N, k = iz - ez * N;
     const long long e = ex + (long long)nelx * (ey + (long long)nely * ez);
-    out[g] = (float)in[e * P3 + ((long long)k * P + j) * P + i];
+    out[g] = (float)((double)in[e * P3 + ((long long)k * P + j) * P + i] * scale);
   }
 }
 
 // x_L += d_g[g(L)] at every local point
 __global__ void k_add_from_global(int64_t nL, double* __restrict__ x, const float* __restrict__ d,
                                   int N, int P, int nelx, int nely, int gx, int gy, FastDiv dP3,
-                                  FastDiv dP, FastDiv dnx, FastDiv dny) {
+                                  FastDiv dP, FastDiv dnx, FastDiv dny, double scale) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nL;
        q += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t qq = (uint32_t)q;
@@ -305,7 +305,7 @@ __global__ void k_add_from_global(int64_t nL, double* __restrict__ x, const floa
     const uint32_t ey = re - ez * (uint32_t)nely;
     const long long g = (long long)(ex * N + i) +
                         (long long)gx * ((long long)(ey * N + j) + (long long)gy * (ez * N + k));
-    x[q] += (double)d[g];
+    x[q] += (double)d[g] * scale;
   }
 }
 
@@ -314,21 +314,22 @@ static int conv_grid(int64_t n) {
 }
 
 template <class Tin>
-void to_global(const sem_handle* h, const Tin* in, float* out, cudaStream_t s) {
+void to_global(const sem_handle* h, const Tin* in, float* out, cudaStream_t s, double scale) {
   const int N = h->N;
   k_to_global<Tin><<<conv_grid(h->nG), 256, 0, s>>>(
       h->nG, in, out, N, h->P, h->nelx, h->nely, h->nelz, FastDiv((uint32_t)(N * h->nelx + 1)),
-      FastDiv((uint32_t)(N * h->nely + 1)), FastDiv((uint32_t)(N > 0 ? N : 1)));
+      FastDiv((uint32_t)(N * h->nely + 1)), FastDiv((uint32_t)(N > 0 ? N : 1)), scale);
   SEM_CHECK_LAUNCH();
 }
-template void to_global<float>(const sem_handle*, const float*, float*, cudaStream_t);
-template void to_global<double>(const sem_handle*, const double*, float*, cudaStream_t);
+template void to_global<float>(const sem_handle*, const float*, float*, cudaStream_t, double);
+template void to_global<double>(const sem_handle*, const double*, float*, cudaStream_t, double);
 
-void add_from_global(const sem_handle* h, double* x, const float* d, cudaStream_t s) {
+void add_from_global(const sem_handle* h, double* x, const float* d, cudaStream_t s,
+                     double scale) {
   k_add_from_global<<<conv_grid(h->nL), 256, 0, s>>>(
       h->nL, x, d, h->N, h->P, h->nelx, h->nely, h->N * h->nelx + 1, h->N * h->nely + 1,
       FastDiv((uint32_t)h->P3), FastDiv((uint32_t)h->P), FastDiv((uint32_t)h->nelx),
-      FastDiv((uint32_t)h->nely));
+      FastDiv((uint32_t)h->nely), scale);
   SEM_CHECK_LAUNCH();
 }
 

@@ -493,6 +493,7 @@ void gmres_solve_mixed(sem_handle* h, const double* b, double* x, const sem_solv
   }
   CGState* st = h->state.ptr;
   outer_norm_b(h, b, s);
+  inner_scale_from_b(h, s);
   if (o.x0_is_zero) SEM_CUDA(cudaMemsetAsync(x, 0, nL * sizeof(double), s));
   info = sem_solve_info{0, 0, 0.0, SEM_ERR_NOCONV};
   std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
@@ -596,7 +597,7 @@ void gmres_solve_mixed(sem_handle* h, const double* b, double* x, const sem_solv
       if (std::fabs(gv[k]) <= itol * beta0) break;
     }
     if (breakdown) { info.status = SEM_ERR_BREAKDOWN; break; }
-    add_from_global(h, x, g.d.ptr, s);
+    add_from_global(h, x, g.d.ptr, s, 1.0 / h->rscale);
   }
   info.iters = total;
   info.outer_iters = outer;

@@ -171,6 +171,7 @@ struct sem_handle {
   sem::DevBuf<int64_t> gid;                 // global numbers
   sem::DevBuf<int> dev_err;                 // device-side error word (SEM_ERR_TIMEOUT)
   sem::DevBuf<float2> gdf, bdf;             // G and B as float pairs (double-float kernel)
+  sem::DevBuf<int> escale;                  // per element: exponents sG | sB << 16 of gdf, bdf
   int f64_kernel = SEM_F64_KERNEL_AUTO;     // which FP64 Ax kernel runs
   struct Tune {
     int ax32_ldg = 0;          // 1: FP32 Ax by the global-load kernel instead of bulk copies
@@ -206,6 +207,10 @@ struct sem_handle {
   std::shared_ptr<sem::GmresWork> gmres;    // GMRES workspace, kept between solves
   std::shared_ptr<sem::GmresWorkF> gmres32; // mixed-precision GMRES workspace
   std::shared_ptr<sem::HostPipe> host_pipe; // streams of the pipelined sem_apply_host
+  // The FP32 inner solves of the mixed-precision solvers work on rscale times
+  // the FP64 residual and add the correction divided by it: a power of two
+  // chosen from ||b|| that keeps the FP32 vectors in FP32's normal range
+  double rscale = 1.0;
   double dinv_h1 = NAN, dinv_h2 = NAN;
   const void* dinv_h1f = nullptr;
   int dinv_valid = 0;
@@ -265,7 +270,9 @@ void mixed_prepare(sem_handle* h, const sem_solve_opts& o, cudaStream_t s);
 void outer_norm_b(sem_handle* h, const double* b, cudaStream_t s);    // <b,b> -> state[0].bb
 void outer_residual(sem_handle* h, const double* b, const double* x, const sem_solve_opts& o,
                     cudaStream_t s);                                   // r, r32, <r,r> -> state[0]
-void outer_update(sem_handle* h, double* x, cudaStream_t s);          // x += x32
+void outer_update(sem_handle* h, double* x, cudaStream_t s);          // x += x32 / rscale
+// rscale from <b,b> in state[0] (reads it: synchronises the stream)
+void inner_scale_from_b(sem_handle* h, cudaStream_t s);
 // global-vector inner solves: vectors and the global Jacobi diagonal; the
 // FP64 residual r (state[0].rr) and its global copy rg
 void glob_prepare(sem_handle* h, cudaStream_t s);
@@ -280,8 +287,10 @@ int64_t glob_padded(const sem_handle* h);          // n_G rounded up to a multip
 bool launch_apply_global(const sem_handle* h, const float* u, float* w, float h1, float h2,
                          const CGState* st, CGState* pwst, cudaStream_t s);
 template <class Tin>
-void to_global(const sem_handle* h, const Tin* in, float* out, cudaStream_t s);  // owner copies
-void add_from_global(const sem_handle* h, double* x, const float* d, cudaStream_t s);
+void to_global(const sem_handle* h, const Tin* in, float* out, cudaStream_t s,
+               double scale = 1.0);                                    // owner copies x scale
+void add_from_global(const sem_handle* h, double* x, const float* d, cudaStream_t s,
+                     double scale = 1.0);                              // x += d x scale
 
 // ---- apply.cu: FP64 operator with host buffers, copies overlapped by slabs
 bool host_pipeline_supported(const sem_handle* h, const void* din, const void* dout);

@@ -10,6 +10,7 @@
 #include <memory>
 
 #include "sem_internal.cuh"
+#include "df.cuh"
 
 namespace sem {
 
@@ -198,11 +199,35 @@ __global__ void convert_kernel(const S* __restrict__ src, D* __restrict__ dst, i
     dst[q] = (D)src[q];
 }
 
-// x -> (hi, lo) with hi = RN(x), lo = RN(x - hi): setup only, FP64 arithmetic
-__global__ void split_kernel(const double* __restrict__ src, float2* __restrict__ dst, int64_t n) {
+// Per-element power-of-two exponents of the double-float kernel's geometric
+// factors (df.cuh): bits 0-15 the exponent sG of G, bits 16-31 that of B
+// (both signed), 0 while the element's largest magnitude lies in
+// [2^-16, 2^16).  One warp per element.
+__global__ void df_escale_kernel(const double* __restrict__ G, const double* __restrict__ B,
+                                 int P3, int64_t E, int* __restrict__ esc) {
+  const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (e >= E) return;                  // whole warps leave together
+  double gm = 0.0, bm = 0.0;
+  for (int q = lane; q < 6 * P3; q += 32) gm = fmax(gm, fabs(G[e * 6 * P3 + q]));
+  for (int q = lane; q < P3; q += 32) bm = fmax(bm, fabs(B[e * P3 + q]));
+  for (int o = 16; o > 0; o >>= 1) {
+    gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+  }
+  if (lane == 0) esc[e] = (df_pick_exp(gm) & 0xFFFF) | (df_pick_exp(bm) << 16);
+}
+
+// float pairs (hi = RN(x), lo = RN(x - hi), FP64 arithmetic at setup) of
+// x = src 2^-s, s the element's exponent in esc (bits 0-15 when shift = 0,
+// bits 16-31 when shift = 16), per = values per element
+__global__ void split_scaled_kernel(const double* __restrict__ src, float2* __restrict__ dst,
+                                    int64_t n, int per, const int* __restrict__ esc, int shift) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const double x = src[q];
+    const int w = esc[q / per];
+    const int sc = shift ? (w >> 16) : (int)(short)(w & 0xFFFF);
+    const double x = sc ? scalbn(src[q], -sc) : src[q];
     const float hi = __double2float_rn(x);
     dst[q] = make_float2(hi, __double2float_rn(x - (double)hi));
   }
@@ -443,11 +468,18 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
     SEM_REQUIRE(!hbad, "sem_setup: element map has detJ <= 0 at some GLL point");
     if (P == 6 || P == 8 || P == 10) {
       // float-pair copies of G and B for the double-float FP64 kernel
+      // (normalised per element where needed, see df.cuh)
       h->gdf.alloc(6 * nL);
       h->bdf.alloc(nL);
-      split_kernel<<<grid_for(6 * nL), 256, 0, s>>>(h->f64.G.ptr, h->gdf.ptr, 6 * nL);
+      h->escale.alloc(h->E);
+      df_escale_kernel<<<(unsigned)((h->E + 7) / 8), 256, 0, s>>>(h->f64.G.ptr, h->f64.B.ptr,
+                                                                  h->P3, h->E, h->escale.ptr);
       SEM_CHECK_LAUNCH();
-      split_kernel<<<grid_for(nL), 256, 0, s>>>(h->f64.B.ptr, h->bdf.ptr, nL);
+      split_scaled_kernel<<<grid_for(6 * nL), 256, 0, s>>>(h->f64.G.ptr, h->gdf.ptr, 6 * nL,
+                                                            6 * h->P3, h->escale.ptr, 0);
+      SEM_CHECK_LAUNCH();
+      split_scaled_kernel<<<grid_for(nL), 256, 0, s>>>(h->f64.B.ptr, h->bdf.ptr, nL, h->P3,
+                                                        h->escale.ptr, 16);
       SEM_CHECK_LAUNCH();
       df_prepare(h.get());
     }
