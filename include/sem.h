@@ -504,6 +504,8 @@ sem_status sem_dot(sem_handle* h, const double* a, const double* b, double* out,
  */
 sem_status sem_dot_noalloc(sem_handle* h, const double* a, const double* b, double* out,
                            void* stream);
+/* the largest n_L sem_dot_noalloc accepts (16,384 blocks of 4,096 points) */
+enum { SEM_NOALLOC_MAX_POINTS = 67108864 };
 
 /*
  * sem_apply_host -- w = mask o QQ^T A_L u with HOST buffers: copies u_host

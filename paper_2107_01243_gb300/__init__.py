@@ -15,7 +15,8 @@ from ._lib import (SemError, SEM_F64, SEM_F32, SEM_PREC_F64, SEM_PREC_F32, SEM_S
                    SEM_F64_KERNEL_NATIVE, SEM_F64_KERNEL_DOUBLEFLOAT, SEM_DSSUM_BOX,
                    SEM_DSSUM_SEGMENTS, SEM_APPLY_LOCAL, SEM_APPLY_FINISH, SEM_APPLY_FULL,
                    SEM_INNER_AUTO, SEM_INNER_LOCAL, SEM_INNER_GLOBAL, SEM_SCHWARZ_LOCAL,
-                   SEM_SCHWARZ_COARSE, SEM_SCHWARZ_BOTH, SEM_CG_STANDARD, SEM_CG_PIPELINED)
+                   SEM_SCHWARZ_COARSE, SEM_SCHWARZ_BOTH, SEM_CG_STANDARD, SEM_CG_PIPELINED,
+                   SEM_ERR_ARG, SEM_NOALLOC_MAX_POINTS)
 from ._lib import (SEM_FACE_XMIN, SEM_FACE_XMAX, SEM_FACE_YMIN, SEM_FACE_YMAX, SEM_FACE_ZMIN,
                    SEM_FACE_ZMAX)
 from .api import (Handle, sem_setup, sem_destroy, sem_get_sizes, sem_get_field, sem_ax,

@@ -26,6 +26,7 @@ SEM_FACE_ALL = 63
 SEM_F64_KERNEL_AUTO, SEM_F64_KERNEL_NATIVE, SEM_F64_KERNEL_DOUBLEFLOAT = 0, 1, 2
 SEM_DSSUM_BOX, SEM_DSSUM_SEGMENTS = 0, 1
 SEM_APPLY_LOCAL, SEM_APPLY_FINISH, SEM_APPLY_FULL = 1, 2, 3
+SEM_NOALLOC_MAX_POINTS = 67108864
 SEM_INNER_AUTO, SEM_INNER_LOCAL, SEM_INNER_GLOBAL = 0, 1, 2
 SEM_SCHWARZ_LOCAL, SEM_SCHWARZ_COARSE, SEM_SCHWARZ_BOTH = 1, 2, 3
 SEM_CG_STANDARD, SEM_CG_PIPELINED = 0, 1

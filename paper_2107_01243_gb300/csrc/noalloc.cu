@@ -18,10 +18,11 @@
 //    contents; each call clears the ticket before its kernel runs.  Calls
 //    whose kernels overlap on the GPU (different streams, no ordering) race
 //    on the array and give wrong results: order them on one stream.
-//  * sem_setup looks up the array's device address with cudaGetSymbolAddress
-//    (noalloc_prepare) and caches it, so every call, the first included, may
-//    run inside a stream capture.
-#include <mutex>
+//  * sem_setup looks up the array's device address once with
+//    cudaGetSymbolAddress (noalloc_prepare, with the handle's device current);
+//    a call then only clears the ticket and launches, so every call, the
+//    first included, may run inside a stream capture.
+#include <atomic>
 
 #include "sem_internal.cuh"
 #include "reduce.cuh"
@@ -32,7 +33,7 @@ constexpr int kNoAllocThreads = 256;
 constexpr int kNoAllocPointsPerBlock = 4096;                // 16 points per thread
 constexpr int kNoAllocMaxBlocks = 16384;
 constexpr int64_t kNoAllocMaxPoints = (int64_t)kNoAllocMaxBlocks * kNoAllocPointsPerBlock;
-constexpr int kNoAllocMaxDevices = 64;
+static_assert(kNoAllocMaxPoints == SEM_NOALLOC_MAX_POINTS, "limit stated in sem.h");
 
 // [0, kNoAllocMaxBlocks): block partial sums; word kNoAllocMaxBlocks: ticket
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxBlocks + 32];
@@ -55,27 +56,18 @@ k_wdot_static(int64_t n, const double* __restrict__ a, const double* __restrict_
   if (grid_sum<1>(v, scratch, ticket, tot) && threadIdx.x == 0) *out = tot[0];
 }
 
-static std::mutex g_noalloc_mu;
-static double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+// Device address of the array, resolved once by sem_setup (the library drives
+// one CUDA device per process, so one address serves every call).
+static std::atomic<double*> g_noalloc_addr{nullptr};
 
-// Device address of the array on the current device, looked up once per device.
-static double* noalloc_scratch() {
-  int dev = -1;
-  SEM_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kNoAllocMaxDevices)
-    throw Error(SEM_ERR_STATE, "sem_dot_noalloc: device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    SEM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_addr[dev] = static_cast<double*>(p);
-  }
-  return g_noalloc_addr[dev];
+// run by sem_setup with the handle's device current, so that every call, the
+// first included, finds the address resolved (and may run inside a capture)
+void noalloc_prepare() {
+  if (g_noalloc_addr.load(std::memory_order_acquire)) return;
+  void* p = nullptr;
+  SEM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  g_noalloc_addr.store(static_cast<double*>(p), std::memory_order_release);
 }
-
-// run by sem_setup, so that a first sem_dot_noalloc inside a stream capture
-// finds the address already resolved
-void noalloc_prepare() { noalloc_scratch(); }
 
 }  // namespace sem
 
@@ -89,7 +81,8 @@ extern "C" sem_status sem_dot_noalloc(sem_handle* h, const double* a, const doub
       throw Error(SEM_ERR_ARG, "sem_dot_noalloc: n_L = " + std::to_string(h->nL) +
                                    " local points exceeds the maximum of " +
                                    std::to_string(kNoAllocMaxPoints) + "; use sem_dot");
-    double* scratch = noalloc_scratch();
+    double* scratch = g_noalloc_addr.load(std::memory_order_acquire);
+    if (!scratch) throw Error(SEM_ERR_STATE, "sem_dot_noalloc: no handle was set up");
     cudaStream_t s = (cudaStream_t)stream;
     const int blocks = (int)((h->nL + kNoAllocPointsPerBlock - 1) / kNoAllocPointsPerBlock);
     SEM_CUDA(cudaMemsetAsync(scratch + kNoAllocMaxBlocks, 0, sizeof(double), s));
