@@ -72,15 +72,29 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# FP64 Ax kernel on the 32^3, N=7 throughput mesh, from one ncu capture of the
-# kernel as it now stands (summary and command under profiles/); a kernel
-# variant that no capture covers reports null.
-AX_TRAFFIC = {"ax_df_kernel<8, 1, 1>": 939_960_320 + 124_171_008}
-# smsp__inst_executed.sum per launch from the same capture: the double-float
-# kernel is bound by instruction issue on the FP32 pipe, so its second roof is
-# the issue rate, 152 SMs x 4 schedulers x the maximum SM clock.
-AX_WARP_INSTR = {"ax_df_kernel<8, 1, 1>": 301_503_392}
+# Source files the FP64 element kernel is built from.  An ncu capture below
+# holds only for the kernel built from files with the recorded digest: after
+# any change to them the bench reports null until the kernel is captured again.
+AX_SOURCES = tuple(os.path.join("paper_2107_01243_gb300", "csrc", f) for f in (
+    "ax_df.cu", "df.cuh", "ax_tile.cuh", "tma.cuh", "reduce.cuh", "cg_state.cuh"))
+
+
+def ax_source_digest(root=ROOT):
+    import hashlib
+    d = hashlib.sha256()
+    for f in AX_SOURCES:
+        with open(os.path.join(root, f), "rb") as fh:
+            d.update(fh.read())
+    return d.hexdigest()[:16]
+
+
+# Per launch of the FP64 Ax kernel on the 32^3, N=7 throughput mesh, from one
+# ncu capture (summary and command under profiles/): DRAM bytes
+# (dram__bytes_read.sum + dram__bytes_write.sum) and warp instructions
+# (smsp__inst_executed.sum).  The double-float kernel is bound by instruction
+# issue on the FP32 pipe, so its second roof is the issue rate, 152 SMs x 4
+# schedulers x the maximum SM clock.
+AX_CAPTURES = {}
 ISSUE_PEAK = 152 * 4 * 2.07e9         # warp instructions per second
 
 
@@ -90,29 +104,42 @@ def ax_kernel_name(tiles):
     return f"ax_df_kernel<8, {tiles['f64_stages']}, 1>"
 
 
-def ax_traffic(tiles):
-    return AX_TRAFFIC.get(ax_kernel_name(tiles))
+def ax_capture(tiles, captures=None, digest=None):
+    """The capture of this kernel variant, if one was taken of the current source."""
+    c = (AX_CAPTURES if captures is None else captures).get(ax_kernel_name(tiles))
+    if c is None:
+        return None
+    if c["source"] != (ax_source_digest() if digest is None else digest):
+        return None
+    return c
 
 
-def alu_roof(tiles, ax_ms):
+def ax_traffic(tiles, **kw):
+    c = ax_capture(tiles, **kw)
+    return None if c is None else c["dram_bytes"]
+
+
+def alu_roof(tiles, ax_ms, **kw):
     """Issue roof of the FP64 Ax kernel: warp instructions per launch (ncu)
     over its CUDA-event duration, against the SMs' issue rate at max clock."""
-    k = ax_kernel_name(tiles)
-    instr = AX_WARP_INSTR.get(k)
-    if instr is None:
+    c = ax_capture(tiles, **kw)
+    if c is None:
         return None
+    instr = c["warp_instructions"]
     achieved = instr / (ax_ms / 1e3)
-    return {"bound": "alu", "kernel": k, "unit": "warp instr/s", "achieved": achieved,
-            "peak": ISSUE_PEAK, "frac": achieved / ISSUE_PEAK,
+    return {"bound": "alu", "kernel": ax_kernel_name(tiles), "unit": "warp instr/s",
+            "achieved": achieved, "peak": ISSUE_PEAK, "frac": achieved / ISSUE_PEAK,
             "warp_instructions_per_launch": instr}
 
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples (every 50 ms) around the timed region; the summary
+    """nvidia-smi samples (every 20 ms) around the timed region; the summary
     keeps the samples whose timestamps fall between mark_start() and
     mark_end() (host times taken after the synchronisations that bracket the
-    region), or all samples if none does."""
+    region).  A region shorter than the sampling interval may hold none: the
+    summary then uses the last sample before it and the first after it, and
+    says so ("window": "adjacent" instead of "timed_region")."""
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -126,7 +153,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -170,13 +197,23 @@ class ClockSampler:
                                         if v.lower().startswith("active")}))
         if not rows:
             return None
-        inside = []
+        inside, window = [], "all"
         if self.t_start is not None and self.t_end is not None:
-            inside = [r for r in rows if r[0] is not None and self.t_start <= r[0] <= self.t_end]
+            timed = [r for r in rows if r[0] is not None]
+            inside = [r for r in timed if self.t_start <= r[0] <= self.t_end]
+            window = "timed_region"
+            if not inside:
+                before = [r for r in timed if r[0] < self.t_start]
+                after = [r for r in timed if r[0] > self.t_end]
+                inside = before[-1:] + after[:1]
+                window = "adjacent"
         use = inside or rows
+        if not inside:
+            window = "all"
         return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": use[-1][2],
                 "reasons": sorted(set().union(*(r[3] for r in use))), "samples": len(rows),
-                "samples_in_timed_region": len(inside)}
+                "samples_in_timed_region": len(inside) if window == "timed_region" else 0,
+                "window": window, "samples_used": len(use)}
 
 
 # ---------------------------------------------------------------- oracle timing
@@ -203,6 +240,72 @@ def time_oracle(nz, min_seconds):
             break
     n = u.size * runs
     return n / el / 1e9, dict(points=u.size, runs=runs, seconds=el, nel=o.nel)
+
+
+def _oracle_worker(nz, min_seconds, barrier, queue):
+    """One host core: the oracle operator on its own slab, timed once every
+    worker has built its data (so that the timed loops overlap)."""
+    o, u = oracle_sample(nz)
+    o.matvec(u)
+    barrier.wait()
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        o.matvec(u)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    queue.put((u.size * runs / el / 1e9, u.size, runs, el))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def time_oracle_all_cores(nz, min_seconds):
+    """The oracle on every host core at once: one spawned process per core
+    (numpy single-threaded in each), each on a 32 x 32 x nz slab; the rate is
+    the sum over the workers."""
+    import multiprocessing as mp
+    n = host_cores()
+    keep = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                           "MKL_NUM_THREADS")}
+    for v in keep:
+        os.environ[v] = "1"
+    ctx = mp.get_context("spawn")      # never fork a process that holds a CUDA context
+    barrier, queue = ctx.Barrier(n), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(nz, min_seconds, barrier, queue))
+             for _ in range(n)]
+    try:
+        for pr in procs:
+            pr.start()
+        res = [queue.get(timeout=900) for _ in procs]
+    finally:
+        for pr in procs:
+            pr.join(timeout=60)
+        for v, old in keep.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+    return sum(r[0] for r in res), dict(workers=n, points=res[0][1],
+                                        runs=sum(r[2] for r in res),
+                                        seconds=max(r[3] for r in res))
 
 
 def run_reference(args):
@@ -246,7 +349,8 @@ def main():
     ap.add_argument("--model-sweep", action="store_true",
                     help="print the Eq. 12-13 cost model against measured kernel times for "
                          "N = 2..9 instead of the benchmark line")
-    ap.add_argument("--sections", default="solve,batch,manufactured,projection,pressure,adjoint",
+    ap.add_argument("--sections",
+                    default="model,solve,batch,manufactured,projection,pressure,adjoint",
                     help="comma list of the solver sections to run after the operator line "
                          "(--no-solve and --no-batch remove theirs)")
     ap.add_argument("--pressure-nel", type=int, default=48,
@@ -334,13 +438,13 @@ def main():
     (ms,) = max_over_ranks([ms], dev)
     value = whole_job_rate(n, K, world, ms)
 
-    def split_times(local, finish, warm=3):
+    def split_times(local, finish, warm=3, reps=None):
         for _ in range(warm):
             local()
             finish()
         torch.cuda.synchronize()
-        e = ev3()
-        for s in range(K):
+        e = ev3()[:reps or K]
+        for s in range(len(e)):
             e[s][0].record(stream)
             local()
             e[s][1].record(stream)
@@ -355,6 +459,10 @@ def main():
                              lambda: sem.sem_apply(h, u32, w32, phase=sem.SEM_APPLY_FINISH))
     sep64 = split_times(lambda: sem.sem_ax(h, u, w), lambda: sem.sem_dssum(h, w))
     sep32 = split_times(lambda: sem.sem_ax(h, u32, w32), lambda: sem.sem_dssum(h, w32))
+    # the IEEE FP64 element kernel (DFMA on the FP64 pipe) on the same mesh
+    sem.sem_set_f64_kernel(h, sem.SEM_F64_KERNEL_NATIVE)
+    nat64 = split_times(lambda: sem.sem_ax(h, u, w), lambda: None, reps=min(K, 50))[0]
+    sem.sem_set_f64_kernel(h, sem.SEM_F64_KERNEL_AUTO)
     # FP32 operator on global vectors (the inner-solve operator): clearing w_g,
     # then the element kernel that gathers u_g and assembles w_g by reductions
     ng = h.n_global
@@ -389,8 +497,11 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "arithmetic": ("FP64 inputs, outputs and gather-scatter; the element kernel "
-                       "evaluates in double-float (pairs of FP32, 48-bit significand) and "
-                       "matches the FP64 oracle to 1e-12"),
+                       "evaluates in double-float (pairs of FP32, 48-bit significand) with "
+                       "exact power-of-two rescaling of elements, geometric factors and "
+                       "coefficients outside FP32's exponent range, and matches the FP64 "
+                       "oracle to 1e-12 for finite inputs of any magnitude; "
+                       "kernels.ax_f64_native_* is the IEEE FP64 kernel on the same mesh"),
         "config": arm_config(world, n),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": ax_traffic(tiles),
@@ -399,6 +510,11 @@ def main():
                      "algorithmic_bytes_per_launch": ax_bytes},
         "alu": alu_roof(tiles, ax_ms),
         "kernels": {"ax_f64_ms": ax_ms, "gs_finish_f64_ms": ds_ms,
+                    "ax_f64_native_ms": nat64,
+                    "ax_f64_native_gdofs": n / (nat64 / 1e3) / 1e9,
+                    "ax_f64_native_frac": ax_bytes / (nat64 / 1e3) / 1e9 / hbm,
+                    "ax_f64_native_note": ("sem_ax with SEM_F64_KERNEL_NATIVE: IEEE FP64 "
+                                           "arithmetic (DFMA), bound by the FP64 pipe"),
                     "ax_f32_ms": ax32, "ax_f32_gbs": 32 * n / (ax32 / 1e3) / 1e9,
                     "ax_f32_frac": 32 * n / (ax32 / 1e3) / 1e9 / hbm,
                     "gs_finish_f32_ms": ds32,
@@ -431,6 +547,9 @@ def main():
         sections -= {"solve", "manufactured", "projection", "pressure", "adjoint"}
     if args.no_batch:
         sections.discard("batch")
+    if "model" in sections:
+        line["model"] = run_model_sweep(sem, torch, dev, orders=(5, 7, 9),
+                                        target_points=8_388_608, reps=10)
     if "solve" in sections:
         line["solve"] = run_solves(sem, torch, dev)
     if "batch" in sections:
@@ -447,12 +566,19 @@ def main():
         line["adjoint"] = run_adjoint(sem, torch, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        gd, meta = time_oracle(8, 10.0)
+        gd1, meta1 = time_oracle(8, 10.0)
+        gdn, metan = time_oracle_all_cores(2, 10.0)
         line["cpu_baseline"] = {
-            "value": gd, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"oracle Ax+dssum (numpy, FP64, 1 thread) on a 32x32x8 slab of the "
-                       f"throughput mesh ({meta['points']} points) x {meta['runs']} runs, "
-                       f"{meta['seconds']:.1f} s")}
+            "value": gdn, "unit": UNIT, "cores": metan["workers"], "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": (f"oracle Ax+dssum (numpy, FP64) on every host core at once: "
+                       f"{metan['workers']} processes, each on its own 32x32x2 slab of the "
+                       f"throughput mesh ({metan['points']} points), {metan['runs']} runs in "
+                       f"all over {metan['seconds']:.1f} s; rate = sum over the processes"),
+            "one_core": {
+                "value": gd1, "unit": UNIT, "cores": 1,
+                "sample": (f"the same on one core: a 32x32x8 slab ({meta1['points']} points) "
+                           f"x {meta1['runs']} runs, {meta1['seconds']:.1f} s")}}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -763,12 +889,21 @@ def model_costs(N, fp64):
     return W_ax, Q_ax, W_gs, Q_gs
 
 
-def run_model_sweep(sem, torch, dev, target_points=16_777_216, reps=20):
+def model_time_ms(W, Q, n, pi, beta):
+    """Eq. 13 for one kernel: n points of W flops and Q bytes each, on a
+    machine of pi flop/s and beta bytes/s; (ms, the bound that decides it)."""
+    tw, tq = W * n / pi, Q * n / beta
+    return max(tw, tq) * 1e3, ("flops" if tw > tq else "bytes")
+
+
+def run_model_sweep(sem, torch, dev, target_points=16_777_216, reps=20, orders=range(2, 10)):
     """Eq. 13 (T = max(W / pi, Q / beta)) against the measured kernel times for
-    N = 2..9 on deformed boxes of about target_points local points."""
+    the given orders on deformed boxes of about target_points local points
+    (the bench line's section: N = 5, 7, 9 on 8.4 M points; --model-sweep:
+    N = 2..9 on 16.8 M)."""
     beta = peaks()[0] * 1e9
     rows = []
-    for N in range(2, 10):
+    for N in orders:
         P = N + 1
         nel = si.near_cubic_box(target_points / P ** 3, max_side=128)
         h = sem.sem_setup(nel, N, length=(si.TWO_PI,) * 3, deform=0.1)
@@ -803,9 +938,8 @@ def run_model_sweep(sem, torch, dev, target_points=16_777_216, reps=20):
                 b.record()
                 torch.cuda.synchronize()
                 ms = a.elapsed_time(b) / reps
-                t_model = max(W * n / pi, Q * n / beta) * 1e3
-                row[f"{name}_{tag}"] = {"ms": ms, "model_ms": t_model,
-                                        "bound": "flops" if W * n / pi > Q * n / beta else "bytes",
+                t_model, bound = model_time_ms(W, Q, n, pi, beta)
+                row[f"{name}_{tag}"] = {"ms": ms, "model_ms": t_model, "bound": bound,
                                         "measured_over_model": ms / t_model}
             del u, w
         sem.sem_destroy(h)
