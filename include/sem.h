@@ -157,7 +157,9 @@ const char* sem_last_error(void);
  * sem_sync -- synchronise the stream, then report a device-side failure
  * recorded by an earlier asynchronous call on this handle: SEM_ERR_TIMEOUT if
  * a bounded wait inside a kernel gave up (the kernel then returned early and
- * its output is incomplete).  Clears the record.
+ * its output is incomplete), SEM_ERR_ARG if sem_gather, sem_scatter_add or
+ * sem_set_multiplicity met an index or a multiplicity out of range (the
+ * entry was skipped).  Clears the record.
  */
 sem_status sem_sync(sem_handle* h, void* stream);
 
@@ -506,6 +508,64 @@ sem_status sem_dot_noalloc(sem_handle* h, const double* a, const double* b, doub
                            void* stream);
 /* the largest n_L sem_dot_noalloc accepts (16,384 blocks of 4,096 points) */
 enum { SEM_NOALLOC_MAX_POINTS = 67108864 };
+
+/*
+ * Element partition across processes (§3.2, Algorithm 1).
+ *
+ * Each rank owns a sub-box of the element box and its own handle: sem_setup
+ * on the sub-box (x0 and len of its elements, the same element size and
+ * deformation map as the whole box) with Dirichlet faces only where the
+ * sub-box touches the global boundary.  The rank's sem_apply then sums the
+ * copies of a shared point inside the rank; the copies on other ranks are
+ * added by an interface exchange that the caller runs (over MPI, NCCL or
+ * gloo): for each direction x, then y, then z, gather the values of the
+ * rank's face planes into buffers, send them to the neighbours across those
+ * faces, and add what the neighbours sent to every local copy of the face
+ * points.  Summing direction by direction also completes the points on the
+ * edges and corners shared by 4 or 8 ranks.  The Krylov dots end in a sum
+ * over the ranks.  The calls below are the device side of that scheme;
+ * paper_2107_01243_gb300/partition.py builds the index lists, runs the
+ * exchange over torch.distributed and drives a partitioned PCG with them.
+ *
+ * Index arrays are DEVICE arrays of int64 owned by the caller.  Indices are
+ * checked in the kernels: an entry outside its vector is skipped and
+ * recorded as SEM_ERR_ARG for sem_sync.  All calls are asynchronous on
+ * stream.
+ */
+
+/* dst[t] = src_L[idx[t]] for t < n (src_L an L-vector of this handle). */
+sem_status sem_gather(sem_handle* h, const double* src_L, const int64_t* idx, int64_t n,
+                      double* dst, void* stream);
+
+/* dst_L[idx[t]] += src[pos[t]] for t < n; src holds n_src values and the
+ * idx[t] must be distinct (each local copy receives one value per call). */
+sem_status sem_scatter_add(sem_handle* h, double* dst_L, const int64_t* idx, const int64_t* pos,
+                           int64_t n, const double* src, int64_t n_src, void* stream);
+
+/* Replace the multiplicities the dots divide by (sem_dot, the solvers'
+ * <a, b> = sum_L a b / mult) with mult_L, the number of copies of each local
+ * point over ALL ranks (>= 1; the exchange applied to the handle's own
+ * multiplicity, SEM_FIELD_MULT, gives it).  sem_dot then returns this rank's
+ * share of the unique-dof inner product. */
+sem_status sem_set_multiplicity(sem_handle* h, const double* mult_L, void* stream);
+
+/* d_L = QQ^T diag(h1 A_L + h2 B_L) inside this handle (no mask): the Jacobi
+ * diagonal before the interface exchange. */
+sem_status sem_jacobi_diag(sem_handle* h, double h1, double h2, double* d_L, void* stream);
+
+/* dinv_L = mask / d_L (0 on Dirichlet points). */
+sem_status sem_jacobi_invert(sem_handle* h, const double* d_L, double* dinv_L, void* stream);
+
+/* One PCG vector step: x += alpha p, r -= alpha w, z = dinv o r, and this
+ * rank's shares of <r, z> and <r, r> (unique-dof weights) into dots[0],
+ * dots[1] (a DEVICE array of 2 doubles). */
+sem_status sem_cg_update(sem_handle* h, double alpha, const double* p, const double* w,
+                         double* x, double* r, const double* dinv, double* z, double* dots,
+                         void* stream);
+
+/* p = z + beta p. */
+sem_status sem_cg_direction(sem_handle* h, double beta, const double* z, double* p,
+                            void* stream);
 
 /*
  * sem_apply_host -- w = mask o QQ^T A_L u with HOST buffers: copies u_host

@@ -28,5 +28,8 @@ from .api import (Handle, sem_setup, sem_destroy, sem_get_sizes, sem_get_field, 
                   sem_dot_noalloc, Batch, sem_batch_create, sem_batch_solve,
                   sem_batch_destroy, Projection, sem_proj_create, sem_proj_solve,
                   sem_proj_size, sem_proj_reset, sem_proj_destroy, Schwarz,
-                  sem_schwarz_create, sem_schwarz_apply, sem_schwarz_destroy, sem_gmres_solve)
+                  sem_schwarz_create, sem_schwarz_apply, sem_schwarz_destroy, sem_gmres_solve,
+                  sem_gather, sem_scatter_add, sem_set_multiplicity, sem_jacobi_diag,
+                  sem_jacobi_invert, sem_cg_update, sem_cg_direction)
 from .autograd import HelmholtzSolve, helmholtz_solve
+from . import partition

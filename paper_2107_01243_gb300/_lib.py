@@ -120,6 +120,13 @@ SIGNATURES = {
                                        ctypes.POINTER(SolveInfo)]),
     "sem_selftest_timeout": (ctypes.c_int, [_P, ctypes.c_double, _P]),
     "sem_dot_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "sem_gather": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
+    "sem_scatter_add": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P]),
+    "sem_set_multiplicity": (ctypes.c_int, [_P, _P, _P]),
+    "sem_jacobi_diag": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P, _P]),
+    "sem_jacobi_invert": (ctypes.c_int, [_P, _P, _P, _P]),
+    "sem_cg_update": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "sem_cg_direction": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P]),
 }
 
 _lib = None

@@ -496,3 +496,72 @@ def sem_gmres_solve(h, b, x, h1=1.0, h2=0.0, tol=1e-8, maxit=5000, restart=30, p
     if st != 0 and (raise_on_fail or st not in (SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN)):
         check(st)
     return res
+
+
+# ---------------------------------------------------------------- partition primitives
+def _dev_tensor(t, name, dtype, n=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise SemError(1, f"{name} must be a contiguous CUDA tensor")
+    if t.dtype != dtype:
+        raise SemError(1, f"{name} must be {dtype}")
+    if n is not None and t.numel() != n:
+        raise SemError(1, f"{name} has {t.numel()} values, expected {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def sem_gather(h, src, idx, dst, stream=None):
+    """dst[t] = src[idx[t]] (src an FP64 L-vector, idx int64 on the device)."""
+    n = idx.numel()
+    check(_lib.load().sem_gather(h.ptr, h._vec(src, "src", torch.float64),
+                                 _dev_tensor(idx, "idx", torch.int64), int(n),
+                                 _dev_tensor(dst, "dst", torch.float64, n), _stream(stream)))
+    return dst
+
+
+def sem_scatter_add(h, dst, idx, pos, src, stream=None):
+    """dst[idx[t]] += src[pos[t]] (dst an FP64 L-vector; the idx[t] distinct)."""
+    n = idx.numel()
+    check(_lib.load().sem_scatter_add(h.ptr, h._vec(dst, "dst", torch.float64),
+                                      _dev_tensor(idx, "idx", torch.int64),
+                                      _dev_tensor(pos, "pos", torch.int64, n), int(n),
+                                      _dev_tensor(src, "src", torch.float64), int(src.numel()),
+                                      _stream(stream)))
+    return dst
+
+
+def sem_set_multiplicity(h, mult, stream=None):
+    """The dots' multiplicities replaced by mult (copies over all ranks)."""
+    check(_lib.load().sem_set_multiplicity(h.ptr, h._vec(mult, "mult", torch.float64),
+                                           _stream(stream)))
+
+
+def sem_jacobi_diag(h, d, h1=1.0, h2=0.0, stream=None):
+    """d = QQ^T diag(h1 A_L + h2 B_L) inside the handle (no mask)."""
+    check(_lib.load().sem_jacobi_diag(h.ptr, float(h1), float(h2),
+                                      h._vec(d, "d", torch.float64), _stream(stream)))
+    return d
+
+
+def sem_jacobi_invert(h, d, dinv, stream=None):
+    """dinv = mask / d."""
+    check(_lib.load().sem_jacobi_invert(h.ptr, h._vec(d, "d", torch.float64),
+                                        h._vec(dinv, "dinv", torch.float64), _stream(stream)))
+    return dinv
+
+
+def sem_cg_update(h, alpha, p, w, x, r, dinv, z, dots, stream=None):
+    """x += alpha p, r -= alpha w, z = dinv r; dots <- this rank's <r, z>, <r, r>."""
+    f = torch.float64
+    check(_lib.load().sem_cg_update(h.ptr, float(alpha), h._vec(p, "p", f), h._vec(w, "w", f),
+                                    h._vec(x, "x", f), h._vec(r, "r", f),
+                                    h._vec(dinv, "dinv", f), h._vec(z, "z", f),
+                                    _dev_tensor(dots, "dots", f, 2), _stream(stream)))
+    return dots
+
+
+def sem_cg_direction(h, beta, z, p, stream=None):
+    """p = z + beta p."""
+    f = torch.float64
+    check(_lib.load().sem_cg_direction(h.ptr, float(beta), h._vec(z, "z", f), h._vec(p, "p", f),
+                                       _stream(stream)))
+    return p

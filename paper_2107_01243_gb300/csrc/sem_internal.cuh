@@ -200,8 +200,11 @@ struct sem_handle {
   int inner_vectors = SEM_INNER_AUTO;       // sem_set_inner_vectors
   int cg_variant = SEM_CG_STANDARD;         // sem_set_cg_variant
   sem::DevBuf<double> pipe_u, pipe_z, pipe_q, pipe_s, pipe_m, pipe_n;   // pipelined CG
-  sem::DevBuf<double> partials;             // reduction partials: [0,2B) solves, [2B,3B) sem_dot
-  sem::DevBuf<sem::CGState> state;          // [3]: outer/FP64, inner/FP32, sem_dot ticket
+  // reduction partials (B = kRedBlocks): [0,2B) solves, [2B,3B) sem_dot,
+  // [4B,4B+F) the element kernels' fused <p, Hp>, [4B+F,6B+F) sem_cg_update
+  sem::DevBuf<double> partials;
+  // [4]: outer/FP64, inner/FP32, sem_dot ticket, sem_cg_update ticket
+  sem::DevBuf<sem::CGState> state;
   // host staging for sem_apply_host
   sem::DevBuf<double> stage_in, stage_out;
   std::shared_ptr<sem::GmresWork> gmres;    // GMRES workspace, kept between solves

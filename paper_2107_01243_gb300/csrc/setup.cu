@@ -486,9 +486,9 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
     noalloc_prepare();
     h->dev_err.alloc(1);
     SEM_CUDA(cudaMemsetAsync(h->dev_err.ptr, 0, sizeof(int), s));
-    h->state.alloc(3);
-    SEM_CUDA(cudaMemsetAsync(h->state.ptr, 0, 3 * sizeof(CGState), s));
-    h->partials.alloc(4 * kRedBlocks + kFusedPartials);
+    h->state.alloc(4);
+    SEM_CUDA(cudaMemsetAsync(h->state.ptr, 0, 4 * sizeof(CGState), s));
+    h->partials.alloc(6 * kRedBlocks + kFusedPartials);
     SEM_CUDA(cudaStreamSynchronize(s));
     *out = h.release();
   });
@@ -583,7 +583,10 @@ extern "C" sem_status sem_sync(sem_handle* h, void* stream) {
     if (herr) {
       SEM_CUDA(cudaMemsetAsync(h->dev_err.ptr, 0, sizeof(int), s));
       SEM_CUDA(cudaStreamSynchronize(s));
-      throw Error((sem_status)herr, "sem_sync: a device wait timed out in an earlier call");
+      throw Error((sem_status)herr,
+                  herr == SEM_ERR_TIMEOUT
+                      ? "sem_sync: a device wait timed out in an earlier call"
+                      : "sem_sync: an earlier call found an index outside its vector");
     }
   });
 }
