@@ -94,7 +94,13 @@ def ax_source_digest(root=ROOT):
 # (smsp__inst_executed.sum).  The double-float kernel is bound by instruction
 # issue on the FP32 pipe, so its second roof is the issue rate, 152 SMs x 4
 # schedulers x the maximum SM clock.
-AX_CAPTURES = {}
+AX_CAPTURES = {
+    "ax_df_kernel<8, 1, 1>": {
+        "source": "f0463547637b6812",
+        "dram_bytes": 939_873_792 + 124_119_040,
+        "warp_instructions": 314_236_376,       # profiles/ax_df_kernel_fused_f64_e32768_n7.md
+    },
+}
 ISSUE_PEAK = 152 * 4 * 2.07e9         # warp instructions per second
 
 
