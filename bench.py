@@ -615,24 +615,46 @@ def run_batch(sem, torch, dev, n_problems=64, e_hi=32768):
     npts = [h.n_local for h in hs]
     batch = sem.sem_batch_create(hs)
     xb = [torch.empty_like(b) for b in bs]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    infos = sem.sem_batch_solve(batch, bs, xb, [1.0] * len(hs), lams, tol=1e-8)
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
+
+    def batched(concurrent):
+        sem.sem_batch_set_concurrency(batch, concurrent)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        inf = sem.sem_batch_solve(batch, bs, xb, [1.0] * len(hs), lams, tol=1e-8)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, inf
+
+    batched(False)                     # warm-up (graph instantiation, first-call set-up)
+    tb, infos = batched(False)         # order classes one after another (the default)
+    tcon, _ = batched(True)            # the same as concurrent graph branches
     xs_ = [torch.empty_like(b) for b in bs]
     torch.cuda.synchronize()
+    seq, tper = [], []
     t0 = time.perf_counter()
-    seq = [sem.sem_cg_solve(h, b, x, h1=1.0, h2=lam, tol=1e-8, precision=sem.SEM_SOLVE_MIXED)
-           for h, b, x, lam in zip(hs, bs, xs_, lams)]
+    for h, b, x, lam in zip(hs, bs, xs_, lams):
+        t1 = time.perf_counter()
+        seq.append(sem.sem_cg_solve(h, b, x, h1=1.0, h2=lam, tol=1e-8,
+                                    precision=sem.SEM_SOLVE_MIXED))
+        tper.append(time.perf_counter() - t1)         # the call synchronises
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
     work = sum(n * i["iters"] for n, i in zip(npts, infos))
+    per_order = {}
+    for N in sorted({q["N"] for q in probs}):
+        ix = [k for k, q in enumerate(probs) if q["N"] == N]
+        w_n = sum(npts[k] * seq[k]["iters"] for k in ix)
+        per_order[str(N)] = {"problems": len(ix), "local_points": int(sum(npts[k] for k in ix)),
+                             "sequential_seconds": sum(tper[k] for k in ix),
+                             "gdof_iters_per_s": w_n / sum(tper[k] for k in ix) / 1e9}
     out = {"workload": f"{len(hs)} Helmholtz problems, E in [512, {e_hi}], N in {{5,7,9}}, "
                        "h2 in [0.1, 10], deformed boxes, tol 1e-8, FP32 inner / FP64 refine",
            "local_points": int(sum(npts)),
-           "batched_seconds": tb, "sequential_seconds": ts, "speedup": ts / tb,
+           "batched_seconds": tb, "batched_concurrent_classes_seconds": tcon,
+           "sequential_seconds": ts, "speedup": ts / tb,
            "gdof_iters_per_s": work / tb / 1e9,
+           "sequential_per_order": per_order,
+           "note": "each timing after one untimed batched solve; sequential = the same "
+                   "problems through sem_cg_solve one after another",
            "all_converged": all(i["status"] == "SEM_OK" for i in infos),
            "max_rel_res": max(i["rel_res"] for i in infos),
            "iters_total": int(sum(i["iters"] for i in infos)),

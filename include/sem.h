@@ -446,6 +446,14 @@ sem_status sem_batch_solve(sem_batch* b, const double* const* b_L, double* const
                            const double* h1, const double* h2, const sem_solve_opts* opts,
                            sem_solve_info* infos);
 sem_status sem_batch_destroy(sem_batch* b);
+/* sem_batch_set_concurrency: concurrent = 1 launches the element kernels of
+ * the order classes of an inner iteration as concurrent branches (side
+ * streams forked from and joined back into the solve's stream; parallel paths
+ * of the iteration graph), so that the persistent grids of the classes can
+ * fill one another's tails; 0 (the default) launches them one after another.
+ * The classes touch disjoint problems, so either way computes the same
+ * iteration.  SEM_ERR_ARG for a NULL batch or a flag other than 0 or 1. */
+sem_status sem_batch_set_concurrency(sem_batch* b, int concurrent);
 
 /*
  * Projection onto previous solutions for successive right-hand sides (§4,

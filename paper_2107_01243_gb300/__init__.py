@@ -26,7 +26,7 @@ from .api import (Handle, sem_setup, sem_destroy, sem_get_sizes, sem_get_field, 
                   sem_selftest_timeout, sem_set_f64_kernel, sem_set_dssum_kernel,
                   sem_autotune, sem_set_tuning,
                   sem_dot_noalloc, Batch, sem_batch_create, sem_batch_solve,
-                  sem_batch_destroy, Projection, sem_proj_create, sem_proj_solve,
+                  sem_batch_destroy, sem_batch_set_concurrency, Projection, sem_proj_create, sem_proj_solve,
                   sem_proj_size, sem_proj_reset, sem_proj_destroy, Schwarz,
                   sem_schwarz_create, sem_schwarz_apply, sem_schwarz_destroy, sem_gmres_solve,
                   sem_gather, sem_scatter_add, sem_set_multiplicity, sem_jacobi_diag,

@@ -102,6 +102,7 @@ SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]),
     "sem_batch_destroy": (ctypes.c_int, [_P]),
+    "sem_batch_set_concurrency": (ctypes.c_int, [_P, ctypes.c_int]),
     "sem_sync": (ctypes.c_int, [_P, _P]),
     "sem_autotune": (ctypes.c_int, [_P, _P, ctypes.c_void_p]),
     "sem_set_tuning": (ctypes.c_int, [_P, ctypes.c_void_p]),

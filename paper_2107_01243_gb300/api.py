@@ -337,6 +337,12 @@ def sem_batch_destroy(batch):
         check(_lib.load().sem_batch_destroy(ptr))
 
 
+def sem_batch_set_concurrency(batch, concurrent=True):
+    """Launch the order classes' element kernels as concurrent branches (True)
+    or one after another (False, the library's default)."""
+    check(_lib.load().sem_batch_set_concurrency(batch.ptr, int(bool(concurrent))))
+
+
 def sem_batch_solve(batch, bs, xs, h1s, h2s, tol=1e-8, maxit=20000, inner_tol=1e-4,
                     max_outer=30, check_every=16, use_graph=True, stream=None):
     """Solve every problem of the batch (FP32 inner / FP64 refinement);

@@ -589,6 +589,18 @@ struct sem_batch {
   int ngitems = 0;
   int nitems = 0, maxP = 0;
   cudaStream_t stream = nullptr;
+  // per-order element launches as concurrent branches (fork on fork_ev, one
+  // side stream per order class, joined back by join_ev) when concurrent
+  bool concurrent = false;
+  cudaStream_t side[kMaxP / 2] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kMaxP / 2] = {};
+  ~sem_batch() {
+    for (int q = 0; q < kMaxP / 2; ++q) {
+      if (join_ev[q]) cudaEventDestroy(join_ev[q]);
+      if (side[q]) cudaStreamDestroy(side[q]);
+    }
+    if (fork_ev) cudaEventDestroy(fork_ev);
+  }
 };
 
 namespace sem {
@@ -690,20 +702,45 @@ static void launch_bfinish(sem_batch* bt, cudaStream_t s) {
   }
 }
 
+// launch(P, stream) for every order class present: on s one after another,
+// or (bt->concurrent, two or more classes) as branches forked from s on the
+// side streams and joined back into s, so that the classes' persistent grids
+// fill one another's tails; in a stream capture the branches become parallel
+// paths of the graph
+template <class F>
+static void for_classes(sem_batch* bt, cudaStream_t s, F launch) {
+  int ncl = 0;
+  for (int P = 2; P <= kMaxP; P += 2) ncl += bt->ncls[P] ? 1 : 0;
+  if (!bt->concurrent || ncl < 2) {
+    for (int P = 2; P <= kMaxP; P += 2)
+      if (bt->ncls[P]) launch(P, s);
+    return;
+  }
+  SEM_CUDA(cudaEventRecord(bt->fork_ev, s));
+  int q = 0;
+  for (int P = 2; P <= kMaxP; P += 2) {
+    if (!bt->ncls[P]) continue;
+    SEM_CUDA(cudaStreamWaitEvent(bt->side[q], bt->fork_ev, 0));
+    launch(P, bt->side[q]);
+    SEM_CUDA(cudaEventRecord(bt->join_ev[q], bt->side[q]));
+    ++q;
+  }
+  for (int k = 0; k < q; ++k) SEM_CUDA(cudaStreamWaitEvent(s, bt->join_ev[k], 0));
+}
+
 // one inner iteration over the batch (captured into a graph)
 static void batch_iteration(sem_batch* bt, cudaStream_t s) {
   const int n = (int)bt->hs.size();
   if (bt->glob) {
-    for (int P = 2; P <= kMaxP; P += 2) {
-      if (!bt->ncls[P]) continue;
+    for_classes(bt, s, [&](int P, cudaStream_t t) {
       switch (P) {
-        case 2: launch_bglob<2>(bt, s); break;
-        case 4: launch_bglob<4>(bt, s); break;
-        case 6: launch_bglob<6>(bt, s); break;
-        case 8: launch_bglob<8>(bt, s); break;
-        default: launch_bglob<10>(bt, s); break;
+        case 2: launch_bglob<2>(bt, t); break;
+        case 4: launch_bglob<4>(bt, t); break;
+        case 6: launch_bglob<6>(bt, t); break;
+        case 8: launch_bglob<8>(bt, t); break;
+        default: launch_bglob<10>(bt, t); break;
       }
-    }
+    });
     const int gblocks = std::min(bt->ngitems, 8 * kNumSMs);
     bgpw_kernel<<<gblocks, 256, 0, s>>>(bt->probs.ptr, bt->gitem_prob.ptr, n, bt->ngitems,
                                         bt->partials.ptr, bt->tickets.ptr);
@@ -716,28 +753,22 @@ static void batch_iteration(sem_batch* bt, cudaStream_t s) {
     return;
   }
   if (bt->fused) {
-    for (int P = 6; P <= kMaxP; P += 2) {
-      if (!bt->ncls[P]) continue;
-      if (P == 6) launch_bapply<6>(bt, s);
-      else if (P == 8) launch_bapply<8>(bt, s);
-      else launch_bapply<10>(bt, s);
-    }
-    for (int P = 6; P <= kMaxP; P += 2) {
-      if (!bt->ncls[P]) continue;
-      if (P == 6) launch_bfinish<6>(bt, s);
-      else if (P == 8) launch_bfinish<8>(bt, s);
-      else launch_bfinish<10>(bt, s);
-    }
-  }
-  for (int P = 2; P <= kMaxP && !bt->fused; P += 2) {
-    if (!bt->ncls[P]) continue;
-    switch (P) {
-      case 2: launch_bax<2>(bt, s); break;
-      case 4: launch_bax<4>(bt, s); break;
-      case 6: launch_bax<6>(bt, s); break;
-      case 8: launch_bax<8>(bt, s); break;
-      default: launch_bax<10>(bt, s); break;
-    }
+    // each class: its element launch, then its finishing passes
+    for_classes(bt, s, [&](int P, cudaStream_t t) {
+      if (P == 6) { launch_bapply<6>(bt, t); launch_bfinish<6>(bt, t); }
+      else if (P == 8) { launch_bapply<8>(bt, t); launch_bfinish<8>(bt, t); }
+      else { launch_bapply<10>(bt, t); launch_bfinish<10>(bt, t); }
+    });
+  } else {
+    for_classes(bt, s, [&](int P, cudaStream_t t) {
+      switch (P) {
+        case 2: launch_bax<2>(bt, t); break;
+        case 4: launch_bax<4>(bt, t); break;
+        case 6: launch_bax<6>(bt, t); break;
+        case 8: launch_bax<8>(bt, t); break;
+        default: launch_bax<10>(bt, t); break;
+      }
+    });
   }
   if (!bt->fused) {
     const int dblocks = (int)std::min<long long>((bt->Dtot + 255) / 256, 32LL * kNumSMs);
@@ -937,8 +968,21 @@ extern "C" sem_status sem_batch_create(sem_handle* const* handles, int n, sem_ba
     bt->states.alloc(n);
     SEM_CUDA(cudaMemset(bt->states.ptr, 0, n * sizeof(CGState)));
     bt->probs.alloc(n);
+    for (int q = 0; q < kMaxP / 2; ++q) {
+      SEM_CUDA(cudaStreamCreateWithFlags(&bt->side[q], cudaStreamNonBlocking));
+      SEM_CUDA(cudaEventCreateWithFlags(&bt->join_ev[q], cudaEventDisableTiming));
+    }
+    SEM_CUDA(cudaEventCreateWithFlags(&bt->fork_ev, cudaEventDisableTiming));
     SEM_CUDA(cudaDeviceSynchronize());
     *out = bt.release();
+  });
+}
+
+extern "C" sem_status sem_batch_set_concurrency(sem_batch* bt, int concurrent) {
+  return guarded("sem_batch_set_concurrency", [&] {
+    SEM_REQUIRE(bt, "sem_batch_set_concurrency: null batch");
+    SEM_REQUIRE(concurrent == 0 || concurrent == 1, "sem_batch_set_concurrency: flag not 0 or 1");
+    bt->concurrent = concurrent != 0;
   });
 }
 

@@ -38,15 +38,19 @@ def _setup(problems):
     return hs, oracles, bs
 
 
+@pytest.mark.parametrize("concurrent", [True, False], ids=["branches", "serial"])
 @pytest.mark.parametrize("use_graph", [True, False])
 @pytest.mark.parametrize("problems", [PROBLEMS, PROBLEMS_FUSED], ids=["unfused", "fused"])
 @pytest.mark.parametrize("inner", [sem.SEM_INNER_AUTO, sem.SEM_INNER_LOCAL],
                          ids=["global-vectors", "local-vectors"])
-def test_batch_matches_oracle_and_single_solves(use_graph, problems, inner):
+def test_batch_matches_oracle_and_single_solves(use_graph, problems, inner, concurrent):
+    """The order classes' element launches one after another (the default)
+    or as concurrent branches (parallel paths of the iteration graph)."""
     hs, oracles, bs = _setup(problems)
     for h in hs:
         sem.sem_set_inner_vectors(h, inner)
     batch = sem.sem_batch_create(hs)
+    sem.sem_batch_set_concurrency(batch, concurrent)
     xs = [torch.empty_like(b) for _, b in bs]
     lams = [lam for _, _, lam in problems]
     infos = sem.sem_batch_solve(batch, [b for _, b in bs], xs, [1.0] * len(hs), lams, tol=1e-8,
@@ -108,12 +112,13 @@ def test_batch_large_grids_walk_across_problems():
     lams = [lam for _, _, lam in PROBLEMS_LARGE]
     batch = sem.sem_batch_create(hs)
     runs = {}
-    for use_graph in (True, False):
+    for use_graph, concurrent in ((True, False), (False, False), (True, True)):
+        sem.sem_batch_set_concurrency(batch, concurrent)
         xs = [torch.empty_like(b) for b in bs]
         infos = sem.sem_batch_solve(batch, bs, xs, [1.0] * len(hs), lams, tol=1e-8,
                                     check_every=8, use_graph=use_graph)
         assert all(i["status"] == "SEM_OK" for i in infos), infos
-        runs[use_graph] = (xs, infos)
+        runs[(use_graph, concurrent)] = (xs, infos)
     sem.sem_batch_destroy(batch)
     for q, ((nel, N, lam), h, b, b_ref, o) in enumerate(zip(PROBLEMS_LARGE, hs, bs, refs,
                                                               oracles)):
