@@ -124,7 +124,7 @@ k_sz(T* __restrict__ w, uint32_t layer, uint32_t total, const CGState* __restric
 }
 
 int sweep_blocks(long long total) {
-  return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 16LL * kNumSMs));
+  return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 16LL * sem_num_sms()));
 }
 
 // the finishing passes on a box of nelx x nely x nelz elements starting at w

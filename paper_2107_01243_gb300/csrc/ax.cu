@@ -179,7 +179,7 @@ template <class T>
 void launch_local_diag(const sem_handle* h, const OpData<T>& op, T* d, T h1, T h2, const T* h1f,
                        cudaStream_t s) {
   int64_t nL = h->nL;
-  int blocks = (int)std::min<int64_t>((nL + 255) / 256, 16 * kNumSMs);
+  int blocks = (int)std::min<int64_t>((nL + 255) / 256, 16 * sem_num_sms());
   local_diag_kernel<T><<<blocks, 256, 0, s>>>(h->P, nL, op.G.ptr, op.B.ptr, h1f, h1, h2,
                                               op.D.ptr, d);
   SEM_CHECK_LAUNCH();

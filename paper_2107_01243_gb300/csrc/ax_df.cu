@@ -426,17 +426,6 @@ static size_t df_smem_bytes(bool helm) {
   return 128 + STAGES * SB + 4 * (size_t)L::VOL * sizeof(float2);
 }
 
-static int df_num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-      n = kNumSMs;
-  }
-  return n;
-}
-
 // copies D and its even-odd halves for this order into constant memory (once
 // per process: the library drives one device, see sem_setup)
 static void df_upload_d(const sem_handle* h) {
@@ -513,7 +502,6 @@ static void df_prepare_p(const sem_handle* h) {
     df_occupancy<P, 1, true>(helm != 0);
     df_occupancy<P, 2, true>(helm != 0);
   }
-  df_num_sms();
   df_upload_d(h);
 }
 
@@ -546,7 +534,7 @@ static int launch_df_p(const sem_handle* h, const double* u, double* w, double h
   const int E = slab ? slab->E : (int)h->E;
   const int64_t e0 = slab ? slab->e0 : 0;
   constexpr int64_t P3 = (int64_t)P * P * P;
-  int grid = (int)std::min<int64_t>(E, (int64_t)o * df_num_sms());
+  int grid = (int)std::min<int64_t>(E, (int64_t)o * sem_num_sms());
   if (grid < 1) grid = 1;
   if (pwst) grid = std::min(grid, kFusedPartials);
   const FuseBox fb = slab ? slab->fb : FuseBox{h->nelx, h->nely, h->nelz, h->faces};

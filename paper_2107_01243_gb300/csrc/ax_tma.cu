@@ -165,17 +165,6 @@ static size_t tma_smem_bytes(int nf) {
   return 128 + (size_t)(STAGES * nf + 3) * K * P * P * P * sizeof(T);
 }
 
-static int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-      n = kNumSMs;
-  }
-  return n;
-}
-
 // returns the grid it launched (the fused operator's later passes need it)
 template <int P, class T, int STAGES, int K, bool FUSE = false>
 static int launch_tma_p(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1, T h2,
@@ -200,7 +189,7 @@ static int launch_tma_p(const sem_handle* h, const OpData<T>& op, const T* u, T*
   for (int a = 0; a < P * P; ++a) D.d[a] = (T)h->Dh[a];
   const int E = (int)h->E;
   const int nitems = (E + K - 1) / K;
-  int grid = std::min<int64_t>(nitems, (int64_t)o * num_sms());
+  int grid = std::min<int64_t>(nitems, (int64_t)o * sem_num_sms());
   if (grid < 1) grid = 1;
   if (pwst) grid = std::min(grid, kFusedPartials);
   const FuseBox fb{h->nelx, h->nely, h->nelz, h->faces};

@@ -670,7 +670,7 @@ static void launch_bglob(sem_batch* bt, cudaStream_t s) {
 }
 
 static int pass_blocks(long long total) {
-  return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 16LL * kNumSMs));
+  return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 16LL * sem_num_sms()));
 }
 
 template <int P>
@@ -741,7 +741,7 @@ static void batch_iteration(sem_batch* bt, cudaStream_t s) {
         default: launch_bglob<10>(bt, t); break;
       }
     });
-    const int gblocks = std::min(bt->ngitems, 8 * kNumSMs);
+    const int gblocks = std::min(bt->ngitems, 8 * sem_num_sms());
     bgpw_kernel<<<gblocks, 256, 0, s>>>(bt->probs.ptr, bt->gitem_prob.ptr, n, bt->ngitems,
                                         bt->partials.ptr, bt->tickets.ptr);
     SEM_CHECK_LAUNCH();
@@ -771,11 +771,11 @@ static void batch_iteration(sem_batch* bt, cudaStream_t s) {
     });
   }
   if (!bt->fused) {
-    const int dblocks = (int)std::min<long long>((bt->Dtot + 255) / 256, 32LL * kNumSMs);
+    const int dblocks = (int)std::min<long long>((bt->Dtot + 255) / 256, 32LL * sem_num_sms());
     bdssum_kernel<<<dblocks, 256, 0, s>>>(bt->probs.ptr, bt->d_off.ptr, n, bt->Dtot);
     SEM_CHECK_LAUNCH();
   }
-  const int vblocks = std::min(bt->nitems, 8 * kNumSMs);
+  const int vblocks = std::min(bt->nitems, 8 * sem_num_sms());
   bpw_kernel<<<vblocks, 256, 0, s>>>(bt->probs.ptr, bt->item_prob.ptr, n, bt->nitems,
                                      bt->partials.ptr, bt->tickets.ptr);
   SEM_CHECK_LAUNCH();
@@ -1090,12 +1090,12 @@ extern "C" sem_status sem_batch_solve(sem_batch* bt, const double* const* b_L,
       }
       const BProb& b = bt->hp[p];
       if (bt->glob) {
-        bginit_kernel<<<std::min(b.g_cnt, 4 * kNumSMs), 256, 0, own>>>(
+        bginit_kernel<<<std::min(b.g_cnt, 4 * sem_num_sms()), 256, 0, own>>>(
             bt->probs.ptr, bt->gitem_prob.ptr, b.g_off, b.g_cnt, bt->ngitems, bt->partials.ptr,
             bt->tickets.ptr, inner_target(o.inner_tol, o.tol, rel[p]),
             std::max(1, o.maxit - iters[p]));
       } else {
-        binit_kernel<<<std::min(b.v_cnt, 4 * kNumSMs), 256, 0, own>>>(
+        binit_kernel<<<std::min(b.v_cnt, 4 * sem_num_sms()), 256, 0, own>>>(
             bt->probs.ptr, bt->item_prob.ptr, b.v_off, b.v_cnt, bt->nitems, bt->partials.ptr,
             bt->tickets.ptr, inner_target(o.inner_tol, o.tol, rel[p]),
             std::max(1, o.maxit - iters[p]));

@@ -592,7 +592,7 @@ k_pipe_update(int64_t n, double* __restrict__ x, double* __restrict__ r, double*
 }
 
 static int ew_grid(int64_t n) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * kNumSMs));
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * sem_num_sms()));
 }
 
 // ------------------------------------------------------------------ host drivers

@@ -38,7 +38,7 @@ void launch_dssum(const sem_handle* h, T* w, bool apply_mask, const CGState* st,
   const int nm = apply_mask ? (int)h->nmasked : 0;
   const int total = nseg + nm;
   if (total == 0) return;
-  int blocks = std::min((total + 255) / 256, 32 * kNumSMs);
+  int blocks = std::min((total + 255) / 256, 32 * sem_num_sms());
   dssum_kernel<T><<<blocks, 256, 0, s>>>(w, h->seg_ptr.ptr, h->seg_idx.ptr, nseg,
                                          h->masked_idx.ptr, nm, st);
   SEM_CHECK_LAUNCH();

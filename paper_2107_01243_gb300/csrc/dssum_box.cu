@@ -135,7 +135,7 @@ template <int N, class T>
 static void launch_box_n(const BoxDims& d, T* w, const int* masked, int nm, const CGState* st,
                          cudaStream_t s) {
   const uint32_t total = d.nSX + d.nSY + d.nSZ + (uint32_t)nm;
-  const int blocks = (int)std::min<long long>((total + 255) / 256, 32LL * kNumSMs);
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 32LL * sem_num_sms());
   dssum_box_kernel<N, T><<<blocks, 256, 0, s>>>(w, d, masked, nm, st);
   SEM_CHECK_LAUNCH();
 }

@@ -233,7 +233,7 @@ static void launch_glob_p(const sem_handle* h, const float* u, float* w, float h
   DMat<P, float> D;
   for (int a = 0; a < P * P; ++a) D.d[a] = (float)h->Dh[a];
   const int E = (int)h->E;
-  int grid = (int)std::min<int64_t>(E, (int64_t)o * kNumSMs);
+  int grid = (int)std::min<int64_t>(E, (int64_t)o * sem_num_sms());
   if (pwst) grid = std::min(grid, kFusedPartials);
   if (grid < 1) grid = 1;
   kern<<<grid, P * P, smem, s>>>(u, w, h->f32.G.ptr, h->f32.B.ptr, h1, h2, D, E, make_gbox(h), st,
@@ -310,7 +310,7 @@ __global__ void k_add_from_global(int64_t nL, double* __restrict__ x, const floa
 }
 
 static int conv_grid(int64_t n) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * kNumSMs));
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * sem_num_sms()));
 }
 
 template <class Tin>

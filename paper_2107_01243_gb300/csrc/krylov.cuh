@@ -64,7 +64,7 @@ __global__ void k_scale2(int64_t n, const double* __restrict__ a, const double* 
 }
 
 inline int lin_grid(int64_t n) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * kNumSMs));
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * sem_num_sms()));
 }
 
 }  // namespace

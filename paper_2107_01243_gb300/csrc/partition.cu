@@ -114,7 +114,7 @@ __global__ void k_cg_direction(int64_t n, double beta, const double* __restrict_
 }
 
 static int part_grid(int64_t n) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8LL * kNumSMs));
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8LL * sem_num_sms()));
 }
 
 }  // namespace sem

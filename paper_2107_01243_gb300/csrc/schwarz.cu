@@ -469,7 +469,7 @@ __global__ void k_sw_combine(int64_t nL, const float* __restrict__ zg, const flo
 }
 
 int ew_blocks(int64_t n) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * kNumSMs));
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * sem_num_sms()));
 }
 
 }  // namespace
@@ -504,7 +504,7 @@ void launch_local(sem_schwarz* sw, const float* rg, float* zg, cudaStream_t s) {
     SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, 0));
     if (occ < 1) occ = 1;
   }
-  const int grid = (int)std::min<int64_t>(h->E, (int64_t)occ * kNumSMs);
+  const int grid = (int)std::min<int64_t>(h->E, (int64_t)occ * sem_num_sms());
   kern<<<grid, T, 0, s>>>(rg, zg, sw->rc.ptr, sw->tab.ptr, sw->prm, (int)h->E);
   SEM_CHECK_LAUNCH();
 }
@@ -581,7 +581,7 @@ void build_coarse(sem_schwarz* sw, cudaStream_t s) {
     k_vertex_field<<<ew_blocks(nL), 256, 0, s>>>(nL, h->P, v, xi.ptr, phi.ptr);
     SEM_CHECK_LAUNCH();
     launch_ax<double>(h, h->f64, phi.ptr, hphi.ptr, sw->h1, sw->h2, nullptr, nullptr, s);
-    k_coarse_entries<<<(int)std::min<int64_t>(E, 8 * kNumSMs), 128, 0, s>>>(
+    k_coarse_entries<<<(int)std::min<int64_t>(E, 8 * sem_num_sms()), 128, 0, s>>>(
         (int)E, h->P, v, hphi.ptr, xi.ptr, sw->K.ptr, dg.ptr);
     SEM_CHECK_LAUNCH();
   }

@@ -22,11 +22,18 @@ struct HostPipe;                     // apply.cu
 
 constexpr int kMaxN = 10;            // highest supported polynomial order
 constexpr int kMaxP = kMaxN + 1;
-constexpr int kNumSMs = 152;         // GB300: 2 dies x 76 SMs
-constexpr int kRedBlocks = 4 * kNumSMs;   // blocks of every reduction kernel
+// blocks of every reduction kernel (four per SM of a 152-SM GB300).  A fixed
+// count, not the device's: the partial sums, and so the rounding of every dot
+// product, are then the same on any device.
+constexpr int kRedBlocks = 608;
 constexpr int kRedThreads = 256;
 constexpr int kFusedPartials = 2048;   // partials of the element kernels' fused <p, Hp>
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;   // bounded device waits give up after 2 s
+
+// SM count of the device the library is bound to, set by the first sem_setup
+// (every entry point that launches a kernel holds a handle, so it is set by then).
+// Grids of the grid-stride kernels are sized in multiples of it.
+int sem_num_sms();
 
 // ------------------------------------------------------------------ errors
 struct Error : std::runtime_error {

@@ -242,7 +242,7 @@ __global__ void recip_kernel(const float* __restrict__ src, D* __restrict__ dst,
 
 template <class S, class D>
 static void convert(const S* src, D* dst, int64_t n, cudaStream_t s) {
-  int blocks = (int)std::min<int64_t>((n + 255) / 256, 8 * kNumSMs);
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 8 * sem_num_sms());
   if (blocks < 1) blocks = 1;
   convert_kernel<S, D><<<blocks, 256, 0, s>>>(src, dst, n);
   SEM_CHECK_LAUNCH();
@@ -250,7 +250,7 @@ static void convert(const S* src, D* dst, int64_t n, cudaStream_t s) {
 
 static int grid_for(int64_t n, int threads = 256) {
   int64_t b = (n + threads - 1) / threads;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 16 * kNumSMs));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 16 * sem_num_sms()));
 }
 
 // ------------------------------------------------------------------ topology (host)
@@ -380,6 +380,9 @@ extern "C" const char* sem_last_error(void) { return g_last_error.c_str(); }
 // and kernel attributes are set up once.  The first sem_setup binds the
 // device current at that call; a later one on another device is refused.
 static std::atomic<int> g_bound_device{-1};
+static std::atomic<int> g_num_sms{0};
+
+int sem::sem_num_sms() { return g_num_sms.load(std::memory_order_relaxed); }
 
 extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_flags,
                                 void* stream, sem_handle** out) {
@@ -404,6 +407,12 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
       throw Error(SEM_ERR_STATE, "sem_setup: the library drives one CUDA device per process "
                                  "(bound to device " + std::to_string(bound) + ", current " +
                                  std::to_string(dev) + ")");
+    if (g_num_sms.load(std::memory_order_relaxed) == 0) {
+      int sms = 0;
+      SEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      SEM_REQUIRE(sms > 0, "sem_setup: the device reports no SMs");
+      g_num_sms.store(sms, std::memory_order_relaxed);
+    }
     cudaStream_t s = (cudaStream_t)stream;
     std::unique_ptr<sem_handle> h(new sem_handle());
     h->N = N;

@@ -77,8 +77,8 @@ def test_batch_rejects_even_order():
 # Problems large enough that every persistent grid of the batched inner solve
 # on global vectors walks its work more than once and crosses from one problem
 # to the next inside a CTA: per order class more elements than 2 x 8 CTAs per
-# SM x 152 SMs, and more global-vector work items (16,384 values each) than the
-# 8 x 152 blocks of the vector kernels.
+# SM x the device's SMs, and more global-vector work items (16,384 values each)
+# than the 8 blocks per SM of the vector kernels.
 PROBLEMS_LARGE = [((16, 16, 16), 9, 0.7), ((16, 16, 15), 9, 3.1), ((14, 14, 14), 7, 1.7),
                   ((16, 16, 16), 9, 9.5), ((12, 12, 12), 5, 0.4), ((16, 15, 16), 9, 2.2),
                   ((16, 16, 16), 7, 5.0), ((15, 16, 16), 9, 0.9), ((16, 16, 16), 9, 4.4),
@@ -87,7 +87,7 @@ GCHUNK = 16384
 
 
 def test_batch_large_grids_walk_across_problems():
-    nsm = 152
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
     per_order = {}
     items = 0
     for nel, N, _ in PROBLEMS_LARGE:
