@@ -16,7 +16,12 @@
 //   G        every point: (WR, WS, WT) = h1 G (UR, US, UT), in place
 //   backward group g: lines of W along direction g, in place          (D^T)
 //   final    w = CR + CS + CT (+ h2 B u) -> double
-// Sums use exact float transformations (TwoSum, FMA product errors).
+// Sums use exact float transformations (TwoSum, FMA product errors).  At
+// P = 8 the G products and the backward contractions use the cheaper
+// extraction form (df.cuh: 7 instead of 12 instructions a term); the forward
+// derivatives keep TwoSum, whose error stays relative to the products where
+// smooth u makes the derivatives cancel (the extraction form lost 2-3 bits
+// there in a float32 emulation against the FP64 oracle).
 // The shared-memory layout (DFLayout) keeps the line and point accesses free
 // of bank conflicts; each thread computes its positions once per launch.
 #include "sem_internal.cuh"
@@ -35,6 +40,9 @@ __constant__ float c_df_dl[kMaxP + 1][kMaxP * kMaxP];
 // [0: high, 1: low][i * (P/2) + l], M = D or D^T
 constexpr int kMaxH = kMaxP / 2 + 1;
 __constant__ float c_df_eo[kMaxP + 1][2][2][2][kMaxH * kMaxH];
+// bounds of the transposed even-odd rows: [0: A, 1: S][i] = (1 + 2^-18) sum_l
+// |high part of A_il| (resp. S_il)
+__constant__ float c_df_rb[kMaxP + 1][2][kMaxH];
 
 // h1 = m1 2^t1, h2 = m2 2^t2 with the mantissas as pairs (t = 0 while
 // |h| lies in [2^-16, 2^16), see df.cuh)
@@ -105,6 +113,62 @@ __device__ __forceinline__ void line_task(const float2* in, float2* out, const i
   }
 #pragma unroll
   for (int i = 0; i < P; ++i) out[off[i]] = make_float2(yh[i], yl[i]);
+}
+
+// The transposed line task y_i = sum_l D_li x_l with extraction dots (df.cuh):
+// the same even-odd split, with one power-of-two bound per output pair,
+// sigma_i >= sum_l |A_il| |o_l| + |S_il| |e_l|, taken from the row sums of
+// the tables (c_df_rb, enlarged by 2^-18 to cover the roundings of the bound)
+// and the largest |o| and |e| of the line.  Both dots of a pair share sigma_i,
+// so their sums y_i = SP + SM and y_{N-i} = SP - SM are exact as well.
+template <int P>
+__device__ __forceinline__ void line_task_xt(const float2* in, float2* out, const int (&off)[P]) {
+  static_assert(P % 2 == 0, "even-odd split needs an even number of points");
+  constexpr int H = P / 2, N = P - 1;
+  float xh[P], xl[P];
+#pragma unroll
+  for (int l = 0; l < P; ++l) {
+    const float2 v = in[off[l]];
+    xh[l] = v.x;
+    xl[l] = v.y;
+  }
+  float eh[H], el[H], oh[H], ol[H];
+  float me = 0.0f, mo = 0.0f;
+#pragma unroll
+  for (int l = 0; l < H; ++l) {
+    dfadd(xh[l], xl[l], xh[N - l], xl[N - l], eh[l], el[l]);
+    dfadd(xh[l], xl[l], -xh[N - l], -xl[N - l], oh[l], ol[l]);
+    me = fmaxf(me, fabsf(eh[l]));
+    mo = fmaxf(mo, fabsf(oh[l]));
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const float sig = df_pow2_ceil(__fmaf_rn(c_df_rb[P][0][i], mo, __fmul_rn(c_df_rb[P][1][i], me)));
+    float SP, EP, SM, EM;
+    xmac0(c_df_eo[P][1][0][0][i * H], c_df_eo[P][1][0][1][i * H], oh[0], ol[0], sig, SP, EP);
+    xmac0(c_df_eo[P][1][1][0][i * H], c_df_eo[P][1][1][1][i * H], eh[0], el[0], sig, SM, EM);
+#pragma unroll
+    for (int l = 1; l < H; ++l) {
+      xmac(c_df_eo[P][1][0][0][i * H + l], c_df_eo[P][1][0][1][i * H + l], oh[l], ol[l], sig, SP,
+           EP);
+      xmac(c_df_eo[P][1][1][0][i * H + l], c_df_eo[P][1][1][1][i * H + l], eh[l], el[l], sig, SM,
+           EM);
+    }
+    // the line's inputs are all in registers, so the outputs may go out now
+    out[off[i]] = make_float2(__fadd_rn(SP, SM), __fadd_rn(EP, EM));
+    out[off[N - i]] = make_float2(__fsub_rn(SP, SM), __fsub_rn(EP, EM));
+  }
+}
+
+// sum of three products g_a * v_a with extraction against sigma (df.cuh)
+__device__ __forceinline__ void dot3_x(float2 g0, float2 g1, float2 g2, float2 v0, float2 v1,
+                                       float2 v2, float sig, float& oh, float& ol) {
+  float S, E;
+  xmac0(g0.x, g0.y, v0.x, v0.y, sig, S, E);
+  xmac(g1.x, g1.y, v1.x, v1.y, sig, S, E);
+  xmac(g2.x, g2.y, v2.x, v2.y, sig, S, E);
+  oh = S;
+  ol = E;
 }
 
 // sum of three products g_a * v_a
@@ -304,9 +368,21 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       const float2 g12 = sg[3 * P3 + q], g13 = sg[4 * P3 + q], g23 = sg[5 * P3 + q];
       const float2 ur = R[0][at], us = R[1][at], ut = R[2][at];
       float rh, rl, sh, sl, th, tl;
-      dot3_df(g11, g12, g13, ur, us, ut, rh, rl);
-      dot3_df(g12, g22, g23, ur, us, ut, sh, sl);
-      dot3_df(g13, g23, g33, ur, us, ut, th, tl);
+      if constexpr (P == 8) {
+        // one bound for the point's three rows: 3 max|G| max|u'| (1 + 2^-18)
+        const float mg = fmaxf(fmaxf(fmaxf(fabsf(g11.x), fabsf(g22.x)), fmaxf(fabsf(g33.x),
+                                                                           fabsf(g12.x))),
+                               fmaxf(fabsf(g13.x), fabsf(g23.x)));
+        const float mu = fmaxf(fmaxf(fabsf(ur.x), fabsf(us.x)), fabsf(ut.x));
+        const float sig = df_pow2_ceil(__fmul_rn(__fmul_rn(mg, 3.0f * (1.0f + 0x1p-18f)), mu));
+        dot3_x(g11, g12, g13, ur, us, ut, sig, rh, rl);
+        dot3_x(g12, g22, g23, ur, us, ut, sig, sh, sl);
+        dot3_x(g13, g23, g33, ur, us, ut, sig, th, tl);
+      } else {
+        dot3_df(g11, g12, g13, ur, us, ut, rh, rl);
+        dot3_df(g12, g22, g23, ur, us, ut, sh, sl);
+        dot3_df(g13, g23, g33, ur, us, ut, th, tl);
+      }
       if (scale1) {
         dfmul(cf.x, cf.y, rh, rl, rh, rl);
         dfmul(cf.x, cf.y, sh, sl, sh, sl);
@@ -326,7 +402,10 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       }
     }
     // transposed derivatives, in place: group g along direction g
-    line_task<P, true>(myR, myR, loff);
+    if constexpr (P == 8)
+      line_task_xt<P>(myR, myR, loff);
+    else
+      line_task<P, true>(myR, myR, loff);
     __syncthreads();
     // w = CR + CS + CT (+ c2 B u), times 2^oexp -> double
     const int2 ci = s_ci;
@@ -456,6 +535,14 @@ static void df_upload_d(const sem_handle* h) {
       }
   }
   SEM_CUDA(cudaMemcpyToSymbol(c_df_eo, eo, sizeof(eo), (size_t)P * sizeof(eo)));
+  float rb[2][kMaxH] = {};
+  for (int a = 0; a < 2; ++a)
+    for (int i = 0; i < H; ++i) {
+      double sum = 0.0;
+      for (int l = 0; l < H; ++l) sum += std::fabs((double)eo[1][a][0][i * H + l]);
+      rb[a][i] = (float)(sum * (1.0 + 0x1p-18));
+    }
+  SEM_CUDA(cudaMemcpyToSymbol(c_df_rb, rb, sizeof(rb), (size_t)P * sizeof(rb)));
   // a copy from pageable memory may still be in flight when the call returns,
   // and only the legacy stream is ordered after it: wait once, so that kernels
   // on non-blocking streams see the tables

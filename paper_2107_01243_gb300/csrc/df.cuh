@@ -120,6 +120,43 @@ __device__ __forceinline__ void dfmul(float ah, float al, float bh, float bl, fl
   pl = e;
 }
 
+// --------------------------------------------------- extraction dot products
+// Error-free extraction against a power-of-two bound (Rump, Ogita and Oishi,
+// "Accurate floating-point summation", SIAM J. Sci. Comput. 31, 2008): with
+// sigma = 2^k >= sum_l |c_l z_l|, the float q = RN(c z + sigma) - sigma is a
+// multiple of 2^-24 sigma, so the running sum S of the q of a dot product is
+// exact (every partial sum is such a multiple below sigma in magnitude), and
+// r = RN(c z - q) is the product's remainder.  A term costs 7 instructions
+// instead of the 12 of the TwoSum form above; the price is that the error term
+// E collects remainders of size up to 2^-24 sigma rather than 2^-24 |c z|, so
+// its rounding costs one to three bits against the TwoSum form (measured in a
+// float32 emulation of both against the FP64 oracle).  The kernel therefore
+// uses it only where the bound is tight: the geometric-factor products and the
+// transposed contractions, not the first derivatives of u.
+
+// smallest power of two >= b for a finite b >= 0 (0 for b = 0)
+__device__ __forceinline__ float df_pow2_ceil(float b) {
+  return __uint_as_float((__float_as_uint(b) + 0x007FFFFFu) & 0xFF800000u);
+}
+
+// first term: S = q, E = r + cross terms
+__device__ __forceinline__ void xmac0(float ch, float cl, float zh, float zl, float sig,
+                                      float& S, float& E) {
+  const float q = __fsub_rn(__fmaf_rn(ch, zh, sig), sig);
+  const float r = __fmaf_rn(ch, zh, -q);
+  S = q;
+  E = __fmaf_rn(cl, zh, __fmaf_rn(ch, zl, r));
+}
+
+// next term: S += q exactly, E += r + cross terms
+__device__ __forceinline__ void xmac(float ch, float cl, float zh, float zl, float sig,
+                                     float& S, float& E) {
+  const float q = __fsub_rn(__fmaf_rn(ch, zh, sig), sig);
+  const float r = __fmaf_rn(ch, zh, -q);
+  S = __fadd_rn(S, q);
+  E = __fmaf_rn(cl, zh, __fmaf_rn(ch, zl, __fadd_rn(E, r)));
+}
+
 // ------------------------------------------------------------------ range
 // Pair arithmetic keeps its 48 bits only while every intermediate stays in
 // FP32's exponent range (normal floats from 2^-126 to 2^128).  The element
