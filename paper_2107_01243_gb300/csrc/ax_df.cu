@@ -97,17 +97,27 @@ __device__ __forceinline__ void line_task(const float2* in, float2* out, const i
     dfadd(xh[l], xl[l], xh[N - l], xl[N - l], eh[l], el[l]);
     dfadd(xh[l], xl[l], -xh[N - l], -xl[N - l], oh[l], ol[l]);
   }
+  // D annihilates constants (its rows sum to zero), hence so do the rows of S:
+  // S e = sum_{l >= 1} S_il (e_l - e_0), one term fewer per dot for the
+  // price of H - 1 pair subtractions.  D^T has no such property.
+  constexpr int L0 = TRANS ? 0 : 1;
+  if constexpr (!TRANS) {
+#pragma unroll
+    for (int l = 1; l < H; ++l) dfadd(eh[l], el[l], -eh[0], -el[0], eh[l], el[l]);
+  }
   float yh[P], yl[P];
 #pragma unroll
   for (int i = 0; i < H; ++i) {
     float Ph, Pl, Mh, Ml;
     tmac0(c_df_eo[P][T][0][0][i * H], c_df_eo[P][T][0][1][i * H], oh[0], ol[0], Ph, Pl);
-    tmac0(c_df_eo[P][T][1][0][i * H], c_df_eo[P][T][1][1][i * H], eh[0], el[0], Mh, Ml);
+    tmac0(c_df_eo[P][T][1][0][i * H + L0], c_df_eo[P][T][1][1][i * H + L0], eh[L0], el[L0], Mh,
+          Ml);
 #pragma unroll
-    for (int l = 1; l < H; ++l) {
+    for (int l = 1; l < H; ++l)
       tmac(c_df_eo[P][T][0][0][i * H + l], c_df_eo[P][T][0][1][i * H + l], oh[l], ol[l], Ph, Pl);
+#pragma unroll
+    for (int l = L0 + 1; l < H; ++l)
       tmac(c_df_eo[P][T][1][0][i * H + l], c_df_eo[P][T][1][1][i * H + l], eh[l], el[l], Mh, Ml);
-    }
     dfadd(Ph, Pl, Mh, Ml, yh[i], yl[i]);
     dfadd(Ph, Pl, -Mh, -Ml, yh[N - i], yl[N - i]);
   }
@@ -240,12 +250,18 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
   float2* myR = g == 0 ? R[0] : (g == 1 ? R[1] : R[2]);
   const ItemSeq<FUSE> seq{E};          // this CTA's elements in order
 
+  // the element's exponent word comes with its stage (a 4-byte cp.async that
+  // thread 0 completes before it reads the word), so that the per-element
+  // setup of thread 0 does not wait on a global load
+  __shared__ int s_esc[STAGES];
   auto issue = [&](int e, int s) {
     unsigned char* dst = stage0 + s * SB;
     mbar_arrive_expect_tx(&bar[s], SB);
     bulk_g2s(dst, u + (size_t)e * P3, UB, &bar[s]);
     bulk_g2s(dst + UB, G + (size_t)e * 6 * P3, GB, &bar[s]);
     if (helm) bulk_g2s(dst + UB + GB, B + (size_t)e * P3, BB, &bar[s]);
+    cp_async4(&s_esc[s], esc + e);
+    cp_async_commit();
   };
   if (tid == 0) {
 #pragma unroll
@@ -253,8 +269,14 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     mbar_fence_init();
   }
   __syncthreads();
-  int ahead = seq.first(), issued = 0;     // thread 0: next element to prefetch, copies issued
+  // thread 0's state, kept in shared memory so that it takes no registers in
+  // the other threads: next element to prefetch, copies issued, box position
+  __shared__ struct {
+    int ahead, issued;
+    BoxWalk bw;
+  } s_pr;
   if (tid == 0) {
+    int ahead = seq.first(), issued = 0;
 #pragma unroll
     for (int s = 0; s < STAGES; ++s) {
       if (ahead < E) {
@@ -263,9 +285,10 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
         ++issued;
       }
     }
+    s_pr.ahead = ahead;
+    s_pr.issued = issued;
   }
 
-  BoxWalk bw;                          // thread 0 (FUSE)
   __shared__ unsigned s_fl;            // FusedStore flags of the current element
   __shared__ unsigned s_key[NW];       // per-warp magnitude keys of u_e
   __shared__ float4 s_cf;              // the element's c1 (x, y) and c2 (z, w) pairs
@@ -306,8 +329,9 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     if (__syncthreads_or(!ok || wbad)) {
       if (__syncthreads_or(!ok)) {
         if (tid == 0) {
-          for (int nn = n; nn < issued; ++nn)
+          for (int nn = n; nn < s_pr.issued; ++nn)
             mbar_wait_bounded(&bar[nn % STAGES], (uint32_t)(nn / STAGES) & 1u, err, timeout_ns);
+          cp_async_wait<0>();
         }
         break;                         // the reduction below still counts this CTA
       }
@@ -334,11 +358,12 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     }
     if (tid == 0) {
       if (FUSE) {                      // box position of e, read back in the output phase
-        if (e % kFuseSeg == 0) bw.start(e, fb); else bw.step(fb);
-        s_fl = fused_flags(e, bw, fb);
+        if (e % kFuseSeg == 0) s_pr.bw.start(e, fb); else s_pr.bw.step(fb);
+        s_fl = fused_flags(e, s_pr.bw, fb);
       }
       // the element's coefficients and exponents
-      const int sw = esc[e];
+      cp_async_wait<0>();
+      const int sw = s_esc[s];
       const int a1 = (int)(short)(sw & 0xFFFF) + C.t1;
       const int a2 = helm ? (sw >> 16) + C.t2 : a1;
       const int unit = max(a1, a2);
@@ -394,11 +419,11 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     }
     __syncthreads();
     if (!helm && tid == 0) {                   // stage s consumed
-      if (ahead < E) {
+      if (s_pr.ahead < E) {
         fence_proxy_async_smem();
-        issue(ahead, s);
-        ahead = seq.next(ahead);
-        ++issued;
+        issue(s_pr.ahead, s);
+        s_pr.ahead = seq.next(s_pr.ahead);
+        ++s_pr.issued;
       }
     }
     // transposed derivatives, in place: group g along direction g
@@ -467,11 +492,11 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     if (helm) {
       __syncthreads();                         // U and the stage are free
       if (tid == 0) {
-        if (ahead < E) {
+        if (s_pr.ahead < E) {
           fence_proxy_async_smem();
-          issue(ahead, s);
-          ahead = seq.next(ahead);
-          ++issued;
+          issue(s_pr.ahead, s);
+          s_pr.ahead = seq.next(s_pr.ahead);
+          ++s_pr.issued;
         }
       }
     }
