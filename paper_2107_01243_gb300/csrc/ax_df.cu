@@ -7,7 +7,7 @@
 // STAGES elements in flight with bulk copies (u_e as doubles, the 6 G pairs,
 // B pairs for Helmholtz).  Contractions are "line tasks": a thread reads one
 // line of P pairs and makes the P outputs of that line, so every D index is a
-// compile-time constant (D lives in constant memory).  The three thread
+// compile-time constant (D's tables are immediates).  The three thread
 // groups take the r-, s- and t-lines side by side and run the same code with
 // different element positions, which keeps the kernel small enough for the instruction
 // cache:
@@ -16,33 +16,30 @@
 //   G        every point: (WR, WS, WT) = h1 G (UR, US, UT), in place
 //   backward group g: lines of W along direction g, in place          (D^T)
 //   final    w = CR + CS + CT (+ h2 B u) -> double
-// Sums use exact float transformations (TwoSum, FMA product errors).  At
-// P = 8 the G products and the backward contractions use the cheaper
-// extraction form (df.cuh: 7 instead of 12 instructions a term); the forward
-// derivatives keep TwoSum, whose error stays relative to the products where
-// smooth u makes the derivatives cancel (the extraction form lost 2-3 bits
-// there in a float32 emulation against the FP64 oracle).
+// Sums use exact float transformations.  The forward derivatives use TwoSum
+// and FMA product errors, whose error stays relative to the products where
+// smooth u makes the derivatives cancel; the G products and the backward
+// contractions use the cheaper extraction form (df.cuh: 7 instead of 12
+// instructions a term), which lost 2-3 bits against TwoSum on the forward
+// derivatives of smooth fields in a float32 emulation against the FP64
+// oracle and about one bit where it is used.  D's tables are compile-time
+// constants (df_tables.cuh).
 // The shared-memory layout (DFLayout) keeps the line and point accesses free
 // of bank conflicts; each thread computes its positions once per launch.
 #include "sem_internal.cuh"
 #include "tma.cuh"
 #include "df.cuh"
+#include "df_tables.cuh"
 #include "ax_tile.cuh"
 #include "reduce.cuh"
 #include "cg_state.cuh"
 
 namespace sem {
 
-// D (high and low parts) for every order, filled once per order on first use
-__constant__ float c_df_dh[kMaxP + 1][kMaxP * kMaxP];
-__constant__ float c_df_dl[kMaxP + 1][kMaxP * kMaxP];
-// even-odd halves for even P: [trans][0: A = (M_il - M_i,N-l)/2, 1: S = (M_il + M_i,N-l)/2]
-// [0: high, 1: low][i * (P/2) + l], M = D or D^T
-constexpr int kMaxH = kMaxP / 2 + 1;
-__constant__ float c_df_eo[kMaxP + 1][2][2][2][kMaxH * kMaxH];
-// bounds of the transposed even-odd rows: [0: A, 1: S][i] = (1 + 2^-18) sum_l
-// |high part of A_il| (resp. S_il)
-__constant__ float c_df_rb[kMaxP + 1][2][kMaxH];
+// D's even-odd tables as compile-time constants (df_tables.cuh, written by
+// gen_df_tables.py): [t: D or D^T][A or S][high or low][i * (P/2) + l] with
+// A = (M_il - M_i,N-l)/2, S = (M_il + M_i,N-l)/2, and the bounds of the
+// transposed extraction dots
 
 // h1 = m1 2^t1, h2 = m2 2^t2 with the mantissas as pairs (t = 0 while
 // |h| lies in [2^-16, 2^16), see df.cuh)
@@ -109,15 +106,15 @@ __device__ __forceinline__ void line_task(const float2* in, float2* out, const i
 #pragma unroll
   for (int i = 0; i < H; ++i) {
     float Ph, Pl, Mh, Ml;
-    tmac0(c_df_eo[P][T][0][0][i * H], c_df_eo[P][T][0][1][i * H], oh[0], ol[0], Ph, Pl);
-    tmac0(c_df_eo[P][T][1][0][i * H + L0], c_df_eo[P][T][1][1][i * H + L0], eh[L0], el[L0], Mh,
+    tmac0(DFTab<P>::eo(T, 0, 0, i * H), DFTab<P>::eo(T, 0, 1, i * H), oh[0], ol[0], Ph, Pl);
+    tmac0(DFTab<P>::eo(T, 1, 0, i * H + L0), DFTab<P>::eo(T, 1, 1, i * H + L0), eh[L0], el[L0], Mh,
           Ml);
 #pragma unroll
     for (int l = 1; l < H; ++l)
-      tmac(c_df_eo[P][T][0][0][i * H + l], c_df_eo[P][T][0][1][i * H + l], oh[l], ol[l], Ph, Pl);
+      tmac(DFTab<P>::eo(T, 0, 0, i * H + l), DFTab<P>::eo(T, 0, 1, i * H + l), oh[l], ol[l], Ph, Pl);
 #pragma unroll
     for (int l = L0 + 1; l < H; ++l)
-      tmac(c_df_eo[P][T][1][0][i * H + l], c_df_eo[P][T][1][1][i * H + l], eh[l], el[l], Mh, Ml);
+      tmac(DFTab<P>::eo(T, 1, 0, i * H + l), DFTab<P>::eo(T, 1, 1, i * H + l), eh[l], el[l], Mh, Ml);
     dfadd(Ph, Pl, Mh, Ml, yh[i], yl[i]);
     dfadd(Ph, Pl, -Mh, -Ml, yh[N - i], yl[N - i]);
   }
@@ -127,10 +124,12 @@ __device__ __forceinline__ void line_task(const float2* in, float2* out, const i
 
 // The transposed line task y_i = sum_l D_li x_l with extraction dots (df.cuh):
 // the same even-odd split, with one power-of-two bound per output pair,
-// sigma_i >= sum_l |A_il| |o_l| + |S_il| |e_l|, taken from the row sums of
-// the tables (c_df_rb, enlarged by 2^-18 to cover the roundings of the bound)
-// and the largest |o| and |e| of the line.  Both dots of a pair share sigma_i,
-// so their sums y_i = SP + SM and y_{N-i} = SP - SM are exact as well.
+// sigma_i >= sum_l |A_il| |o_l| + |S_il| |e_l|.  P <= 8: the bound is taken
+// from the row sums of the tables (DFTab::rb) and the largest |o| and |e| of
+// the line; P = 10, whose rows are longer and whose bound that way is looser,
+// forms the sum itself from the absolute entries (DFTab::ab).  Both tables
+// are enlarged by 2^-18 to cover the roundings of the bound.  Both dots of a
+// pair share sigma_i, so y_i = SP + SM and y_{N-i} = SP - SM are exact too.
 template <int P>
 __device__ __forceinline__ void line_task_xt(const float2* in, float2* out, const int (&off)[P]) {
   static_assert(P % 2 == 0, "even-odd split needs an even number of points");
@@ -153,15 +152,26 @@ __device__ __forceinline__ void line_task_xt(const float2* in, float2* out, cons
   }
 #pragma unroll
   for (int i = 0; i < H; ++i) {
-    const float sig = df_pow2_ceil(__fmaf_rn(c_df_rb[P][0][i], mo, __fmul_rn(c_df_rb[P][1][i], me)));
+    float sig;
+    if constexpr (P >= 10) {
+      float b = 0.0f;
+#pragma unroll
+      for (int l = 0; l < H; ++l) {
+        b = __fmaf_rn(DFTab<P>::ab(0, i * H + l), fabsf(oh[l]), b);
+        b = __fmaf_rn(DFTab<P>::ab(1, i * H + l), fabsf(eh[l]), b);
+      }
+      sig = df_pow2_ceil(b);
+    } else {
+      sig = df_pow2_ceil(__fmaf_rn(DFTab<P>::rb(0, i), mo, __fmul_rn(DFTab<P>::rb(1, i), me)));
+    }
     float SP, EP, SM, EM;
-    xmac0(c_df_eo[P][1][0][0][i * H], c_df_eo[P][1][0][1][i * H], oh[0], ol[0], sig, SP, EP);
-    xmac0(c_df_eo[P][1][1][0][i * H], c_df_eo[P][1][1][1][i * H], eh[0], el[0], sig, SM, EM);
+    xmac0(DFTab<P>::eo(1, 0, 0, i * H), DFTab<P>::eo(1, 0, 1, i * H), oh[0], ol[0], sig, SP, EP);
+    xmac0(DFTab<P>::eo(1, 1, 0, i * H), DFTab<P>::eo(1, 1, 1, i * H), eh[0], el[0], sig, SM, EM);
 #pragma unroll
     for (int l = 1; l < H; ++l) {
-      xmac(c_df_eo[P][1][0][0][i * H + l], c_df_eo[P][1][0][1][i * H + l], oh[l], ol[l], sig, SP,
+      xmac(DFTab<P>::eo(1, 0, 0, i * H + l), DFTab<P>::eo(1, 0, 1, i * H + l), oh[l], ol[l], sig, SP,
            EP);
-      xmac(c_df_eo[P][1][1][0][i * H + l], c_df_eo[P][1][1][1][i * H + l], eh[l], el[l], sig, SM,
+      xmac(DFTab<P>::eo(1, 1, 0, i * H + l), DFTab<P>::eo(1, 1, 1, i * H + l), eh[l], el[l], sig, SM,
            EM);
     }
     // the line's inputs are all in registers, so the outputs may go out now
@@ -179,17 +189,6 @@ __device__ __forceinline__ void dot3_x(float2 g0, float2 g1, float2 g2, float2 v
   xmac(g2.x, g2.y, v2.x, v2.y, sig, S, E);
   oh = S;
   ol = E;
-}
-
-// sum of three products g_a * v_a
-__device__ __forceinline__ void dot3_df(float2 g0, float2 g1, float2 g2, float2 v0, float2 v1,
-                                        float2 v2, float& oh, float& ol) {
-  float S, err;
-  tmac0(g0.x, g0.y, v0.x, v0.y, S, err);
-  tmac(g1.x, g1.y, v1.x, v1.y, S, err);
-  tmac(g2.x, g2.y, v2.x, v2.y, S, err);
-  oh = S;
-  ol = err;
 }
 
 // Three groups of P x P threads, one per direction, run the line tasks of the
@@ -249,6 +248,9 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
   }
   float2* myR = g == 0 ? R[0] : (g == 1 ? R[1] : R[2]);
   const ItemSeq<FUSE> seq{E};          // this CTA's elements in order
+  // FUSE: NT is a multiple of P, so every point of this thread has i = tid % P
+  static_assert(NT % P == 0, "points of a thread must share their i");
+  const bool xlow = (tid % P) == 0;    // this thread's points pair with e - 1 along x
 
   // the element's exponent word comes with its stage (a 4-byte cp.async that
   // thread 0 completes before it reads the word), so that the per-element
@@ -310,7 +312,7 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
 #pragma unroll
     for (int m = 0; m < NQ; ++m) {
       const int q = tid + m * NT;
-      if (q < P3) {
+      if ((m + 1) * NT <= P3 || q < P3) {
         const double x = su[q];
         const unsigned long long xb = (unsigned long long)__double_as_longlong(x);
         key = max(key, (unsigned)(xb >> 32) & 0x7FFFFFFFu);
@@ -387,27 +389,21 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
 #pragma unroll
     for (int m = 0; m < NQ; ++m) {
       const int q = tid + m * NT;
-      if (q >= P3) break;
+      if ((m + 1) * NT > P3 && q >= P3) break;
       const int at = qoff[m];
       const float2 g11 = sg[q], g22 = sg[P3 + q], g33 = sg[2 * P3 + q];
       const float2 g12 = sg[3 * P3 + q], g13 = sg[4 * P3 + q], g23 = sg[5 * P3 + q];
       const float2 ur = R[0][at], us = R[1][at], ut = R[2][at];
       float rh, rl, sh, sl, th, tl;
-      if constexpr (P == 8) {
-        // one bound for the point's three rows: 3 max|G| max|u'| (1 + 2^-18)
-        const float mg = fmaxf(fmaxf(fmaxf(fabsf(g11.x), fabsf(g22.x)), fmaxf(fabsf(g33.x),
-                                                                           fabsf(g12.x))),
-                               fmaxf(fabsf(g13.x), fabsf(g23.x)));
-        const float mu = fmaxf(fmaxf(fabsf(ur.x), fabsf(us.x)), fabsf(ut.x));
-        const float sig = df_pow2_ceil(__fmul_rn(__fmul_rn(mg, 3.0f * (1.0f + 0x1p-18f)), mu));
-        dot3_x(g11, g12, g13, ur, us, ut, sig, rh, rl);
-        dot3_x(g12, g22, g23, ur, us, ut, sig, sh, sl);
-        dot3_x(g13, g23, g33, ur, us, ut, sig, th, tl);
-      } else {
-        dot3_df(g11, g12, g13, ur, us, ut, rh, rl);
-        dot3_df(g12, g22, g23, ur, us, ut, sh, sl);
-        dot3_df(g13, g23, g33, ur, us, ut, th, tl);
-      }
+      // one bound for the point's three rows: 3 max|G| max|u'| (1 + 2^-18)
+      const float mg = fmaxf(fmaxf(fmaxf(fabsf(g11.x), fabsf(g22.x)), fmaxf(fabsf(g33.x),
+                                                                         fabsf(g12.x))),
+                             fmaxf(fabsf(g13.x), fabsf(g23.x)));
+      const float mu = fmaxf(fmaxf(fabsf(ur.x), fabsf(us.x)), fabsf(ut.x));
+      const float sig = df_pow2_ceil(__fmul_rn(__fmul_rn(mg, 3.0f * (1.0f + 0x1p-18f)), mu));
+      dot3_x(g11, g12, g13, ur, us, ut, sig, rh, rl);
+      dot3_x(g12, g22, g23, ur, us, ut, sig, sh, sl);
+      dot3_x(g13, g23, g33, ur, us, ut, sig, th, tl);
       if (scale1) {
         dfmul(cf.x, cf.y, rh, rl, rh, rl);
         dfmul(cf.x, cf.y, sh, sl, sh, sl);
@@ -427,10 +423,7 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       }
     }
     // transposed derivatives, in place: group g along direction g
-    if constexpr (P == 8)
-      line_task_xt<P>(myR, myR, loff);
-    else
-      line_task<P, true>(myR, myR, loff);
+    line_task_xt<P>(myR, myR, loff);
     __syncthreads();
     // w = CR + CS + CT (+ c2 B u), times 2^oexp -> double
     const int2 ci = s_ci;
@@ -443,15 +436,14 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       pw_e = 0.0f;
     }
     double* we = w + (size_t)e * P3;
-    FusedStore<P, double> fs;
-    if constexpr (FUSE) {
-      fs.we = we;
-      fs.fl = s_fl;
-    }
+    // FUSE: masked points are written as zero, and the i = 0 points of an
+    // element that pairs with e - 1 add the copy e - 1 stored before
+    const unsigned fl = FUSE ? s_fl : 0u;
+    const bool xpair = (fl & 1u) && xlow;
 #pragma unroll
     for (int m = 0; m < NQ; ++m) {
       const int q = tid + m * NT;
-      if (q >= P3) break;
+      if ((m + 1) * NT > P3 && q >= P3) break;
       const int at = qoff[m];
       const float2 cr = R[0][at], cs = R[1][at], ct = R[2][at];
       float S = cr.x, er = cr.y;
@@ -478,10 +470,22 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       double val = (double)S + (double)er;   // exact widenings, one rounding
       if (ci.x != 0) val = df_ldexp(val, ci.x);
       if (nanel) val = __longlong_as_double(0x7FF8000000000000ll);
-      if constexpr (FUSE)
-        fs.store(q % P, (q / P) % P, q / P2, val);
-      else
-        we[q] = val;
+      if constexpr (FUSE) {
+        if (fl & 0xFCu) {            // element on a Dirichlet face (uniform branch)
+          const int i = tid % P, j = (q / P) % P, k = q / P2;
+          const unsigned pf = (i == 0 ? 4u : 0u) | (i == P - 1 ? 8u : 0u) |
+                              (j == 0 ? 16u : 0u) | (j == P - 1 ? 32u : 0u) |
+                              (k == 0 ? 64u : 0u) | (k == P - 1 ? 128u : 0u);
+          if (pf & fl) val = 0.0;
+        }
+        if (xpair) {
+          double* lo = we + q - P3 + (P - 1);
+          const double sum = *lo + val;
+          *lo = sum;
+          val = sum;
+        }
+      }
+      we[q] = val;
     }
     if (FUSE && pwst && (pwexp != 0 || nanel)) {
       pw_d += nanel ? __longlong_as_double(0x7FF8000000000000ll)
@@ -530,51 +534,6 @@ static size_t df_smem_bytes(bool helm) {
   return 128 + STAGES * SB + 4 * (size_t)L::VOL * sizeof(float2);
 }
 
-// copies D and its even-odd halves for this order into constant memory (once
-// per process: the library drives one device, see sem_setup)
-static void df_upload_d(const sem_handle* h) {
-  static bool done[kMaxP + 1] = {};
-  const int P = h->P, N = P - 1, H = P / 2;
-  if (done[P]) return;
-  float dh[kMaxP * kMaxP] = {}, dl[kMaxP * kMaxP] = {};
-  for (int q = 0; q < P * P; ++q) {
-    const double d = h->Dh[q];
-    dh[q] = (float)d;
-    dl[q] = (float)(d - (double)dh[q]);
-  }
-  const size_t off = (size_t)P * kMaxP * kMaxP * sizeof(float);
-  SEM_CUDA(cudaMemcpyToSymbol(c_df_dh, dh, sizeof(dh), off));
-  SEM_CUDA(cudaMemcpyToSymbol(c_df_dl, dl, sizeof(dl), off));
-  float eo[2][2][2][kMaxH * kMaxH] = {};
-  for (int t = 0; t < 2; ++t) {
-    auto M = [&](int i, int l) { return t ? h->Dh[l * P + i] : h->Dh[i * P + l]; };
-    for (int i = 0; i < H; ++i)
-      for (int l = 0; l < H; ++l) {
-        const double a = 0.5 * (M(i, l) - M(i, N - l));
-        const double sm = 0.5 * (M(i, l) + M(i, N - l));
-        const float ah = (float)a, sh = (float)sm;
-        eo[t][0][0][i * H + l] = ah;
-        eo[t][0][1][i * H + l] = (float)(a - (double)ah);
-        eo[t][1][0][i * H + l] = sh;
-        eo[t][1][1][i * H + l] = (float)(sm - (double)sh);
-      }
-  }
-  SEM_CUDA(cudaMemcpyToSymbol(c_df_eo, eo, sizeof(eo), (size_t)P * sizeof(eo)));
-  float rb[2][kMaxH] = {};
-  for (int a = 0; a < 2; ++a)
-    for (int i = 0; i < H; ++i) {
-      double sum = 0.0;
-      for (int l = 0; l < H; ++l) sum += std::fabs((double)eo[1][a][0][i * H + l]);
-      rb[a][i] = (float)(sum * (1.0 + 0x1p-18));
-    }
-  SEM_CUDA(cudaMemcpyToSymbol(c_df_rb, rb, sizeof(rb), (size_t)P * sizeof(rb)));
-  // a copy from pageable memory may still be in flight when the call returns,
-  // and only the legacy stream is ordered after it: wait once, so that kernels
-  // on non-blocking streams see the tables
-  SEM_CUDA(cudaDeviceSynchronize());
-  done[P] = true;
-}
-
 // A slab of whole element planes: elements [e0, e0 + E) of the handle, the
 // box fb (its nelz the slab's planes, its faces those the slab touches).
 struct DFSlab {
@@ -614,7 +573,6 @@ static void df_prepare_p(const sem_handle* h) {
     df_occupancy<P, 1, true>(helm != 0);
     df_occupancy<P, 2, true>(helm != 0);
   }
-  df_upload_d(h);
 }
 
 // The once-per-process setup of the double-float kernels (constant tables,
@@ -639,7 +597,6 @@ static int launch_df_p(const sem_handle* h, const double* u, double* w, double h
   const size_t smem = df_smem_bytes<P, STAGES>(helm);
   auto kern = ax_df_kernel<P, STAGES, FUSE>;
   const int o = df_occupancy<P, STAGES, FUSE>(helm);
-  df_upload_d(h);
   DFScal c;
   df_split_scalar(h1, c.h1h, c.h1l, c.t1);
   df_split_scalar(h2, c.h2h, c.h2l, c.t2);
