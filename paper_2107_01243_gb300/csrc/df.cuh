@@ -2,8 +2,9 @@
 //
 // A value is an unevaluated pair hi + lo of floats (about 48 significant bits).
 // GB300 runs FP32 FMA 60x faster than FP64 FMA, so FP64-accurate kernels that
-// would be bound by the FP64 pipe run on pairs instead.  Conversions to and
-// from double use integer bit manipulation only (no FP64 instructions).
+// would be bound by the FP64 pipe run on pairs instead.  The conversion from
+// double uses integer bit manipulation only (no FP64 instructions); results
+// go back to double as the exact widening of both parts and one FP64 add.
 //
 // Dot products keep the running sum S of the rounded high-part products and
 // an FP32 error term: each product's rounding error comes from an FMA, each
@@ -24,45 +25,20 @@ __device__ __forceinline__ void d2df(double x, float& hi, float& lo) {
   const unsigned int sign = h32 & 0x80000000u;
   const int ex = (int)((h32 >> 20) & 0x7FF);
   const int fe = ex - 1023 + 127;
-  if (fe <= 0) {
-    hi = 0.0f;
-    lo = 0.0f;
-    return;
-  }
-  hi = __uint_as_float(sign | ((unsigned)fe << 23) | ((h32 & 0xFFFFFu) << 3) | (l32 >> 29));
+  // the funnel shift leaves ex's low 9 bits in 31..23 and the top 23
+  // significand bits below them; adding 2^30 subtracts 896 from the exponent
+  // modulo 2^9, which gives fe with bit 31 clear for fe in [1, 254]
+  const float h = __uint_as_float(((__funnelshift_l(l32, h32, 3) + 0x40000000u) & 0x7FFFFFFFu) |
+                                  sign);
   // remaining 29 bits: keep the top 23 as an exact float integer, then scale
   const unsigned int r = (l32 & 0x1FFFFFFFu) >> 6;
   const float ri = __fsub_rn(__uint_as_float(0x4B000000u | r), 8388608.0f);
   const int se = ex - 942;                       // 2^(ex - 1075 + 6) as a float exponent
   const float scale = se > 0 ? __int_as_float(se << 23) : 0.0f;
-  lo = __uint_as_float(__float_as_uint(__fmul_rn(ri, scale)) | sign);
-}
-
-// (hi, lo) -> double, integer only.  The pair is first renormalised with
-// TwoSum so that |lo| <= ulp(hi)/2; lo's bits are then merged into the 53-bit
-// significand (truncated beyond it).
-__device__ __forceinline__ double df2d(float hi, float lo) {
-  const float s = __fadd_rn(hi, lo);
-  const float bb = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(lo, bb));
-  const unsigned int bs = __float_as_uint(s);
-  const int es = (int)((bs >> 23) & 0xFF);
-  if (es == 0) return 0.0;
-  unsigned long long m = ((unsigned long long)((bs & 0x7FFFFFu) | 0x800000u)) << 29;
-  int ed = es - 127 + 1023;
-  const unsigned int be = __float_as_uint(e);
-  const int ee = (int)((be >> 23) & 0xFF);
-  if (ee != 0) {
-    const unsigned long long me = (unsigned long long)((be & 0x7FFFFFu) | 0x800000u);
-    const int sh = 29 - (es - ee);               // <= 5 for a normalised pair
-    unsigned long long a = sh >= 0 ? (me << sh) : (sh > -64 ? (me >> (-sh)) : 0ull);
-    if ((be ^ bs) & 0x80000000u) m -= a; else m += a;
-    if (m >= (1ull << 53)) { m >>= 1; ++ed; }
-    else if (m < (1ull << 52)) { m <<= 1; --ed; }
-  }
-  const unsigned long long out = ((unsigned long long)(bs & 0x80000000u) << 32) |
-                                 ((unsigned long long)ed << 52) | (m & ((1ull << 52) - 1));
-  return __longlong_as_double((long long)out);
+  const float l = __uint_as_float(__float_as_uint(__fmul_rn(ri, scale)) | sign);
+  // selects rather than a branch: fe <= 0 (below FP32's normal range) gives 0
+  hi = fe > 0 ? h : 0.0f;
+  lo = fe > 0 ? l : 0.0f;
 }
 
 // First term of a dot product: (S, err) = c z exactly up to the dropped cl zl.
