@@ -208,12 +208,16 @@ __device__ __forceinline__ void dot3_x(float2 g0, float2 g1, float2 g2, float2 v
 // combines the exponents into the element's coefficients c1, c2 (both
 // <= 2 in magnitude after scaling, or h1, h2 themselves in the common case)
 // and the output exponent, by which the FP64 result is multiplied.
-template <int P, int STAGES, bool FUSE>
+template <int P, int STAGES, int MODE>
 __global__ void __launch_bounds__(3 * P * P, P == 8 ? 5 : 1)     // P = 8: five CTAs per SM
 ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2* __restrict__ G,
              const float2* __restrict__ B, const int* __restrict__ esc, DFScal C, int E,
              const CGState* __restrict__ st, int* __restrict__ err, uint64_t timeout_ns,
              FuseBox fb, CGState* __restrict__ pwst, double* __restrict__ partials) {
+  // MODE 0: plain output; 1: fused output (FUSE); 2: fused output and
+  // <p, H p> (PW, pwst set; whole-warp CTAs only)
+  constexpr bool FUSE = MODE >= 1, PW = MODE == 2;
+  static_assert(!PW || (3 * P * P) % 32 == 0, "<p, H p> needs whole-warp CTAs");
   using L = DFLayout<P>;
   constexpr int P2 = P * P, P3 = P2 * P, NT = 3 * P2;
   constexpr int NW = (NT + 31) / 32;
@@ -248,8 +252,13 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
   }
   float2* myR = g == 0 ? R[0] : (g == 1 ? R[1] : R[2]);
   const ItemSeq<FUSE> seq{E};          // this CTA's elements in order
-  // FUSE: NT is a multiple of P, so every point of this thread has i = tid % P
-  static_assert(NT % P == 0, "points of a thread must share their i");
+  // FUSE: NT = 3 P^2, so every point of this thread has i = tid % P and
+  // j = (tid / P) % P, and k = tid / P^2 + 3 m: the i- and j-face bits of its
+  // points (fused_flags' layout) are fixed for the kernel
+  static_assert(NT == 3 * P2, "points of a thread must share their i and j");
+  const unsigned pij = ((tid % P) == 0 ? 4u : 0u) | ((tid % P) == P - 1 ? 8u : 0u) |
+                       (((tid / P) % P) == 0 ? 16u : 0u) | (((tid / P) % P) == P - 1 ? 32u : 0u);
+  const int k0 = tid / P2;
   const bool xlow = (tid % P) == 0;    // this thread's points pair with e - 1 along x
 
   // the element's exponent word comes with its stage (a 4-byte cp.async that
@@ -372,7 +381,7 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       s_cf = make_float4(df_scale_down(C.h1h, a1 - unit), df_scale_down(C.h1l, a1 - unit),
                          df_scale_down(C.h2h, a2 - unit), df_scale_down(C.h2l, a2 - unit));
       int kE = 0;
-      if (FUSE && pwst && kU == 0 && !nanel) {
+      if (PW && kU == 0 && !nanel) {
         unsigned km = 0u;
 #pragma unroll
         for (int w2 = 0; w2 < NW; ++w2) km = max(km, s_key[w2]);
@@ -430,7 +439,7 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     // <p, H p> of an element with a nonzero exponent: the running pair is
     // moved to FP64 first, the element's own sum is scaled and added after
     const int pwexp = 2 * (ci.y + kU) + ci.x - kU;
-    if (FUSE && pwst && (pwexp != 0 || nanel)) {
+    if (PW && (pwexp != 0 || nanel)) {
       pw_d += (double)pw_s + (double)pw_e;
       pw_s = 0.0f;
       pw_e = 0.0f;
@@ -455,7 +464,7 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
         dfmul(cf.z, cf.w, bv.x, bv.y, bh, bl);
         tmac(bh, bl, uv.x, uv.y, S, er);
       }
-      if (FUSE && pwst) {
+      if constexpr (PW) {
         float2 pv = U[at];
         float ws = S, wl = er;
         if (ci.y != 0) {               // p and H p times 2^-kE, into [1, 2^49)
@@ -471,13 +480,9 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       if (ci.x != 0) val = df_ldexp(val, ci.x);
       if (nanel) val = __longlong_as_double(0x7FF8000000000000ll);
       if constexpr (FUSE) {
-        if (fl & 0xFCu) {            // element on a Dirichlet face (uniform branch)
-          const int i = tid % P, j = (q / P) % P, k = q / P2;
-          const unsigned pf = (i == 0 ? 4u : 0u) | (i == P - 1 ? 8u : 0u) |
-                              (j == 0 ? 16u : 0u) | (j == P - 1 ? 32u : 0u) |
-                              (k == 0 ? 64u : 0u) | (k == P - 1 ? 128u : 0u);
-          if (pf & fl) val = 0.0;
-        }
+        const int k = k0 + 3 * m;
+        const unsigned pf = pij | (k == 0 ? 64u : 0u) | (k == P - 1 ? 128u : 0u);
+        if (pf & fl & 0xFCu) val = 0.0;
         if (xpair) {
           double* lo = we + q - P3 + (P - 1);
           const double sum = *lo + val;
@@ -487,7 +492,7 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       }
       we[q] = val;
     }
-    if (FUSE && pwst && (pwexp != 0 || nanel)) {
+    if (PW && (pwexp != 0 || nanel)) {
       pw_d += nanel ? __longlong_as_double(0x7FF8000000000000ll)
                     : df_ldexp((double)pw_s + (double)pw_e, pwexp);
       pw_s = 0.0f;
@@ -505,13 +510,11 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
       }
     }
   }
-  if constexpr (FUSE && (3 * P * P) % 32 == 0) {
-    if (pwst) {
-      double v[1] = {((double)pw_s + (double)pw_e) + pw_d};
-      double tot[1];
-      if (grid_sum<1>(v, partials, &pwst->counter, tot) && threadIdx.x == 0) {
-        st_after_pw(pwst, tot[0]);
-      }
+  if constexpr (PW) {
+    double v[1] = {((double)pw_s + (double)pw_e) + pw_d};
+    double tot[1];
+    if (grid_sum<1>(v, partials, &pwst->counter, tot) && threadIdx.x == 0) {
+      st_after_pw(pwst, tot[0]);
     }
   }
 }
@@ -544,9 +547,9 @@ struct DFSlab {
 
 // CTAs per SM of one kernel variant (Poisson or Helmholtz stage size); the
 // first call also sets the variant's shared-memory attributes
-template <int P, int STAGES, bool FUSE>
+template <int P, int STAGES, int MODE>
 static int df_occupancy(bool helm) {
-  auto kern = ax_df_kernel<P, STAGES, FUSE>;
+  auto kern = ax_df_kernel<P, STAGES, MODE>;
   static bool configured = false;
   static int occ[2] = {0, 0};
   if (!configured) {
@@ -568,10 +571,14 @@ static int df_occupancy(bool helm) {
 template <int P>
 static void df_prepare_p(const sem_handle* h) {
   for (int helm = 0; helm < 2; ++helm) {
-    df_occupancy<P, 1, false>(helm != 0);
-    df_occupancy<P, 2, false>(helm != 0);
-    df_occupancy<P, 1, true>(helm != 0);
-    df_occupancy<P, 2, true>(helm != 0);
+    df_occupancy<P, 1, 0>(helm != 0);
+    df_occupancy<P, 2, 0>(helm != 0);
+    df_occupancy<P, 1, 1>(helm != 0);
+    df_occupancy<P, 2, 1>(helm != 0);
+    if constexpr ((3 * P * P) % 32 == 0) {
+      df_occupancy<P, 1, 2>(helm != 0);
+      df_occupancy<P, 2, 2>(helm != 0);
+    }
   }
 }
 
@@ -589,14 +596,14 @@ void df_prepare(const sem_handle* h) {
 }
 
 // returns the grid it launched (the fused operator's later passes need it)
-template <int P, int STAGES, bool FUSE = false>
+template <int P, int STAGES, int MODE = 0>
 static int launch_df_p(const sem_handle* h, const double* u, double* w, double h1, double h2,
                        const CGState* st, cudaStream_t s, CGState* pwst = nullptr,
                        const DFSlab* slab = nullptr) {
   const bool helm = h2 != 0.0;
   const size_t smem = df_smem_bytes<P, STAGES>(helm);
-  auto kern = ax_df_kernel<P, STAGES, FUSE>;
-  const int o = df_occupancy<P, STAGES, FUSE>(helm);
+  auto kern = ax_df_kernel<P, STAGES, MODE>;
+  const int o = df_occupancy<P, STAGES, MODE>(helm);
   DFScal c;
   df_split_scalar(h1, c.h1h, c.h1l, c.t1);
   df_split_scalar(h2, c.h2h, c.h2l, c.t2);
@@ -648,16 +655,21 @@ bool launch_ax_df_fused(const sem_handle* h, const double* u, double* w, double 
   const bool two = h->tune.df_variant != 0;
   switch (h->P) {
     case 6:
-      if (two) launch_df_p<6, 2, true>(h, u, w, h1, h2, st, s);
-      else launch_df_p<6, 1, true>(h, u, w, h1, h2, st, s);
+      if (two) launch_df_p<6, 2, 1>(h, u, w, h1, h2, st, s);
+      else launch_df_p<6, 1, 1>(h, u, w, h1, h2, st, s);
       return false;
     case 8:
-      if (two) launch_df_p<8, 2, true>(h, u, w, h1, h2, st, s, pwst);
-      else launch_df_p<8, 1, true>(h, u, w, h1, h2, st, s, pwst);
+      if (pwst) {
+        if (two) launch_df_p<8, 2, 2>(h, u, w, h1, h2, st, s, pwst);
+        else launch_df_p<8, 1, 2>(h, u, w, h1, h2, st, s, pwst);
+      } else {
+        if (two) launch_df_p<8, 2, 1>(h, u, w, h1, h2, st, s);
+        else launch_df_p<8, 1, 1>(h, u, w, h1, h2, st, s);
+      }
       return pwst != nullptr;
     case 10:
-      if (two) launch_df_p<10, 2, true>(h, u, w, h1, h2, st, s);
-      else launch_df_p<10, 1, true>(h, u, w, h1, h2, st, s);
+      if (two) launch_df_p<10, 2, 1>(h, u, w, h1, h2, st, s);
+      else launch_df_p<10, 1, 1>(h, u, w, h1, h2, st, s);
       return false;
     default: throw Error(SEM_ERR_ARG, "launch_ax_df_fused: unsupported order");
   }
@@ -675,16 +687,16 @@ void launch_ax_df_fused_slab(const sem_handle* h, const double* u, double* w, do
   const bool two = h->tune.df_variant != 0;
   switch (h->P) {
     case 6:
-      if (two) launch_df_p<6, 2, true>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
-      else launch_df_p<6, 1, true>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
+      if (two) launch_df_p<6, 2, 1>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
+      else launch_df_p<6, 1, 1>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
       break;
     case 8:
-      if (two) launch_df_p<8, 2, true>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
-      else launch_df_p<8, 1, true>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
+      if (two) launch_df_p<8, 2, 1>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
+      else launch_df_p<8, 1, 1>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
       break;
     case 10:
-      if (two) launch_df_p<10, 2, true>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
-      else launch_df_p<10, 1, true>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
+      if (two) launch_df_p<10, 2, 1>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
+      else launch_df_p<10, 1, 1>(h, u, w, h1, h2, nullptr, s, nullptr, &sl);
       break;
     default: throw Error(SEM_ERR_ARG, "launch_ax_df_fused_slab: unsupported order");
   }
