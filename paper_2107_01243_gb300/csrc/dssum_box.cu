@@ -59,22 +59,33 @@ __device__ __forceinline__ void sum_point(T* __restrict__ w, const BoxDims& d, i
   const bool fz = (k == N) && (ez < d.nelz - 1);
   const long long e0 = (long long)ex + (long long)d.nelx * (ey + (long long)d.nely * ez);
   const long long sx = P3, sy = (long long)d.nelx * P3, sz = (long long)d.nelx * d.nely * P3;
-  // offsets of the copies in increasing element order
+  // the (up to) eight copies c = cx + 2 cy + 4 cz in increasing element order,
+  // all loaded before any is added (one memory round trip per point)
   long long idx[8];
-  int nc = 0;
-  for (int cz = 0; cz <= (fz ? 1 : 0); ++cz)
-    for (int cy = 0; cy <= (fy ? 1 : 0); ++cy)
-      for (int cx = 0; cx <= (fx ? 1 : 0); ++cx) {
-        const int li = cx ? 0 : i, lj = cy ? 0 : j, lk = cz ? 0 : k;
-        idx[nc++] = e0 * P3 + cx * sx + cy * sy + cz * sz + (lk * P + lj) * P + li;
-      }
+  bool has[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+    has[c] = (!cx || fx) && (!cy || fy) && (!cz || fz);
+    const int li = cx ? 0 : i, lj = cy ? 0 : j, lk = cz ? 0 : k;
+    idx[c] = e0 * P3 + cx * sx + cy * sy + cz * sz + (lk * P + lj) * P + li;
+  }
   if (d.faces && on_mask(d, ix, iy, iz)) {
-    for (int c = 0; c < nc; ++c) w[idx[c]] = T(0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (has[c]) w[idx[c]] = T(0);
     return;
   }
-  T s = w[idx[0]];
-  for (int c = 1; c < nc; ++c) s += w[idx[c]];
-  for (int c = 0; c < nc; ++c) w[idx[c]] = s;
+  T v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = has[c] ? w[idx[c]] : T(0);
+  T s = v[0];
+#pragma unroll
+  for (int c = 1; c < 8; ++c)
+    if (has[c]) s += v[c];
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    if (has[c]) w[idx[c]] = s;
 }
 
 // m-th lattice coordinate that is not an interior element interface:
