@@ -449,6 +449,16 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
     // element that pairs with e - 1 add the copy e - 1 stored before
     const unsigned fl = FUSE ? s_fl : 0u;
     const bool xpair = (fl & 1u) && xlow;
+    // MODE 1: the lower neighbour's copies of this thread's i = 0 points read
+    // before the output sums, so that the loads overlap them
+    double xprev[NQ];
+    if constexpr (FUSE && !PW) {
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) {
+        const int q = tid + m * NT;
+        xprev[m] = (xpair && ((m + 1) * NT <= P3 || q < P3)) ? we[q - P3 + (P - 1)] : 0.0;
+      }
+    }
 #pragma unroll
     for (int m = 0; m < NQ; ++m) {
       const int q = tid + m * NT;
@@ -485,7 +495,7 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
         if (pf & fl & 0xFCu) val = 0.0;
         if (xpair) {
           double* lo = we + q - P3 + (P - 1);
-          const double sum = *lo + val;
+          const double sum = (FUSE && !PW ? xprev[m] : *lo) + val;
           *lo = sum;
           val = sum;
         }
