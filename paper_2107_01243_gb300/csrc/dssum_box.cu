@@ -79,10 +79,28 @@ __device__ __forceinline__ void sum_point(T* __restrict__ w, const BoxDims& d, i
   T v[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) v[c] = has[c] ? w[idx[c]] : T(0);
+  // FP64: the adds of copies that no lane of the warp has are skipped as a
+  // whole (warp-uniform branches): FP64 adds run at 1/64 of the FP32 rate on
+  // this GPU, and a predicated add still occupies the pipe (FP32 adds are
+  // cheaper than the votes)
+  bool ax = true, ay = true, az = true;
+  if constexpr (sizeof(T) == 8) {
+    const unsigned am = __activemask();
+    ax = __any_sync(am, fx);
+    ay = __any_sync(am, fy);
+    az = __any_sync(am, fz);
+  }
   T s = v[0];
+  if (ax && has[1]) s += v[1];
+  if (ay) {
+    if (has[2]) s += v[2];
+    if (ax && has[3]) s += v[3];
+  }
+  if (az) {
 #pragma unroll
-  for (int c = 1; c < 8; ++c)
-    if (has[c]) s += v[c];
+    for (int c = 4; c < 8; ++c)
+      if (has[c]) s += v[c];
+  }
 #pragma unroll
   for (int c = 0; c < 8; ++c)
     if (has[c]) w[idx[c]] = s;
