@@ -219,3 +219,44 @@ def test_doublefloat_rejects_unsupported_order():
     h, _ = make((2, 2, 2), 4)
     with pytest.raises(sem.SemError):
         sem.sem_set_f64_kernel(h, sem.SEM_F64_KERNEL_DOUBLEFLOAT)
+
+
+def per_element_rel(a, ref):
+    """max over elements of ||a_e - ref_e||_inf / ||ref_e||_inf."""
+    d = np.abs(a - ref).reshape(ref.shape[0], -1).max(axis=1)
+    m = np.abs(ref).reshape(ref.shape[0], -1).max(axis=1)
+    return float((d / m).max())
+
+
+@pytest.mark.parametrize("N", [5, 7, 9])
+@pytest.mark.parametrize("seed", [3, 1234])
+def test_ax_fp64_smooth_fields(N, seed):
+    """Smooth inputs are the hardest case of the double-float element
+    kernel: the derivatives of a smooth u cancel, so the result is small
+    against the products that form it.  Eight Fourier modes with
+    wavenumbers up to 4 on 4^3 elements of [0, 2 pi]^3 (each element spans
+    up to one wavelength); every element within 1e-12 of its own largest
+    output (a float32 emulation of the kernel's arithmetic gives at most
+    4.3e-13, at N = 9)."""
+    h, o = make((4, 4, 4), N)
+    u = si.eval_fourier(si.fourier_modes(seed), o.x, o.y, o.z)
+    for h1, h2 in ((1.0, 0.0), (0.37, 4.25)):
+        w = torch.empty(h.n_local, dtype=torch.float64, device=DEV)
+        sem.sem_ax(h, to_dev(u).view(-1), w, h1, h2)
+        torch.cuda.synchronize()
+        assert per_element_rel(to_np(w).reshape(o.shape), o.ax(u, h1, h2)) < TOL64, (h1, h2)
+
+
+@pytest.mark.parametrize("N", [5, 7, 9])
+def test_ax_fp64_strongly_deformed(N):
+    """A deformation amplitude of 0.3 (three times the workload's) makes the
+    off-diagonal geometric factors comparable to the diagonal ones; the
+    kernel's per-point bound of the G products takes the largest of all
+    six."""
+    h, o = make((3, 3, 2), N, deform=0.3)
+    assert np.all(o.detJ > 0)
+    for u in (si.uniform(o.shape, 71), si.eval_fourier(si.fourier_modes(72), o.x, o.y, o.z)):
+        w = torch.empty(h.n_local, dtype=torch.float64, device=DEV)
+        sem.sem_ax(h, to_dev(u).view(-1), w)
+        torch.cuda.synchronize()
+        assert per_element_rel(to_np(w).reshape(o.shape), o.ax(u)) < TOL64
