@@ -99,6 +99,208 @@ ax_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ G,
   }
 }
 
+// ------------------------------------------------- IEEE FP64, even P
+// The same operator in IEEE FP64 arithmetic for even P, with the even-odd
+// split of D: D is centro-antisymmetric on GLL nodes (D_{N-i,N-l} = -D_il),
+// so with e_l = x_l + x_{N-l} and o_l = x_l - x_{N-l} (l < P/2) a line's
+// outputs come in pairs y_i = A_i.o + S_i.e, y_{N-i} = A_i.o - S_i.e, where
+// A_il = (M_il - M_{i,N-l}) / 2 and S_il = (M_il + M_{i,N-l}) / 2 (M = D or
+// D^T): 2P^2 / 4 + 2P operations per line instead of P^2, about 20% fewer
+// FP64 operations per point at P = 8 for a kernel that GB300's FP64 pipe
+// bounds.  One element per CTA of 3 P^2 threads: group g runs the lines of
+// direction g (forward derivatives, then transposed contractions, in
+// place), and the geometric factors are applied point by point in between.
+// Used at P = 8 and 10 (see launch_ax).
+
+// even-odd halves of D in double: [P][trans][0: A, 1: S][i * (P/2) + l]
+constexpr int kEoH = kMaxP / 2 + 1;
+__constant__ double c_eo[kMaxP + 1][2][2][kEoH * kEoH];
+
+// shared-memory position of (i, j, k) for 8-byte values: P = 8 uses unpadded
+// 64-value planes with rows and columns XOR-swizzled by the plane parity (the
+// lines of all three directions and the point phases are free of bank
+// conflicts); other orders pad rows to P + 2 and planes to 8 mod 16 values
+template <int P>
+struct EoLayout {
+  static constexpr int RS = P + 2;
+  static constexpr int PL0 = P * RS;
+  static constexpr int PL = PL0 + ((8 - (PL0 % 16)) + 16) % 16;
+  static constexpr int VOL = P * PL;
+  __device__ static int at(int i, int j, int k) { return k * PL + j * RS + i; }
+};
+template <>
+struct EoLayout<8> {
+  static constexpr int PL = 64;
+  static constexpr int VOL = 8 * PL;
+  __device__ static int at(int i, int j, int k) {
+    return k * PL + 8 * (j ^ (k & 1)) + (i ^ (((j >> 1) + 4 * (k & 1)) & 7));
+  }
+};
+
+// tab: the even-odd halves of M in shared memory, [0: A, 1: S][i * (P/2) + l]
+// (read at every use: the compiler would otherwise keep all of them in
+// registers across the element loop and halve the CTAs per SM)
+template <int P>
+__device__ __forceinline__ void eo_line(const double* in, double* out, const int (&off)[P],
+                                        const double* tab) {
+  constexpr int H = P / 2, N = P - 1;
+  double x[P];
+#pragma unroll
+  for (int l = 0; l < P; ++l) x[l] = in[off[l]];
+  double e[H], o[H];
+#pragma unroll
+  for (int l = 0; l < H; ++l) {
+    e[l] = x[l] + x[N - l];
+    o[l] = x[l] - x[N - l];
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    double a = tab[i * H] * o[0];
+    double s = tab[H * H + i * H] * e[0];
+#pragma unroll
+    for (int l = 1; l < H; ++l) {
+      a = fma(tab[i * H + l], o[l], a);
+      s = fma(tab[H * H + i * H + l], e[l], s);
+    }
+    out[off[i]] = a + s;
+    out[off[N - i]] = a - s;
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(3 * P * P)
+ax_eo_kernel(const double* __restrict__ u, double* __restrict__ w, const double* __restrict__ G,
+             const double* __restrict__ B, const double* __restrict__ h1f, double h1, double h2,
+             int E, const CGState* __restrict__ st) {
+  using L = EoLayout<P>;
+  constexpr int P2 = P * P, P3 = P2 * P, NT = 3 * P2, NQ = (P3 + NT - 1) / NT;
+  if (st && st->done) return;
+  constexpr int H = P / 2;
+  __shared__ double sU[L::VOL];
+  __shared__ double sR[3][L::VOL];
+  __shared__ double sTab[2][2 * H * H];        // [D, D^T][A, S][i * H + l]
+  const int tid = threadIdx.x;
+  for (int q = tid; q < 4 * H * H; q += NT)
+    sTab[q / (2 * H * H)][q % (2 * H * H)] =
+        c_eo[P][q / (2 * H * H)][(q / (H * H)) % 2][q % (H * H)];
+  const int g = tid / P2, lam = tid % P2, c1 = lam % P, c2 = lam / P;
+  int loff[P];
+#pragma unroll
+  for (int l = 0; l < P; ++l)
+    loff[l] = g == 0 ? L::at(l, c1, c2) : (g == 1 ? L::at(c1, l, c2) : L::at(c1, c2, l));
+  int qoff[NQ];
+#pragma unroll
+  for (int m = 0; m < NQ; ++m) {
+    const int q = tid + m * NT;
+    qoff[m] = q < P3 ? L::at(q % P, (q / P) % P, q / P2) : 0;
+  }
+  double* myR = sR[g];
+  const bool helm = h2 != 0.0;
+  for (int e = blockIdx.x; e < E; e += gridDim.x) {
+    const size_t base = (size_t)e * P3;
+#pragma unroll
+    for (int m = 0; m < NQ; ++m) {
+      const int q = tid + m * NT;
+      if (q < P3) sU[qoff[m]] = u[base + q];
+    }
+    __syncthreads();
+    eo_line<P>(sU, myR, loff, sTab[0]);          // forward derivatives along g
+    __syncthreads();
+    const double* ge = G + (size_t)e * 6 * P3;
+#pragma unroll
+    for (int m = 0; m < NQ; ++m) {
+      const int q = tid + m * NT;
+      if (q >= P3) break;
+      const int at = qoff[m];
+      const double ur = sR[0][at], us = sR[1][at], ut = sR[2][at];
+      const double g11 = ge[q], g22 = ge[P3 + q], g33 = ge[2 * P3 + q];
+      const double g12 = ge[3 * P3 + q], g13 = ge[4 * P3 + q], g23 = ge[5 * P3 + q];
+      double wr = fma(g13, ut, fma(g12, us, g11 * ur));
+      double ws = fma(g23, ut, fma(g22, us, g12 * ur));
+      double wt = fma(g33, ut, fma(g23, us, g13 * ur));
+      const double c = h1f ? h1f[base + q] : h1;
+      if (h1f || c != 1.0) {
+        wr *= c;
+        ws *= c;
+        wt *= c;
+      }
+      sR[0][at] = wr;
+      sR[1][at] = ws;
+      sR[2][at] = wt;
+    }
+    __syncthreads();
+    eo_line<P>(myR, myR, loff, sTab[1]);         // transposed contractions, in place
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < NQ; ++m) {
+      const int q = tid + m * NT;
+      if (q >= P3) break;
+      const int at = qoff[m];
+      double acc = (sR[0][at] + sR[1][at]) + sR[2][at];
+      if (helm) acc = fma(h2 * B[base + q], sU[at], acc);
+      w[base + q] = acc;
+    }
+    // the next element's first phase rewrites sU (read above for Helmholtz)
+    // and its forward phase sR (read above): all threads finish here first
+    __syncthreads();
+  }
+}
+
+// copies the even-odd halves of D for this order into constant memory (once
+// per process: the library drives one device)
+static void eo_upload_d(const sem_handle* h) {
+  static bool done[kMaxP + 1] = {};
+  const int P = h->P, N = P - 1, H = P / 2;
+  if (done[P]) return;
+  double eo[2][2][kEoH * kEoH] = {};
+  for (int t = 0; t < 2; ++t) {
+    auto M = [&](int i, int l) { return t ? h->Dh[l * P + i] : h->Dh[i * P + l]; };
+    for (int i = 0; i < H; ++i)
+      for (int l = 0; l < H; ++l) {
+        eo[t][0][i * H + l] = 0.5 * (M(i, l) - M(i, N - l));
+        eo[t][1][i * H + l] = 0.5 * (M(i, l) + M(i, N - l));
+      }
+  }
+  SEM_CUDA(cudaMemcpyToSymbol(c_eo, eo, sizeof(eo), (size_t)P * sizeof(eo)));
+  // a copy from pageable memory may still be in flight when the call returns
+  // and only the legacy stream is ordered after it: wait once
+  SEM_CUDA(cudaDeviceSynchronize());
+  done[P] = true;
+}
+
+template <int P>
+static int eo_occupancy() {
+  static int occ = 0;
+  if (!occ) {
+    SEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ax_eo_kernel<P>, 3 * P * P, 0));
+    if (occ < 1) occ = 1;
+  }
+  return occ;
+}
+
+// the once-per-process setup of the IEEE FP64 even-order kernel (constant
+// tables, occupancy), run by sem_setup outside any stream capture
+void eo_prepare(const sem_handle* h) {
+  switch (h->P) {
+    case 8: eo_occupancy<8>(); break;
+    case 10: eo_occupancy<10>(); break;
+    default: return;
+  }
+  eo_upload_d(h);
+}
+
+template <int P>
+static void launch_eo_p(const sem_handle* h, const OpData<double>& op, const double* u, double* w,
+                        double h1, double h2, const double* h1f, const CGState* st,
+                        cudaStream_t s) {
+  eo_upload_d(h);
+  const int E = (int)h->E;
+  int grid = (int)std::min<int64_t>(E, (int64_t)eo_occupancy<P>() * sem_num_sms());
+  if (grid < 1) grid = 1;
+  ax_eo_kernel<P><<<grid, 3 * P * P, 0, s>>>(u, w, op.G.ptr, op.B.ptr, h1f, h1, h2, E, st);
+  SEM_CHECK_LAUNCH();
+}
+
 // diag(H^e) at every local point: the rr, ss, tt terms run along the line
 // through the point, the mixed terms only see the point (D_ii D_jj ...).
 template <class T>
@@ -159,6 +361,14 @@ void launch_ax(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T h1,
     if (h->f64_kernel == SEM_F64_KERNEL_DOUBLEFLOAT)
       throw Error(SEM_ERR_STATE, "double-float Ax needs N in {5, 7, 9}, constant h1 and "
                                  "16-byte aligned vectors");
+    // IEEE FP64: the even-odd kernel at P = 8 and 10 (measured on 32^3-size
+    // meshes: 2.6% and 17% faster than the column kernel below; at P = 6 its
+    // 108-thread CTAs idle a fifth of their lanes and it was 18% slower)
+    switch (h->P) {
+      case 8: launch_eo_p<8>(h, op, u, w, h1, h2, h1f, st, s); return;
+      case 10: launch_eo_p<10>(h, op, u, w, h1, h2, h1f, st, s); return;
+      default: break;
+    }
   }
   switch (h->P) {
     case 2: launch_ax_p<2, T>(h, op, u, w, h1, h2, h1f, st, s); break;

@@ -256,6 +256,7 @@ void launch_ax_tma(const sem_handle* h, const OpData<T>& op, const T* u, T* w, T
 // FP64-accurate double-float variant (even P in {6, 8, 10}, constant h1)
 bool df_ax_supported(const sem_handle* h, const void* u, const void* w, const void* h1f);
 void df_prepare(const sem_handle* h);          // once-per-process setup, run by sem_setup
+void eo_prepare(const sem_handle* h);          // the same for the IEEE FP64 even-order kernel
 void noalloc_prepare();                        // resolves sem_dot_noalloc's static array
 void launch_ax_df(const sem_handle* h, const double* u, double* w, double h1, double h2,
                   const CGState* state, cudaStream_t s);

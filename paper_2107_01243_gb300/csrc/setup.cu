@@ -492,6 +492,7 @@ extern "C" sem_status sem_setup(const sem_mesh_desc* mesh, int N, int precision_
       SEM_CHECK_LAUNCH();
       df_prepare(h.get());
     }
+    if (h->f64.G.ptr) eo_prepare(h.get());
     noalloc_prepare();
     h->dev_err.alloc(1);
     SEM_CUDA(cudaMemsetAsync(h->dev_err.ptr, 0, sizeof(int), s));

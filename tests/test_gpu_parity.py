@@ -260,3 +260,22 @@ def test_ax_fp64_strongly_deformed(N):
         sem.sem_ax(h, to_dev(u).view(-1), w)
         torch.cuda.synchronize()
         assert per_element_rel(to_np(w).reshape(o.shape), o.ax(u)) < TOL64
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 7, 9])
+def test_ax_fp64_native_every_path(N):
+    """IEEE FP64 Ax (SEM_F64_KERNEL_NATIVE): the even-odd kernel at N = 7
+    and 9, the column kernel at the other orders, with constant h1, a
+    per-point h1 and the Helmholtz term, against the oracle at the FP64
+    tolerance."""
+    h, o = make((3, 2, 2), N)
+    sem.sem_set_f64_kernel(h, sem.SEM_F64_KERNEL_NATIVE)
+    u = si.uniform(o.shape, 81)
+    h1f = si.smooth_coefficient(o.x, o.y, o.z, 82)
+    for h1, h2, field in ((1.0, 0.0, None), (0.37, 4.25, None), (0.0, 1.5, h1f)):
+        w = torch.empty(h.n_local, dtype=torch.float64, device=DEV)
+        sem.sem_ax(h, to_dev(u).view(-1), w, h1, h2,
+                   h1_field=None if field is None else to_dev(field).view(-1))
+        sem.sem_sync(h)
+        ref = o.ax(u, h1, h2, field)
+        assert rel_inf(to_np(w).reshape(o.shape), ref) < TOL64, (h1, h2, field is None)
