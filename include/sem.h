@@ -201,8 +201,11 @@ sem_status sem_ax(sem_handle* h, const void* u_L, void* w_L, double h1, double h
  * kernel (default where supported: N in {5, 7, 9}, constant h1, 16-byte
  * aligned vectors) keeps FP64 inputs and outputs, stores G and B as float
  * pairs (8 bytes per value) and evaluates every sum with error-free float
- * transformations; its error against FP64 is about 1e-14 relative to the
- * largest |w| of an element.  Range: the operator is linear, so the kernel
+ * transformations (TwoSum for the derivatives of u, extraction against a
+ * power-of-two bound for the geometric-factor products and the transposed
+ * contractions); its error against FP64 is 1e-14 to a few 1e-13 relative to
+ * the largest |w| of an element (smooth u, whose derivatives cancel, at the
+ * high end; below 1e-12 in every case).  Range: the operator is linear, so the kernel
  * scales by exact powers of two to keep every intermediate inside FP32's
  * exponent range, and undoes the scaling on the FP64 result.  G and B of an
  * element whose largest magnitude lies outside [2^-16, 2^16), and h1 or h2
@@ -212,7 +215,8 @@ sem_status sem_ax(sem_handle* h, const void* u_L, void* w_L, double h1, double h
  * keeps the stated accuracy, up to FP64's own overflow and underflow of the
  * result.  An element whose u holds an Inf or a NaN gives NaN at all of its
  * points (the native kernel propagates them point by point instead).
- * SEM_F64_KERNEL_NATIVE forces IEEE FP64 arithmetic.  Returns SEM_ERR_ARG
+ * SEM_F64_KERNEL_NATIVE forces IEEE FP64 arithmetic (at N = 7 and 9 with the
+ * even-odd split of D, about 20% fewer FP64 operations).  Returns SEM_ERR_ARG
  * for an unknown kind.
  */
 sem_status sem_set_f64_kernel(sem_handle* h, int kind);
