@@ -214,7 +214,8 @@ sem_status sem_ax(sem_handle* h, const void* u_L, void* w_L, double h1, double h
  * is rescaled by its own maximum in the kernel.  So every finite FP64 input
  * keeps the stated accuracy, up to FP64's own overflow and underflow of the
  * result.  An element whose u holds an Inf or a NaN gives NaN at all of its
- * points (the native kernel propagates them point by point instead).
+ * points (the native kernel lets them spread through the element's contractions
+ * instead, so some of its points stay finite).
  * SEM_F64_KERNEL_NATIVE forces IEEE FP64 arithmetic (at N = 7 and 9 with the
  * even-odd split of D, about 20% fewer FP64 operations).  Returns SEM_ERR_ARG
  * for an unknown kind.
