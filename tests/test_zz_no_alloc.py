@@ -1,6 +1,7 @@
 """sem_dot_noalloc, the entry point for callers that cannot allocate device
 memory at the call site (stream capture, fixed memory budgets): called through
-the C ABI twice in a row, it must give the same inner product as sem_dot.
+the C ABI twice in a row, it must give the oracle's unique-dof inner product
+sum_L a b / mult and the same value as sem_dot.
 Collected last on purpose: it uses the library's static scratch array."""
 import numpy as np
 import pytest
@@ -8,6 +9,7 @@ import torch
 
 import paper_2107_01243_gb300 as sem
 import seeded_inputs as si
+from oracle import mesh, operator
 from tests.helpers import TWO_PI
 
 pytestmark = pytest.mark.gpu
@@ -32,14 +34,18 @@ def test_noalloc_dot_matches_sem_dot_twice(nel, N):
     if nel in ((3, 3, 1), (513, 1, 1)):
         tail = h.n_local % POINTS_PER_BLOCK
         assert h.n_local > POINTS_PER_BLOCK and 0 < tail <= 512, (h.n_local, tail)
+    mult = mesh.multiplicity(mesh.global_ids(*nel, N))
     ref = torch.empty(1, dtype=torch.float64, device=DEV)
     got = torch.empty(1, dtype=torch.float64, device=DEV)
     for call, (sa, sb) in enumerate(((60, 61), (62, 63))):
+        an, bn = si.uniform(shape, sa), si.uniform(shape, sb)
         a, b = _vec(shape, sa), _vec(shape, sb)
         sem.sem_dot(h, a, b, ref)
         sem.sem_dot_noalloc(h, a, b, got)
         torch.cuda.synchronize()
-        scale = float((a * b).abs().sum())
+        want = operator.weighted_dot(an, bn, mult)
+        scale = float(np.sum(np.abs(an * bn) / mult))
+        assert abs(float(got) - want) <= TOL64 * scale, (call, float(got), want)
         assert abs(float(got) - float(ref)) <= TOL64 * scale, (call, float(got), float(ref))
     # the same inputs again give the same bits (the static scratch is reused)
     first = float(got)
