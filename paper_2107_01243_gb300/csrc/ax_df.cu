@@ -265,12 +265,15 @@ ax_df_kernel(const double* __restrict__ u, double* __restrict__ w, const float2*
   // thread 0 completes before it reads the word), so that the per-element
   // setup of thread 0 does not wait on a global load
   __shared__ int s_esc[STAGES];
+  // u_e, G_e and B_e are read once: they leave L2 first, so that the output
+  // w, which the gather-scatter passes read back, stays there
   auto issue = [&](int e, int s) {
     unsigned char* dst = stage0 + s * SB;
+    const uint64_t pol = l2_policy_evict_first();
     mbar_arrive_expect_tx(&bar[s], SB);
-    bulk_g2s(dst, u + (size_t)e * P3, UB, &bar[s]);
-    bulk_g2s(dst + UB, G + (size_t)e * 6 * P3, GB, &bar[s]);
-    if (helm) bulk_g2s(dst + UB + GB, B + (size_t)e * P3, BB, &bar[s]);
+    bulk_g2s_hint(dst, u + (size_t)e * P3, UB, &bar[s], pol);
+    bulk_g2s_hint(dst + UB, G + (size_t)e * 6 * P3, GB, &bar[s], pol);
+    if (helm) bulk_g2s_hint(dst + UB + GB, B + (size_t)e * P3, BB, &bar[s], pol);
     cp_async4(&s_esc[s], esc + e);
     cp_async_commit();
   };

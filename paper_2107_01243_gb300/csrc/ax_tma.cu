@@ -59,15 +59,16 @@ ax_tma_kernel(const T* __restrict__ u, T* __restrict__ w, const T* __restrict__ 
     const int e0 = it * K;
     const int cnt = min(K, E - e0);
     T* dst = stage0 + s * SE;
+    const uint64_t pol = l2_policy_evict_first();   // G, B and h1 are read once
     mbar_arrive_expect_tx(&bar[s], nf * cnt * FB + starve_bytes);
     bulk_g2s(dst, u + (size_t)e0 * P3, cnt * FB, &bar[s]);
-    bulk_g2s(dst + K * P3, G + (size_t)e0 * 6 * P3, 6 * cnt * FB, &bar[s]);
+    bulk_g2s_hint(dst + K * P3, G + (size_t)e0 * 6 * P3, 6 * cnt * FB, &bar[s], pol);
     int off = 7 * K * P3;
     if (helm) {
-      bulk_g2s(dst + off, B + (size_t)e0 * P3, cnt * FB, &bar[s]);
+      bulk_g2s_hint(dst + off, B + (size_t)e0 * P3, cnt * FB, &bar[s], pol);
       off += K * P3;
     }
-    if (var) bulk_g2s(dst + off, h1f + (size_t)e0 * P3, cnt * FB, &bar[s]);
+    if (var) bulk_g2s_hint(dst + off, h1f + (size_t)e0 * P3, cnt * FB, &bar[s], pol);
   };
 
   if (tid == 0) {

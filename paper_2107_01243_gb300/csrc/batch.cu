@@ -203,10 +203,11 @@ bax_kernel(const BProb* __restrict__ probs, const int* __restrict__ cls_prob,
     const uint32_t FB = (uint32_t)(P3 * cnt) * 4u;
     const bool helm = pr.h2 != 0.0f;
     float* dst = stage0 + s * SV;
+    const uint64_t pol = l2_policy_evict_first();   // G and B are read once
     mbar_arrive_expect_tx(&bar[s], (helm ? 8u : 7u) * FB);
     bulk_g2s(dst, pr.p + e0 * P3, FB, &bar[s]);
-    bulk_g2s(dst + K * P3, pr.G + e0 * 6 * P3, 6 * FB, &bar[s]);
-    if (helm) bulk_g2s(dst + 7 * K * P3, pr.B + e0 * P3, FB, &bar[s]);
+    bulk_g2s_hint(dst + K * P3, pr.G + e0 * 6 * P3, 6 * FB, &bar[s], pol);
+    if (helm) bulk_g2s_hint(dst + 7 * K * P3, pr.B + e0 * P3, FB, &bar[s], pol);
   };
   long long ahead = next(blockIdx.x);    // thread 0: next item to prefetch
   if (tid == 0) {

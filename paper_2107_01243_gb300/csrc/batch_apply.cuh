@@ -111,10 +111,11 @@ bapply_kernel(const BProb* __restrict__ probs, const int* __restrict__ cls_prob,
     constexpr uint32_t FB = P3 * 4u;
     const bool helm = pr.h2 != 0.0f;
     float* dst = stage0 + s * SV;
+    const uint64_t pol = l2_policy_evict_first();   // G and B are read once
     mbar_arrive_expect_tx(&bar[s], (helm ? 8u : 7u) * FB);
     bulk_g2s(dst, pr.p + (long long)cur.e * P3, FB, &bar[s]);
-    bulk_g2s(dst + P3, pr.G + (long long)cur.e * 6 * P3, 6 * FB, &bar[s]);
-    if (helm) bulk_g2s(dst + 7 * P3, pr.B + (long long)cur.e * P3, FB, &bar[s]);
+    bulk_g2s_hint(dst + P3, pr.G + (long long)cur.e * 6 * P3, 6 * FB, &bar[s], pol);
+    if (helm) bulk_g2s_hint(dst + 7 * P3, pr.B + (long long)cur.e * P3, FB, &bar[s], pol);
   };
   SegCur ahead = resolve(blockIdx.x);                // thread 0: next element to prefetch
   int issued = 0;

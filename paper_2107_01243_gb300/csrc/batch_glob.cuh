@@ -124,9 +124,10 @@ bglob_kernel(const BProb* __restrict__ probs, const int* __restrict__ cls_prob,
     const long long e = g - s_off[c];
     const bool helm = pr.h2 != 0.0f;
     constexpr uint32_t FB = P3 * sizeof(float);
+    const uint64_t pol = l2_policy_evict_first();   // G and B are read once
     mbar_arrive_expect_tx(&bar[0], (helm ? 7u : 6u) * FB);
-    bulk_g2s(stage, pr.G + e * 6 * P3, 6 * FB, &bar[0]);
-    if (helm) bulk_g2s(stage + 6 * P3, pr.B + e * P3, FB, &bar[0]);
+    bulk_g2s_hint(stage, pr.G + e * 6 * P3, 6 * FB, &bar[0], pol);
+    if (helm) bulk_g2s_hint(stage + 6 * P3, pr.B + e * P3, FB, &bar[0], pol);
   };
   int c0;
   const long long g0 = next(blockIdx.x, c0);

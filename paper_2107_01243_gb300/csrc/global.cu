@@ -94,9 +94,10 @@ ax_glob_kernel(const float* __restrict__ u, float* __restrict__ w, const float* 
   };
   auto issue = [&](int e, int s) {
     float* dst = stage0 + s * SE;
+    const uint64_t pol = l2_policy_evict_first();   // G and B are read once
     mbar_arrive_expect_tx(&bar[s], (uint32_t)nf * FB);
-    bulk_g2s(dst, G + (size_t)e * 6 * P3, 6 * FB, &bar[s]);
-    if (helm) bulk_g2s(dst + 6 * P3, B + (size_t)e * P3, FB, &bar[s]);
+    bulk_g2s_hint(dst, G + (size_t)e * 6 * P3, 6 * FB, &bar[s], pol);
+    if (helm) bulk_g2s_hint(dst + 6 * P3, B + (size_t)e * P3, FB, &bar[s], pol);
   };
   if (tid == 0) {
 #pragma unroll
