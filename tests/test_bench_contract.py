@@ -91,6 +91,25 @@ def test_recorded_captures_match_the_current_kernel_source():
         assert set(cap) == {"source", "dram_bytes", "warp_instructions"}, name
 
 
+def test_capture_figures_match_the_committed_profile():
+    """The ncu figures the bench reports for the FP64 element kernel are the
+    ones its committed profile summary states: the same source digest, warp
+    instructions and DRAM bytes per launch."""
+    import os
+    import re
+    cap = bench.AX_CAPTURES["ax_df_kernel<8, 1, 1>"]
+    path = os.path.join(bench.ROOT, "profiles", "ax_df_kernel_fused_f64_e32768_n7.md")
+    with open(path) as fh:
+        text = fh.read()
+    assert "Source digest of the captured kernel (bench.ax_source_digest): %s." % cap["source"] in text
+    warp = re.search(r"\| smsp__inst_executed\.sum \| ([0-9.]+) M warp instructions", text)
+    assert warp and abs(float(warp.group(1)) * 1e6 - cap["warp_instructions"]) < 0.05e6
+    dram = re.search(r"\| dram__bytes_read\.sum \+ dram__bytes_write\.sum \| ([0-9.]+) \+ ([0-9.]+) = ", text)
+    assert dram
+    total_mb = float(dram.group(1)) + float(dram.group(2))
+    assert abs(total_mb * 1e6 - cap["dram_bytes"]) < 0.1e6
+
+
 def _counted_element_flops(N):
     """Adds and multiplies of one sum-factorised element operator, counted by
     running it on values that count the operations applied to them."""
